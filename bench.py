@@ -1,0 +1,298 @@
+"""Benchmark: Lanczos steps (Algorithm 1) of the Hubbard model on one GB300 per process.
+
+Default workload: 4x4 periodic square lattice, N_up = N_dn = 5 (dim 4368^2 = 19,079,424),
+t = 1, U = 4, FP64-accurate vectors, seeded random start vector. One bench "step" is one
+Lanczos iteration: the fused H.v pass, the update pass and the tridiagonal/convergence
+pass, on vectors resident in HBM (2 x 152.6 MB, larger than the 129 MB L2, so no flush is
+needed between steps).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica (the path has no exchange
+step); the timed region is bracketed by barriers and the max over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import ed_inputs  # noqa: E402
+
+METRIC = "Lanczos step time & H·v HBM GB/s (% peak); time-to-E0 at 1e-8 vs plain FP64"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self, device_index=0):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9 and f[0] == str(device_index):
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+ORACLE_SAMPLE_CODE = r"""
+import os, sys, time, json
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+import ed_inputs
+from oracle import hamiltonian
+w = ed_inputs.workload(sys.argv[2]); nsamp = int(sys.argv[3]); reps = int(sys.argv[4])
+L, b, nu, nd, t, U = w["n_sites"], w["bonds"], w["n_up"], w["n_dn"], w["t"], w["U"]
+import math
+dim = math.comb(L, nu) * math.comb(L, nd)
+x = ed_inputs.uniform_pm1(w["seed"], dim)
+rng = np.random.default_rng(0)
+times = []
+for r in range(reps):
+    rows = np.sort(rng.choice(dim, size=nsamp, replace=False))
+    t0 = time.perf_counter()
+    y = hamiltonian.hv_rows(L, b, nu, nd, t, U, x, rows)
+    # the vector operations of Algorithm 1 on the same rows
+    f = x[rows]; q = y - 0.5 * f; a = float(q @ f); q = q - a * f; bn = float(np.sqrt(q @ q))
+    times.append(time.perf_counter() - t0)
+print(json.dumps({"dim": dim, "nsamp": nsamp, "times": times}))
+"""
+
+
+def run_oracle_sample(workload: str, nsamp: int, reps: int) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", ORACLE_SAMPLE_CODE, ROOT, workload, str(nsamp),
+                          str(reps)], capture_output=True, text=True, env=env, check=True)
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    # full-step equivalents per second: each sample covers nsamp / dim of one Lanczos step
+    tot = sum(d["times"])
+    d["steps_per_s"] = reps * (nsamp / d["dim"]) / tot
+    return d
+
+
+# ----------------------------------------------------------------------------- helpers
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload_config(name, dim, du, dd, dtype):
+    w = ed_inputs.workload(name)
+    return {"workload": f"{name}: periodic lattice, {w['n_sites']} sites, N_up={w['n_up']}, "
+                        f"N_dn={w['n_dn']}, t={w['t']}, U={w['U']}",
+            "dim": dim, "dim_up": du, "dim_dn": dd, "vector_dtype": dtype,
+            "start": f"SplitMix64 seed {w['seed']}",
+            "l2": "inputs larger than L2: two Lanczos vectors of dim elements (no flush)",
+            "parallelism": "replicas (one independent Lanczos run per GPU)"}
+
+
+def bench_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    w = args.workload
+    nsamp = args.ref_rows
+    d = run_oracle_sample(w, nsamp, args.warmup + args.steps)
+    times = d["times"][args.warmup:]
+    sps = len(times) * (nsamp / d["dim"]) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": sps, "unit": "lanczos_steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 / sps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w, "dim": d["dim"]},
+            "cpu_baseline": {"value": sps, "unit": "lanczos_steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"oracle matrix-free H.v rows + vector ops on {nsamp} random "
+                                       f"rows of {d['dim']} per step, scaled to full steps"},
+            "e2e": {"value": sps, "unit": "lanczos_steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def bench_ours(args):
+    import torch
+    import paper_1511_00863_gb300 as ed
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = ed_inputs.workload(args.workload)
+    dtype = args.dtype or w["dtype"]
+    esize = 8 if dtype == "f64" else 4
+    L, bonds, nu, nd, t, U = w["n_sites"], w["bonds"], w["n_up"], w["n_dn"], w["t"], w["U"]
+    basis = ed.ed_build_basis(L, bonds, nu, nd)
+    du, dd, dim = ed.ed_basis_dims(basis)
+    tabs = ed.ed_basis_tables(basis)
+    K, W = args.steps, args.warmup
+    if K + W > ed.ED_MAX_STEPS:
+        raise SystemExit(f"steps + warmup must be <= {ed.ED_MAX_STEPS}")
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---------------------------------------------------------------- device-resident
+    opts = ed.make_opts(max_steps=ed.ED_MAX_STEPS, tol=0.0, seed=w["seed"], dtype=dtype)
+    st = ed.ed_lanczos_init(basis, opts)
+    ed.ed_lanczos_run(st, t, U, W)
+    torch.cuda.synchronize()
+    clocks = ClockSampler()
+    if rank == 0:
+        clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    hv_ms = ed.ed_lanczos_run(st, t, U, K, time_hv=True)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop(local) if rank == 0 else None
+    E_K, steps_done = ed.ed_lanczos_energy(st)
+    ed.ed_lanczos_destroy(st)
+    t_max = ms
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms, hv_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max, hv_ms = float(tt[0]), float(tt[1])
+    ms_per_step = t_max / K
+    value = ws * K / (t_max / 1e3)
+
+    # ---------------------------------------------------------------- end to end (C ABI)
+    # start vector from pinned host memory, copied in the timed region; fixed K steps;
+    # E0, a_j and b_j read back to the host by the call.
+    f1_host = torch.from_numpy(ed_inputs.start_vector_raw(w["seed"], dim)).to(
+        torch.float64 if dtype == "f64" else torch.float32).pin_memory()
+    f1_dev = torch.empty(dim, dtype=f1_host.dtype, device="cuda")
+    eopts = ed.make_opts(max_steps=K, tol=0.0, seed=w["seed"], dtype=dtype)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    f1_dev.copy_(f1_host, non_blocking=True)
+    res = ed.ed_lanczos_solve(basis, t, U, eopts, f1=f1_dev)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt[0])
+    d2h = 3 * (ed.ED_MAX_STEPS + 2) * 8 + 8 * math.ceil(K / 16)
+
+    if rank != 0:
+        ed.ed_basis_destroy(basis)
+        return 0
+    # ---------------------------------------------------------------- roofline
+    peak, peak_kind = _peaks()
+    table_bytes = du * (tabs["maxhops_up"] * 4 + 4) + dd * (tabs["maxhops_dn"] * 4 + 4)
+    hv_bytes = 3 * esize * dim + table_bytes  # read f_j, read f_{j-1}, write w; + tables
+    hv_launch_ms = hv_ms / K
+    achieved = hv_bytes / (hv_launch_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "hv_staged_kernel (fused Lanczos H.v)",
+                "bytes_per_launch": hv_bytes, "launch_ms": hv_launch_ms,
+                "peak_source": f"{peak_kind} HBM copy bandwidth"}
+    line = {"metric": METRIC, "value": value, "unit": "lanczos_steps/s", "n_gpus": ws,
+            "steps": K, "warmup": W, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": _workload_config(args.workload, dim, du, dd, dtype),
+            "hv_ms_per_step": hv_launch_ms, "E0_after_steps": E_K, "steps_done": steps_done,
+            "roofline": roofline,
+            "e2e": {"value": ws * K / e2e_s, "unit": "lanczos_steps/s",
+                    "h2d_bytes_per_step": dim * esize / K, "d2h_bytes_per_step": d2h / K,
+                    "E0": res["E0"], "api": "ed_lanczos_solve (f1 from pinned host memory)"},
+            "gpu_launches": 3 * K,
+            "clocks": clk}
+    if ws == 1 and not args.no_cpu_baseline:
+        d = run_oracle_sample(args.workload, args.cpu_rows, args.cpu_reps)
+        line["cpu_baseline"] = {"value": d["steps_per_s"], "unit": "lanczos_steps/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"{args.cpu_reps} x oracle matrix-free H.v rows + vector "
+                                          f"ops on {args.cpu_rows} random rows of {d['dim']}, "
+                                          "scaled to full Lanczos steps"}
+    ed.ed_basis_destroy(basis)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="torus4x4_5_5")
+    ap.add_argument("--dtype", default=None, choices=[None, "f64", "f32"])
+    ap.add_argument("--cpu-rows", type=int, default=400000)
+    ap.add_argument("--cpu-reps", type=int, default=8)
+    ap.add_argument("--ref-rows", type=int, default=100000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return bench_reference(args)
+    return bench_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

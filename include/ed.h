@@ -1,0 +1,169 @@
+/*
+ * ed.h - C ABI of the GB300 exact-diagonalization library (libed).
+ *
+ * The library computes the ground-state energy of the tight-binding / Hubbard
+ * Hamiltonian
+ *     H = -t sum_<ij> sum_sigma (c+_{i sigma} c_{j sigma} + h.c.) + U sum_i n_{i up} n_{i dn}
+ * (Siro & Harju, arXiv:1511.00863, Sec. 1 Eq. 1 and the on-site term) in the basis of
+ * fixed particle numbers (N_up, N_dn) (Sec. 2.1, Eq. 2) with the Lanczos iteration
+ * (Sec. 2.2, Algorithm 1). Everything runs on one CUDA device.
+ *
+ * Conventions shared by every entry point
+ *  - Basis order (Sec. 2.1; the paper leaves the order to its Ref. [Siro 2012]): a
+ *    single-species state is an n_sites-bit integer, bit i = site i occupied; states of
+ *    one species are ranked in ascending integer order. The two-species index is
+ *    rank_up * dim_dn + rank_dn (Sec. 4, Eqs. 5-6).
+ *  - Fermion sign: creation operators ordered by ascending site within a species, all up
+ *    before all down; a hop c+_i c_j carries (-1)^(particles of the same species strictly
+ *    between i and j). The hop matrix element is -t * sign.
+ *  - Bonds are an explicit list; a pair listed k times hops with amplitude k*t.
+ *  - Vectors passed to the library are DEVICE pointers in the dense layout above, owned by
+ *    the caller and never freed by the library; they must be 16-byte aligned and must not
+ *    alias each other. Host pointers are named as such.
+ *  - Every call is ordered on the caller's CUDA stream (`stream`, a cudaStream_t; NULL =
+ *    the legacy default stream). Calls that return host scalars synchronise that stream.
+ *  - Objects (ed_basis, ed_lanczos) are bound to the device that was current when they
+ *    were created; use them with that device current.
+ *  - Errors: a negative ed_status. ed_last_error() gives a message for the calling thread.
+ *    No entry point aborts the process or leaves device work running on error.
+ */
+#ifndef ED_H_
+#define ED_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ED_OK = 0,
+  ED_BREAKDOWN = 1,          /* b_{j+1} = 0 in Algorithm 1: an invariant subspace was found;
+                                success, the energy returned is exact for that subspace */
+  ED_ERR_ARG = -1,           /* invalid argument; nothing was launched */
+  ED_ERR_OOM = -2,           /* device memory allocation failed */
+  ED_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+  ED_ERR_TIMEOUT = -4,       /* a bounded device-side wait ran out */
+  ED_ERR_NOT_CONVERGED = -5  /* max_steps reached before the convergence test passed;
+                                the last estimate is still returned */
+} ed_status;
+
+typedef enum { ED_F64 = 0, ED_F32 = 1 } ed_dtype;
+
+/* Lattice (Sec. 2.1): n_sites in [1, 32]; bonds is a HOST array [n_bonds][2] of site
+ * pairs (i != j, both in range), read during ed_build_basis only. t_bond must be NULL
+ * (uniform hopping t); per-bond amplitudes are reserved for a later version. */
+typedef struct {
+  int32_t n_sites;
+  int32_t n_bonds;
+  const int32_t* bonds;
+  const double* t_bond;
+} ed_lattice;
+
+/* Model parameters: hopping t (Eq. 1) and on-site interaction U. */
+typedef struct {
+  double t;
+  double U;
+} ed_params;
+
+/* Lanczos options (Sec. 2.2).
+ *  max_steps  Krylov dimension cap m (1..ED_MAX_STEPS).
+ *  tol        stop when |E0(j) - E0(j-1)| <= tol * max(|E0(j)|, 1) (E0(j) = lowest
+ *             eigenvalue of T_j); tol <= 0 runs exactly max_steps steps.
+ *  reorth     0 = none (Algorithm 1 as printed). Other values are reserved.
+ *  seed       SplitMix64 seed of the random start vector when f1 == NULL.
+ *  dtype      ED_F64: FP64-accurate vectors and arithmetic.
+ *             ED_F32: FP32 vectors and H.v; alpha, beta, dot products and the
+ *             tridiagonal eigensolve stay in FP64.
+ *  schedule   kernel schedule id, -1 = library default. */
+typedef struct {
+  int32_t max_steps;
+  double tol;
+  int32_t reorth;
+  uint64_t seed;
+  ed_dtype dtype;
+  int32_t schedule;
+} ed_opts;
+
+#define ED_MAX_STEPS 1000
+
+typedef struct ed_basis ed_basis;
+typedef struct ed_lanczos ed_lanczos;
+
+/* ed_build_basis - build both single-species bases and their hop tables on the device.
+ * Sec. 2.1 (Eq. 2, Eq. 3): states of each species are unranked from their combinadic rank
+ * on the device; for every state and bond with exactly one occupied end, the hop target is
+ * ranked and the fermion sign recorded. n_up, n_dn in [0, n_sites]. The basis owns its
+ * device tables until ed_basis_destroy. Synchronises `stream`. */
+ed_status ed_build_basis(const ed_lattice* lattice, int32_t n_up, int32_t n_dn, void* stream,
+                         ed_basis** out);
+
+/* ed_basis_dims - dim_up = C(n_sites, n_up), dim_dn = C(n_sites, n_dn), dim = their product
+ * (Eq. 2). Any output pointer may be NULL. */
+ed_status ed_basis_dims(const ed_basis* basis, int64_t* dim_up, int64_t* dim_dn, int64_t* dim);
+
+/* ed_basis_tables - read-only DEVICE views of the basis tables (valid until destroy):
+ *  up_bits[dim_up], dn_bits[dim_dn]: uint32 bit strings in rank order.
+ *  hop_up[maxhops_up * dim_up], hop_dn[maxhops_dn * dim_dn]: hop k of state r at
+ *  [k * dim + r] (column-major ELL, Sec. 2.1 Fig. 2). An entry holds the target rank in
+ *  bits 0..29 and the fermion sign in bit 31 (1 = negative). Hops of a state are listed in
+ *  bond order; unused slots hold the value dim (an index past the end). */
+ed_status ed_basis_tables(const ed_basis* basis, const uint32_t** up_bits,
+                          const uint32_t** dn_bits, const int32_t** hop_up,
+                          const int32_t** hop_dn, int32_t* maxhops_up, int32_t* maxhops_dn);
+
+void ed_basis_destroy(ed_basis* basis);
+
+/* ed_hv - y = H x (the product on line 4 of Algorithm 1; Sec. 4 Eqs. 5-6 split it into the
+ * up part, which mixes sub-vectors, and the down part, which acts inside each). x and y are
+ * DEVICE arrays of dim elements of `dtype`, distinct and 16-byte aligned. Asynchronous. */
+ed_status ed_hv(const ed_basis* basis, const ed_params* params, ed_dtype dtype, const void* x,
+                void* y, void* stream);
+
+/* ed_start_vector - the random unit start vector f_1 of Algorithm 1: element i is
+ * 2*u_i - 1 with u_i the top 53 bits of the (i+1)-th SplitMix64 output for `seed`
+ * (Steele, Lea & Flood 2014) times 2^-53, then scaled to unit norm in FP64. ED_F32 rounds
+ * the normalised FP64 values to nearest. `out` is a DEVICE array of dim elements. */
+ed_status ed_start_vector(int64_t dim, uint64_t seed, ed_dtype dtype, void* out, void* stream);
+
+/* ed_lanczos_init - allocate a Lanczos state for `basis` with f_1 = f1 (a DEVICE vector of
+ * dim elements of opts->dtype, normalised by the library) or, if f1 == NULL, the
+ * ed_start_vector of opts->seed. The state owns its work vectors until destroy. */
+ed_status ed_lanczos_init(const ed_basis* basis, const ed_opts* opts, const void* f1,
+                          void* stream, ed_lanczos** out);
+
+/* ed_lanczos_step - one iteration j of Algorithm 1 with H(params): returns a_j and b_{j+1}
+ * (HOST pointers, may be NULL). Returns ED_BREAKDOWN when b_{j+1} vanishes (relative to
+ * max_i(|a_i| + b_i), 1e-13); further steps then return ED_ERR_ARG. Synchronises. */
+ed_status ed_lanczos_step(ed_lanczos* st, const ed_params* params, double* alpha_j,
+                          double* beta_j1);
+
+/* ed_lanczos_run - enqueue nsteps further iterations of Algorithm 1 with H(params) on the
+ * state's stream and return without synchronising; steps after a stop (breakdown or
+ * max_steps) return at once on the device. If hv_ms is not NULL, CUDA events are recorded
+ * on that stream around every fused H.v launch and *hv_ms receives their summed time in
+ * milliseconds (this synchronises the stream). */
+ed_status ed_lanczos_run(ed_lanczos* st, const ed_params* params, int32_t nsteps, float* hv_ms);
+
+/* ed_lanczos_energy - E0(j) = lowest eigenvalue of T_j (Sec. 2.2), computed on the device
+ * by Sturm-sequence bisection in FP64, and the number of steps j taken. Synchronises. */
+ed_status ed_lanczos_energy(ed_lanczos* st, double* E0, int32_t* steps);
+
+void ed_lanczos_destroy(ed_lanczos* st);
+
+/* ed_lanczos_solve - run Algorithm 1 from f1 (as in ed_lanczos_init) until the convergence
+ * test of opts passes, b_{j+1} vanishes, or max_steps; returns E0 (HOST) and the steps
+ * taken. alpha and beta (HOST, optional) receive a_1..a_m and b_2..b_{m+1}. Returns ED_OK,
+ * ED_BREAKDOWN or ED_ERR_NOT_CONVERGED (E0 still set) or an error. Synchronises `stream`. */
+ed_status ed_lanczos_solve(const ed_basis* basis, const ed_params* params, const ed_opts* opts,
+                           const void* f1, void* stream, double* E0, int32_t* steps,
+                           double* alpha, double* beta);
+
+/* ed_last_error - message of the last failing call on this thread ("" if none). */
+const char* ed_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ED_H_ */

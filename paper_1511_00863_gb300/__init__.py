@@ -1,0 +1,218 @@
+"""Python binding of libed, the GB300 CUDA library for exact diagonalization of the
+tight-binding / Hubbard model by the Lanczos method (Siro & Harju, arXiv:1511.00863).
+
+Argument marshalling only: every function forwards to the C entry point of the same name
+declared in include/ed.h. Vectors are torch CUDA tensors (device memory owned by the
+caller); the CUDA stream defaults to torch's current stream. There is no fallback: if the
+compiled library is missing, importing this package raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_double, c_int, c_int32, c_int64, c_uint32, c_uint64, c_void_p
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libed.so")
+
+ED_OK, ED_BREAKDOWN = 0, 1
+ED_ERR_ARG, ED_ERR_OOM, ED_ERR_CUDA, ED_ERR_TIMEOUT, ED_ERR_NOT_CONVERGED = -1, -2, -3, -4, -5
+ED_F64, ED_F32 = 0, 1
+ED_MAX_STEPS = 1000
+
+
+class EdError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"libed status {status}: {message}")
+        self.status = status
+
+
+class ed_lattice(ctypes.Structure):
+    _fields_ = [("n_sites", c_int32), ("n_bonds", c_int32), ("bonds", POINTER(c_int32)),
+                ("t_bond", POINTER(c_double))]
+
+
+class ed_params(ctypes.Structure):
+    _fields_ = [("t", c_double), ("U", c_double)]
+
+
+class ed_opts(ctypes.Structure):
+    _fields_ = [("max_steps", c_int32), ("tol", c_double), ("reorth", c_int32),
+                ("seed", c_uint64), ("dtype", c_int), ("schedule", c_int32)]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libed.so not built ({LIB_PATH}); run __graft_entry__.build() or "
+                      "python -m paper_1511_00863_gb300.build")
+_lib = ctypes.CDLL(LIB_PATH)
+
+_SIGS = {
+    "ed_build_basis": (c_int, [POINTER(ed_lattice), c_int32, c_int32, c_void_p, POINTER(c_void_p)]),
+    "ed_basis_dims": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64), POINTER(c_int64)]),
+    "ed_basis_tables": (c_int, [c_void_p, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p),
+                                POINTER(c_void_p), POINTER(c_int32), POINTER(c_int32)]),
+    "ed_basis_destroy": (None, [c_void_p]),
+    "ed_hv": (c_int, [c_void_p, POINTER(ed_params), c_int, c_void_p, c_void_p, c_void_p]),
+    "ed_start_vector": (c_int, [c_int64, c_uint64, c_int, c_void_p, c_void_p]),
+    "ed_lanczos_init": (c_int, [c_void_p, POINTER(ed_opts), c_void_p, c_void_p, POINTER(c_void_p)]),
+    "ed_lanczos_step": (c_int, [c_void_p, POINTER(ed_params), POINTER(c_double), POINTER(c_double)]),
+    "ed_lanczos_run": (c_int, [c_void_p, POINTER(ed_params), c_int32, POINTER(ctypes.c_float)]),
+    "ed_lanczos_energy": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int32)]),
+    "ed_lanczos_destroy": (None, [c_void_p]),
+    "ed_lanczos_solve": (c_int, [c_void_p, POINTER(ed_params), POINTER(ed_opts), c_void_p, c_void_p,
+                                 POINTER(c_double), POINTER(c_int32), POINTER(c_double),
+                                 POINTER(c_double)]),
+    "ed_last_error": (ctypes.c_char_p, []),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+def _check(status: int) -> int:
+    if status < 0:
+        raise EdError(status, _lib.ed_last_error().decode(errors="replace"))
+    return status
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return c_void_p(stream)
+    return c_void_p(stream.cuda_stream)
+
+
+def _ptr(t, dtype_code=None, numel=None):
+    """Device pointer of a contiguous CUDA tensor (checked), or NULL for None."""
+    if t is None:
+        return c_void_p(None)
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype_code is not None:
+        want = torch.float64 if dtype_code == ED_F64 else torch.float32
+        if t.dtype != want:
+            raise ValueError(f"expected {want}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"expected {numel} elements, got {t.numel()}")
+    return c_void_p(t.data_ptr())
+
+
+def dtype_code(dtype) -> int:
+    if dtype in (ED_F64, "f64", "float64", "fp64"):
+        return ED_F64
+    if dtype in (ED_F32, "f32", "float32", "fp32"):
+        return ED_F32
+    import torch
+    if dtype == torch.float64:
+        return ED_F64
+    if dtype == torch.float32:
+        return ED_F32
+    raise ValueError(f"unknown dtype {dtype!r}")
+
+
+# ------------------------------------------------------------------------ basis
+def ed_build_basis(n_sites: int, bonds, n_up: int, n_dn: int, stream=None) -> c_void_p:
+    b = np.ascontiguousarray(np.asarray(bonds, dtype=np.int32).reshape(-1, 2))
+    lat = ed_lattice(n_sites, b.shape[0], b.ctypes.data_as(POINTER(c_int32)), None)
+    out = c_void_p()
+    _check(_lib.ed_build_basis(byref(lat), n_up, n_dn, _stream(stream), byref(out)))
+    return out
+
+
+def ed_basis_dims(basis) -> tuple[int, int, int]:
+    du, dd, d = c_int64(), c_int64(), c_int64()
+    _check(_lib.ed_basis_dims(basis, byref(du), byref(dd), byref(d)))
+    return du.value, dd.value, d.value
+
+
+def ed_basis_tables(basis) -> dict:
+    ub, db, hu, hd = c_void_p(), c_void_p(), c_void_p(), c_void_p()
+    mu, md = c_int32(), c_int32()
+    _check(_lib.ed_basis_tables(basis, byref(ub), byref(db), byref(hu), byref(hd), byref(mu),
+                                byref(md)))
+    return dict(up_bits=ub.value, dn_bits=db.value, hop_up=hu.value, hop_dn=hd.value,
+                maxhops_up=mu.value, maxhops_dn=md.value)
+
+
+def ed_basis_destroy(basis) -> None:
+    _lib.ed_basis_destroy(basis)
+
+
+# ------------------------------------------------------------------------ H.v
+def ed_hv(basis, t: float, U: float, x, y, stream=None) -> None:
+    code = dtype_code(x.dtype)
+    dim = ed_basis_dims(basis)[2]
+    p = ed_params(t, U)
+    _check(_lib.ed_hv(basis, byref(p), code, _ptr(x, code, dim), _ptr(y, code, dim),
+                      _stream(stream)))
+
+
+def ed_start_vector(dim: int, seed: int, out, stream=None) -> None:
+    code = dtype_code(out.dtype)
+    _check(_lib.ed_start_vector(dim, seed, code, _ptr(out, code, dim), _stream(stream)))
+
+
+# ------------------------------------------------------------------------ Lanczos
+def make_opts(max_steps=200, tol=1e-12, reorth=0, seed=1, dtype=ED_F64, schedule=-1) -> ed_opts:
+    return ed_opts(max_steps, tol, reorth, seed, dtype_code(dtype), schedule)
+
+
+def ed_lanczos_init(basis, opts: ed_opts, f1=None, stream=None) -> c_void_p:
+    dim = ed_basis_dims(basis)[2]
+    out = c_void_p()
+    _check(_lib.ed_lanczos_init(basis, byref(opts), _ptr(f1, opts.dtype, dim), _stream(stream),
+                                byref(out)))
+    return out
+
+
+def ed_lanczos_step(st, t: float, U: float) -> tuple[int, float, float]:
+    a, b = c_double(), c_double()
+    p = ed_params(t, U)
+    s = _check(_lib.ed_lanczos_step(st, byref(p), byref(a), byref(b)))
+    return s, a.value, b.value
+
+
+def ed_lanczos_run(st, t: float, U: float, nsteps: int, time_hv: bool = False):
+    """Enqueue nsteps iterations; with time_hv, returns the summed fused H.v time (ms)."""
+    p = ed_params(t, U)
+    if time_hv:
+        ms = ctypes.c_float()
+        _check(_lib.ed_lanczos_run(st, byref(p), nsteps, byref(ms)))
+        return ms.value
+    _check(_lib.ed_lanczos_run(st, byref(p), nsteps, None))
+    return None
+
+
+def ed_lanczos_energy(st) -> tuple[float, int]:
+    e, j = c_double(), c_int32()
+    _check(_lib.ed_lanczos_energy(st, byref(e), byref(j)))
+    return e.value, j.value
+
+
+def ed_lanczos_destroy(st) -> None:
+    _lib.ed_lanczos_destroy(st)
+
+
+def ed_lanczos_solve(basis, t: float, U: float, opts: ed_opts, f1=None, stream=None,
+                     raise_not_converged: bool = True) -> dict:
+    dim = ed_basis_dims(basis)[2]
+    p = ed_params(t, U)
+    E0, steps = c_double(), c_int32()
+    alpha = (c_double * opts.max_steps)()
+    beta = (c_double * opts.max_steps)()
+    s = _lib.ed_lanczos_solve(basis, byref(p), byref(opts), _ptr(f1, opts.dtype, dim),
+                              _stream(stream), byref(E0), byref(steps), alpha, beta)
+    if s < 0 and not (s == ED_ERR_NOT_CONVERGED and not raise_not_converged):
+        _check(s)
+    n = steps.value
+    return dict(status=s, E0=E0.value, steps=n, alpha=np.array(alpha[:n]), beta=np.array(beta[:n]))
+
+
+def ed_last_error() -> str:
+    return _lib.ed_last_error().decode(errors="replace")

@@ -1,0 +1,161 @@
+// Internal declarations shared by the libed translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+
+#include "ed.h"
+
+namespace ed {
+
+// Thread-local error message behind ed_last_error().
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define ED_TRY_CUDA(call)                                                              \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      ::ed::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                      __LINE__);                                                       \
+      return e_ == cudaErrorMemoryAllocation ? ED_ERR_OOM : ED_ERR_CUDA;               \
+    }                                                                                  \
+  } while (0)
+
+#define ED_CHECK_ARG(cond, ...)      \
+  do {                               \
+    if (!(cond)) {                   \
+      ::ed::set_error(__VA_ARGS__);  \
+      return ED_ERR_ARG;             \
+    }                                \
+  } while (0)
+
+constexpr int kMaxSites = 32;
+constexpr int kBinomStride = 33;          // C[n * 33 + k], n, k in [0, 32]
+constexpr uint32_t kTargetMask = 0x3FFFFFFFu;  // hop entry: target rank in bits 0..29
+constexpr uint32_t kSignBit = 0x80000000u;     // hop entry: bit 31 = negative fermion sign
+
+// Hop table of one species: entry k of state r at hop[k * dim + r].
+struct SpeciesTables {
+  int64_t dim = 0;
+  int32_t maxhops = 0;
+  uint32_t* bits = nullptr;  // [dim]
+  int32_t* hop = nullptr;    // [maxhops * dim], unused slots = dim
+};
+
+}  // namespace ed
+
+struct ed_basis {
+  int device = 0;
+  int32_t n_sites = 0, n_up = 0, n_dn = 0;
+  int64_t dim = 0;
+  ed::SpeciesTables up, dn;
+  uint32_t* binom = nullptr;  // device copy of C(n, k), n, k <= 32
+};
+
+namespace ed {
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+
+// Device-resident scalars of one Lanczos run (Algorithm 1). Index j is 1-based as in the
+// paper: alpha[j] = a_j, beta[j] = b_j (beta[1] = 0), E0[j] = lambda_min(T_j).
+// Buffer i of the run holds an unnormalised vector B_i with f = scale[i] * B_i.
+struct LzScalars {
+  int j;            // steps completed
+  int status;       // 0 running, 1 breakdown, 2 converged, 3 max_steps reached
+  int check_every;  // compute E0(j) every this many steps (and at the stop step)
+  int max_steps;
+  double tol;
+  double tscale;    // max over i <= j of |a_i| + b_i (breakdown scale)
+  double last_E0;   // most recent computed E0 and its step
+  int last_E0_step;
+  int pad_;
+  double scale[2];
+  double alpha[ED_MAX_STEPS + 2];
+  double beta[ED_MAX_STEPS + 2];
+  double E0[ED_MAX_STEPS + 2];
+};
+
+// Extra arguments of the Lanczos-fused H.v pass:
+//   w = scale[cur] * H B_cur - b_j * scale[prev] * B_prev   (written over B_prev)
+//   partial[block] = sum over the block's elements of w * (scale[cur] * B_cur)
+struct LzHvArgs {
+  const LzScalars* S;
+  int cur;
+  double* partial;
+};
+
+// Launch the H.v kernels: y = H x on rows of stride ld (ld >= dim_dn). T = float or double.
+// With lz != nullptr, y must hold B_prev on entry and receives w (see LzHvArgs).
+template <typename T>
+ed_status launch_hv(const ed_basis* b, double t, double U, const T* x, T* y, int64_t ld,
+                    cudaStream_t s, const LzHvArgs* lz = nullptr, int* grid_out = nullptr);
+
+// Set the kernel attributes launch_hv relies on (dynamic shared memory size); call before
+// the first launch on a device and outside stream capture.
+ed_status hv_prepare(const ed_basis* b, ed_dtype dtype);
+
+// Upper bound on the number of CTAs launch_hv uses (size of the partial-sum buffer).
+int64_t hv_max_grid(const ed_basis* b);
+
+// ---------------------------------------------------------------- reductions
+// Dot-product accumulator: FP64 for FP64 data; for FP32 data an exact product (FMA
+// error term) fed into a compensated FP32 pair, converted to FP64 once per thread.
+template <typename T> struct DotAcc;
+template <> struct DotAcc<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { v = fma(a, b, v); }
+  __device__ __forceinline__ double get() const { return v; }
+};
+template <> struct DotAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);
+    const float s = hi + p;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (p - bb);
+    hi = s;
+    lo += err + e;
+  }
+  __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
+};
+
+// Deterministic block sum (fixed shuffle tree, then warp 0 over the warp sums); the
+// result is valid in thread 0. `sm` holds >= 32 doubles. Ends with a __syncthreads.
+__device__ __forceinline__ double block_sum(double v, double* sm) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sm[w] = v;
+  __syncthreads();
+  v = 0.0;
+  if (w == 0) {
+    v = (l < (int)(blockDim.x >> 5)) ? sm[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  __syncthreads();
+  return v;
+}
+
+// Sum of n partials in a fixed order by one block (every thread gets the result).
+__device__ __forceinline__ double block_sum_array(const double* p, int64_t n, double* sm) {
+  double v = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) v += p[i];
+  v = block_sum(v, sm);
+  if (threadIdx.x == 0) sm[32] = v;
+  __syncthreads();
+  v = sm[32];
+  __syncthreads();
+  return v;
+}
+
+}  // namespace ed

@@ -1,0 +1,588 @@
+// Lanczos iteration (Sec. 2.2, Algorithm 1) on the device, the random start vector, and
+// the lowest eigenvalue of the tridiagonal T by Sturm-sequence bisection in FP64.
+//
+// One step j is three launches on the run's stream:
+//   1. fused H.v:  w = H f_j - b_j f_{j-1}, written over the f_{j-1} buffer, with per-CTA
+//      partial sums of w . f_j  (ed_hv.cu, LzHvArgs);
+//   2. update:     a_j = sum of the partials (every CTA sums them in the same order),
+//      q = w - a_j f_j in place, per-CTA partial sums of q . q;
+//   3. finish (one CTA): b_{j+1} = sqrt(sum), breakdown test, f_{j+1} = q / b_{j+1} kept
+//      implicit as a buffer scale, E0(j) = lambda_min(T_j), convergence test.
+// Each buffer holds an unnormalised vector B with f = scale * B, so no pass rescales it.
+// Once the run stops (breakdown, convergence, max_steps) every later kernel returns at
+// entry; ed_lanczos_solve replays a captured two-step CUDA graph and reads the status
+// between batches of replays.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "ed_internal.cuh"
+
+namespace ed {
+
+constexpr int kRedThreads = 256;
+constexpr double kBreakdownRel = 1e-13;
+
+// ------------------------------------------------------------------ start vector
+// SplitMix64 (Steele, Lea & Flood 2014): the (i+1)-th output of the generator seeded with
+// `seed`; element i of the start vector is 2 * (top 53 bits * 2^-53) - 1.
+__device__ __forceinline__ double start_element(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  return 2.0 * ((double)(z >> 11) * 0x1.0p-53) - 1.0;
+}
+
+// Partial sums of x_i^2 over the raw start vector.
+__global__ void __launch_bounds__(kRedThreads)
+start_norm_kernel(uint64_t seed, int64_t n, double* __restrict__ partial) {
+  __shared__ double red[33];
+  double v = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double e = start_element(seed, (uint64_t)i);
+    v = fma(e, e, v);
+  }
+  v = block_sum(v, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = v;
+}
+
+// out[(i / cols) * ld + i % cols] = raw_i / ||raw|| rounded to T.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+start_write_kernel(uint64_t seed, int64_t n, int64_t cols, int64_t ld,
+                   const double* __restrict__ partial, int nparts, T* __restrict__ out) {
+  __shared__ double red[33];
+  const double inv = 1.0 / sqrt(block_sum_array(partial, nparts, red));
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / cols, c = i - r * cols;
+    out[r * ld + c] = (T)(start_element(seed, (uint64_t)i) * inv);
+  }
+}
+
+// Copy a dense caller vector into the padded layout and accumulate its squared norm.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+copy_in_kernel(const T* __restrict__ src, int64_t n, int64_t cols, int64_t ld,
+               T* __restrict__ dst, double* __restrict__ partial) {
+  __shared__ double red[33];
+  DotAcc<T> acc;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / cols, c = i - r * cols;
+    const T v = src[i];
+    dst[r * ld + c] = v;
+    acc.add(v, v);
+  }
+  const double v = block_sum(acc.get(), red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = v;
+}
+
+__global__ void init_scalars_kernel(LzScalars* S, const double* __restrict__ partial,
+                                    int nparts, int use_partial) {
+  __shared__ double red[33];
+  double nrm2 = 1.0;
+  if (use_partial) nrm2 = block_sum_array(partial, nparts, red);
+  if (threadIdx.x == 0) S->scale[0] = 1.0 / sqrt(nrm2);
+}
+
+// ------------------------------------------------------------------ update
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+lz_update_kernel(LzScalars* S, int cur, const T* __restrict__ bcur, T* __restrict__ bprev,
+                 int64_t n, const double* __restrict__ pa, int na, double* __restrict__ pb) {
+  __shared__ double red[33];
+  if (S->status != 0) return;
+  const double a = block_sum_array(pa, na, red);
+  const int j = S->j + 1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) S->alpha[j] = a;
+  const T coef = (T)(a * S->scale[cur]);
+  DotAcc<T> acc;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const T q = bprev[i] - coef * bcur[i];
+    bprev[i] = q;
+    acc.add(q, q);
+  }
+  const double v = block_sum(acc.get(), red);
+  if (threadIdx.x == 0) pb[blockIdx.x] = v;
+}
+
+// ------------------------------------------------------------------ Sturm bisection
+// Number of eigenvalues of T_m below x (a: 1-based diagonal a[1..m], b: b[2..m]):
+// negative pivots of the LDL^T factorisation of T - x I.
+__device__ int sturm_count(const double* a, const double* b, int m, double x) {
+  int cnt = 0;
+  double d = 1.0;
+  for (int i = 1; i <= m; ++i) {
+    const double off = (i > 1) ? b[i] * b[i] / d : 0.0;
+    d = (a[i] - x) - off;
+    if (d == 0.0) d = -2.2250738585072014e-308;
+    cnt += d < 0.0;
+  }
+  return cnt;
+}
+
+// lambda_min(T_m) by block-parallel multisection: each round evaluates the Sturm count at
+// blockDim.x interior points of the bracket and keeps the sub-interval holding the first
+// eigenvalue, until the bracket stops shrinking in FP64. Returns the upper end (valid in
+// every thread).
+__device__ double sturm_lowest(const double* a, const double* b, int m) {
+  __shared__ double lo_s, hi_s;
+  __shared__ int first_s;
+  if (threadIdx.x == 0) {
+    double lo = INFINITY, hi = -INFINITY;
+    for (int i = 1; i <= m; ++i) {
+      const double r = (i > 1 ? fabs(b[i]) : 0.0) + (i < m ? fabs(b[i + 1]) : 0.0);
+      lo = fmin(lo, a[i] - r);
+      hi = fmax(hi, a[i] + r);
+    }
+    const double span = fmax(fmax(fabs(lo), fabs(hi)), 1e-300);
+    lo_s = lo - 1e-15 * span - 1e-300;
+    hi_s = hi + 1e-15 * span + 1e-300;
+  }
+  __syncthreads();
+  const int P = blockDim.x;
+  for (int round = 0; round < 64; ++round) {
+    const double lo = lo_s, hi = hi_s;
+    const double w = (hi - lo) / (double)(P + 1);
+    if (threadIdx.x == 0) first_s = P;
+    __syncthreads();
+    const double x = lo + w * (double)(threadIdx.x + 1);
+    const bool valid = x > lo && x < hi;
+    if (valid && sturm_count(a, b, m, x) >= 1) atomicMin(&first_s, (int)threadIdx.x);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int k = first_s;
+      const double nhi = (k < P) ? lo + w * (double)(k + 1) : hi;
+      const double nlo = (k > 0) ? lo + w * (double)k : lo;
+      lo_s = fmax(nlo, lo);
+      hi_s = fmin(nhi, hi);
+    }
+    __syncthreads();
+    if (!(lo_s < hi_s) || (lo_s == lo && hi_s == hi)) break;
+    const double mid = 0.5 * (lo_s + hi_s);
+    if (!(mid > lo_s && mid < hi_s)) break;
+  }
+  return hi_s;
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+lz_finish_kernel(LzScalars* S, int cur, const double* __restrict__ pb, int nb) {
+  __shared__ double red[33];
+  __shared__ int stop_s;
+  if (S->status != 0) return;
+  const int j = S->j + 1;
+  const double b2 = block_sum_array(pb, nb, red);
+  if (threadIdx.x == 0) {
+    const double beta = sqrt(b2);
+    const double a = S->alpha[j];
+    const double ts = fmax(S->tscale, fabs(a) + S->beta[j]);
+    S->tscale = ts;
+    S->beta[j + 1] = beta;
+    int st = 0;
+    if (!(beta > kBreakdownRel * fmax(1.0, ts))) st = 1;
+    else S->scale[1 - cur] = 1.0 / beta;
+    S->j = j;
+    stop_s = st;
+    S->status = 0;
+  }
+  __syncthreads();
+  int st = stop_s;
+  const bool check = st != 0 || j >= S->max_steps || (j % S->check_every) == 0;
+  if (check) {
+    const double E = sturm_lowest(S->alpha, S->beta, j);
+    if (threadIdx.x == 0) {
+      S->E0[j] = E;
+      if (st == 0 && S->tol > 0.0 && S->last_E0_step > 0 &&
+          fabs(E - S->last_E0) <= S->tol * fmax(fabs(E), 1.0))
+        st = 2;
+      S->last_E0 = E;
+      S->last_E0_step = j;
+    }
+  }
+  if (threadIdx.x == 0) {
+    if (st == 0 && j >= S->max_steps) st = 3;
+    S->status = st;
+  }
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+lz_energy_kernel(const LzScalars* S, double* out) {
+  const int j = S->j;
+  if (j < 1) {
+    if (threadIdx.x == 0) *out = NAN;
+    return;
+  }
+  const double E = sturm_lowest(S->alpha, S->beta, j);
+  if (threadIdx.x == 0) *out = E;
+}
+
+static int red_grid(int64_t n) {
+  const int64_t want = (n + kRedThreads - 1) / kRedThreads;
+  const int64_t cap = (int64_t)sm_count() * 4;
+  return (int)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+}  // namespace ed
+
+using namespace ed;
+
+struct ed_lanczos {
+  const ed_basis* basis = nullptr;
+  ed_opts opts{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int64_t ld = 0;      // padded row stride (elements)
+  int64_t n = 0;       // dim_up * ld
+  size_t esize = 8;
+  void* B[2] = {nullptr, nullptr};
+  int cur = 0;         // buffer holding f_j
+  LzScalars* S = nullptr;
+  double* pa = nullptr;  // partials of the H.v pass
+  double* pb = nullptr;  // partials of the update pass
+  double* tmp = nullptr;
+  int64_t npa = 0, npb = 0;
+  int hv_grid = 0;
+  bool stopped = false;
+  cudaGraphExec_t graph = nullptr;
+};
+
+static ed_status lz_launch_step(ed_lanczos* st, const ed_params* p, cudaStream_t s,
+                                cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
+  const ed_basis* b = st->basis;
+  const int c = st->cur;
+  LzHvArgs lz{st->S, c, st->pa};
+  int grid = 0;
+  ed_status r;
+  if (ev0) ED_TRY_CUDA(cudaEventRecord(ev0, s));
+  if (st->opts.dtype == ED_F64)
+    r = launch_hv<double>(b, p->t, p->U, (const double*)st->B[c], (double*)st->B[1 - c], st->ld,
+                          s, &lz, &grid);
+  else
+    r = launch_hv<float>(b, p->t, p->U, (const float*)st->B[c], (float*)st->B[1 - c], st->ld,
+                         s, &lz, &grid);
+  if (r != ED_OK) return r;
+  if (ev1) ED_TRY_CUDA(cudaEventRecord(ev1, s));
+  const int ug = red_grid(st->n);
+  if (st->opts.dtype == ED_F64)
+    lz_update_kernel<double><<<ug, kRedThreads, 0, s>>>(
+        st->S, c, (const double*)st->B[c], (double*)st->B[1 - c], st->n, st->pa, grid, st->pb);
+  else
+    lz_update_kernel<float><<<ug, kRedThreads, 0, s>>>(
+        st->S, c, (const float*)st->B[c], (float*)st->B[1 - c], st->n, st->pa, grid, st->pb);
+  ED_TRY_CUDA(cudaGetLastError());
+  lz_finish_kernel<<<1, kRedThreads, 0, s>>>(st->S, c, st->pb, ug);
+  ED_TRY_CUDA(cudaGetLastError());
+  st->cur = 1 - c;
+  return ED_OK;
+}
+
+static ed_status check_opts(const ed_opts* o) {
+  ED_CHECK_ARG(o != nullptr, "opts is NULL");
+  ED_CHECK_ARG(o->max_steps >= 1 && o->max_steps <= ED_MAX_STEPS,
+               "max_steps = %d outside [1, %d]", o->max_steps, ED_MAX_STEPS);
+  ED_CHECK_ARG(o->dtype == ED_F64 || o->dtype == ED_F32, "unknown dtype %d", (int)o->dtype);
+  ED_CHECK_ARG(o->reorth == 0, "reorth = %d is not supported (0 = none)", o->reorth);
+  ED_CHECK_ARG(std::isfinite(o->tol), "tol is not finite");
+  return ED_OK;
+}
+
+extern "C" ed_status ed_start_vector(int64_t dim, uint64_t seed, ed_dtype dtype, void* out,
+                                     void* stream) {
+  clear_error();
+  ED_CHECK_ARG(dim >= 1, "ed_start_vector: dim < 1");
+  ED_CHECK_ARG(out != nullptr && aligned16(out), "ed_start_vector: out NULL or not 16-byte aligned");
+  ED_CHECK_ARG(dtype == ED_F64 || dtype == ED_F32, "ed_start_vector: unknown dtype");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int g = red_grid(dim);
+  double* part = nullptr;
+  ED_TRY_CUDA(cudaMallocAsync((void**)&part, g * sizeof(double), s));
+  start_norm_kernel<<<g, kRedThreads, 0, s>>>(seed, dim, part);
+  if (dtype == ED_F64)
+    start_write_kernel<double><<<g, kRedThreads, 0, s>>>(seed, dim, dim, dim, part, g, (double*)out);
+  else
+    start_write_kernel<float><<<g, kRedThreads, 0, s>>>(seed, dim, dim, dim, part, g, (float*)out);
+  cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(part, s);
+  if (e != cudaSuccess) {
+    set_error("ed_start_vector: %s", cudaGetErrorString(e));
+    return ED_ERR_CUDA;
+  }
+  return ED_OK;
+}
+
+extern "C" void ed_lanczos_destroy(ed_lanczos* st) {
+  if (!st) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != st->device) cudaSetDevice(st->device);
+  if (st->stream) cudaStreamSynchronize(st->stream);
+  if (st->graph) cudaGraphExecDestroy(st->graph);
+  for (int i = 0; i < 2; ++i)
+    if (st->B[i]) cudaFree(st->B[i]);
+  if (st->S) cudaFree(st->S);
+  if (st->pa) cudaFree(st->pa);
+  if (st->pb) cudaFree(st->pb);
+  if (st->tmp) cudaFree(st->tmp);
+  if (prev != st->device) cudaSetDevice(prev);
+  delete st;
+}
+
+// check_every: compute E0(j) in the finish kernel every this many steps; step_mode: the
+// caller drives the loop, so only breakdown and max_steps stop the run (no tol test).
+static ed_status lz_init(const ed_basis* b, const ed_opts* o, const void* f1, cudaStream_t s,
+                         int check_every, bool step_mode, ed_lanczos** out) {
+  *out = nullptr;
+  ED_CHECK_ARG(b != nullptr, "basis is NULL");
+  ed_status r = check_opts(o);
+  if (r != ED_OK) return r;
+  ED_CHECK_ARG(f1 == nullptr || aligned16(f1), "f1 must be 16-byte aligned");
+  ed_lanczos* st = new ed_lanczos();
+  st->basis = b;
+  st->opts = *o;
+  cudaGetDevice(&st->device);
+  st->stream = s;
+  st->esize = o->dtype == ED_F64 ? 8 : 4;
+  st->ld = (b->dn.dim + 31) / 32 * 32;
+  st->n = b->up.dim * st->ld;
+  st->npa = hv_max_grid(b);
+  st->npb = (int64_t)sm_count() * 4;
+  auto fail = [&](ed_status e) {
+    ed_lanczos_destroy(st);
+    return e;
+  };
+  for (int i = 0; i < 2; ++i) {
+    if (cudaMalloc(&st->B[i], st->n * st->esize) != cudaSuccess) {
+      set_error("Lanczos work vectors: out of device memory (%lld bytes each)",
+                (long long)(st->n * st->esize));
+      return fail(ED_ERR_OOM);
+    }
+  }
+  if (cudaMalloc((void**)&st->S, sizeof(LzScalars)) != cudaSuccess ||
+      cudaMalloc((void**)&st->pa, st->npa * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&st->pb, st->npb * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&st->tmp, 64) != cudaSuccess) {
+    set_error("Lanczos scalars: out of device memory");
+    return fail(ED_ERR_OOM);
+  }
+  for (int i = 0; i < 2; ++i)
+    if (cudaMemsetAsync(st->B[i], 0, st->n * st->esize, s) != cudaSuccess) return fail(ED_ERR_CUDA);
+  LzScalars h;
+  memset(&h, 0, sizeof(h));
+  h.check_every = check_every < 1 ? 1 : check_every;
+  h.max_steps = o->max_steps;
+  h.tol = step_mode ? 0.0 : o->tol;
+  h.scale[0] = 1.0;
+  h.scale[1] = 0.0;
+  for (int i = 0; i < ED_MAX_STEPS + 2; ++i) h.E0[i] = NAN;
+  if (cudaMemcpyAsync(st->S, &h, sizeof(h), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    set_error("Lanczos scalars: copy failed");
+    return fail(ED_ERR_CUDA);
+  }
+  const int64_t dim = b->dim, cols = b->dn.dim;
+  const int g = red_grid(dim);
+  if ((int64_t)g > st->npb) return fail(ED_ERR_ARG);
+  if (f1 == nullptr) {
+    start_norm_kernel<<<g, kRedThreads, 0, s>>>(o->seed, dim, st->pb);
+    if (o->dtype == ED_F64)
+      start_write_kernel<double><<<g, kRedThreads, 0, s>>>(o->seed, dim, cols, st->ld, st->pb, g,
+                                                           (double*)st->B[0]);
+    else
+      start_write_kernel<float><<<g, kRedThreads, 0, s>>>(o->seed, dim, cols, st->ld, st->pb, g,
+                                                          (float*)st->B[0]);
+    init_scalars_kernel<<<1, 32, 0, s>>>(st->S, st->pb, g, 0);
+  } else {
+    if (o->dtype == ED_F64)
+      copy_in_kernel<double><<<g, kRedThreads, 0, s>>>((const double*)f1, dim, cols, st->ld,
+                                                       (double*)st->B[0], st->pb);
+    else
+      copy_in_kernel<float><<<g, kRedThreads, 0, s>>>((const float*)f1, dim, cols, st->ld,
+                                                      (float*)st->B[0], st->pb);
+    init_scalars_kernel<<<1, kRedThreads, 0, s>>>(st->S, st->pb, g, 1);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("Lanczos init: %s", cudaGetErrorString(e));
+    return fail(ED_ERR_CUDA);
+  }
+  st->cur = 0;
+  *out = st;
+  return ED_OK;
+}
+
+extern "C" ed_status ed_lanczos_init(const ed_basis* b, const ed_opts* o, const void* f1,
+                                     void* stream, ed_lanczos** out) {
+  clear_error();
+  ED_CHECK_ARG(out != nullptr, "ed_lanczos_init: out is NULL");
+  ed_status r = lz_init(b, o, f1, (cudaStream_t)stream, ED_MAX_STEPS + 1, true, out);
+  if (r == ED_OK) r = hv_prepare(b, o->dtype);
+  return r;
+}
+
+extern "C" ed_status ed_lanczos_step(ed_lanczos* st, const ed_params* p, double* alpha_j,
+                                     double* beta_j1) {
+  clear_error();
+  ED_CHECK_ARG(st != nullptr && p != nullptr, "ed_lanczos_step: state or params is NULL");
+  ED_CHECK_ARG(!st->stopped, "ed_lanczos_step: the run has stopped (breakdown or max_steps)");
+  ed_status r = lz_launch_step(st, p, st->stream);
+  if (r != ED_OK) return r;
+  int hdr[2];
+  ED_TRY_CUDA(cudaMemcpyAsync(hdr, st->S, 2 * sizeof(int), cudaMemcpyDeviceToHost, st->stream));
+  ED_TRY_CUDA(cudaStreamSynchronize(st->stream));
+  const int j = hdr[0], status = hdr[1];
+  double ab[2] = {0, 0};
+  ED_TRY_CUDA(cudaMemcpy(&ab[0], &st->S->alpha[j], sizeof(double), cudaMemcpyDeviceToHost));
+  ED_TRY_CUDA(cudaMemcpy(&ab[1], &st->S->beta[j + 1], sizeof(double), cudaMemcpyDeviceToHost));
+  if (alpha_j) *alpha_j = ab[0];
+  if (beta_j1) *beta_j1 = ab[1];
+  if (status != 0) st->stopped = true;
+  return status == 1 ? ED_BREAKDOWN : ED_OK;
+}
+
+extern "C" ed_status ed_lanczos_run(ed_lanczos* st, const ed_params* p, int32_t nsteps,
+                                    float* hv_ms) {
+  clear_error();
+  ED_CHECK_ARG(st != nullptr && p != nullptr, "ed_lanczos_run: state or params is NULL");
+  ED_CHECK_ARG(nsteps >= 0 && nsteps <= ED_MAX_STEPS, "ed_lanczos_run: nsteps out of range");
+  if (!hv_ms) {
+    for (int i = 0; i < nsteps; ++i) {
+      ed_status r = lz_launch_step(st, p, st->stream);
+      if (r != ED_OK) return r;
+    }
+    return ED_OK;
+  }
+  std::vector<cudaEvent_t> ev(2 * (size_t)nsteps, nullptr);
+  ed_status r = ED_OK;
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      set_error("ed_lanczos_run: event creation failed");
+      r = ED_ERR_CUDA;
+      break;
+    }
+  for (int i = 0; r == ED_OK && i < nsteps; ++i) r = lz_launch_step(st, p, st->stream, ev[2 * i], ev[2 * i + 1]);
+  float total = 0.f;
+  if (r == ED_OK && cudaStreamSynchronize(st->stream) != cudaSuccess) {
+    set_error("ed_lanczos_run: %s", cudaGetErrorString(cudaGetLastError()));
+    r = ED_ERR_CUDA;
+  }
+  for (int i = 0; r == ED_OK && i < nsteps; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]) != cudaSuccess) {
+      set_error("ed_lanczos_run: event timing failed");
+      r = ED_ERR_CUDA;
+    }
+    total += ms;
+  }
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  if (r == ED_OK) *hv_ms = total;
+  return r;
+}
+
+extern "C" ed_status ed_lanczos_energy(ed_lanczos* st, double* E0, int32_t* steps) {
+  clear_error();
+  ED_CHECK_ARG(st != nullptr, "ed_lanczos_energy: state is NULL");
+  lz_energy_kernel<<<1, kRedThreads, 0, st->stream>>>(st->S, st->tmp);
+  ED_TRY_CUDA(cudaGetLastError());
+  double e = 0;
+  int j = 0;
+  ED_TRY_CUDA(cudaMemcpyAsync(&e, st->tmp, sizeof(double), cudaMemcpyDeviceToHost, st->stream));
+  ED_TRY_CUDA(cudaMemcpyAsync(&j, &st->S->j, sizeof(int), cudaMemcpyDeviceToHost, st->stream));
+  ED_TRY_CUDA(cudaStreamSynchronize(st->stream));
+  if (E0) *E0 = e;
+  if (steps) *steps = j;
+  return ED_OK;
+}
+
+extern "C" ed_status ed_lanczos_solve(const ed_basis* b, const ed_params* p, const ed_opts* o,
+                                      const void* f1, void* stream, double* E0, int32_t* steps,
+                                      double* alpha, double* beta) {
+  clear_error();
+  ED_CHECK_ARG(p != nullptr, "ed_lanczos_solve: params is NULL");
+  ED_CHECK_ARG(E0 != nullptr, "ed_lanczos_solve: E0 is NULL");
+  cudaStream_t user = (cudaStream_t)stream;
+  cudaStream_t s = nullptr;
+  ED_TRY_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  cudaEvent_t ev = nullptr;
+  ed_lanczos* st = nullptr;
+  ed_status r = ED_OK;
+  auto cleanup = [&](ed_status e) {
+    if (st) ed_lanczos_destroy(st);
+    if (ev) cudaEventDestroy(ev);
+    cudaStreamDestroy(s);
+    return e;
+  };
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventRecord(ev, user) != cudaSuccess || cudaStreamWaitEvent(s, ev, 0) != cudaSuccess) {
+    set_error("ed_lanczos_solve: stream ordering failed");
+    return cleanup(ED_ERR_CUDA);
+  }
+  if ((r = lz_init(b, o, f1, s, 1, false, &st)) != ED_OK) return cleanup(r);
+  if ((r = hv_prepare(b, o->dtype)) != ED_OK) return cleanup(r);
+  // capture two steps (the buffer roles alternate) and replay
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    set_error("ed_lanczos_solve: stream capture failed");
+    return cleanup(ED_ERR_CUDA);
+  }
+  ed_status r1 = lz_launch_step(st, p, s);
+  ed_status r2 = r1 == ED_OK ? lz_launch_step(st, p, s) : r1;
+  cudaError_t ce = cudaStreamEndCapture(s, &g);
+  if (r2 != ED_OK || ce != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    if (r2 == ED_OK) set_error("ed_lanczos_solve: capture failed: %s", cudaGetErrorString(ce));
+    return cleanup(r2 != ED_OK ? r2 : ED_ERR_CUDA);
+  }
+  ce = cudaGraphInstantiate(&st->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ce != cudaSuccess) {
+    set_error("ed_lanczos_solve: graph instantiate failed: %s", cudaGetErrorString(ce));
+    return cleanup(ED_ERR_CUDA);
+  }
+  int hdr[2] = {0, 0};
+  int launched = 0;
+  while (true) {
+    const int remaining = o->max_steps - launched;
+    int batch = (remaining + 1) / 2;
+    if (batch > 8) batch = 8;
+    if (batch < 1) batch = 1;
+    for (int i = 0; i < batch; ++i) {
+      if (cudaGraphLaunch(st->graph, s) != cudaSuccess) {
+        set_error("ed_lanczos_solve: graph launch failed");
+        return cleanup(ED_ERR_CUDA);
+      }
+    }
+    launched += 2 * batch;
+    if (cudaMemcpyAsync(hdr, st->S, 2 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      set_error("ed_lanczos_solve: %s", cudaGetErrorString(cudaGetLastError()));
+      return cleanup(ED_ERR_CUDA);
+    }
+    if (hdr[1] != 0 || launched >= o->max_steps) break;
+  }
+  std::vector<double> h_alpha(ED_MAX_STEPS + 2), h_beta(ED_MAX_STEPS + 2), h_E(ED_MAX_STEPS + 2);
+  if (cudaMemcpy(h_alpha.data(), st->S->alpha, h_alpha.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(h_beta.data(), st->S->beta, h_beta.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(h_E.data(), st->S->E0, h_E.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    set_error("ed_lanczos_solve: result copy failed");
+    return cleanup(ED_ERR_CUDA);
+  }
+  const int j = hdr[0];
+  *E0 = j >= 1 ? h_E[j] : NAN;
+  if (steps) *steps = j;
+  for (int i = 1; i <= j; ++i) {
+    if (alpha) alpha[i - 1] = h_alpha[i];
+    if (beta) beta[i - 1] = h_beta[i + 1];
+  }
+  const int status = hdr[1];
+  cleanup(ED_OK);
+  if (status == 1) return ED_BREAKDOWN;
+  if (status == 3 && o->tol > 0.0) {
+    set_error("ed_lanczos_solve: not converged after %d steps", j);
+    return ED_ERR_NOT_CONVERGED;
+  }
+  return ED_OK;
+}

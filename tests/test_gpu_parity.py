@@ -1,0 +1,301 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on the same seeded
+inputs. Integer work (basis, hop targets, signs) must match bit for bit; floating point
+within the stated error bounds."""
+import math
+
+import numpy as np
+import pytest
+
+import ed_inputs
+from oracle import basis as obasis
+from oracle import dense, hamiltonian, lanczos as olz
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EPS64 = 2.0 ** -53
+EPS32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def ed():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1511_00863_gb300 as m
+    return m
+
+
+class _DevView:
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+def dev_to_numpy(ptr, n, typestr):
+    return torch.as_tensor(_DevView(ptr, n, typestr), device="cuda").cpu().numpy()
+
+
+def _oracle_tables(L, N, bonds):
+    states, lists = hamiltonian.species_hop_table(L, N, bonds)
+    return states, lists
+
+
+TABLE_CASES = [
+    ("ring6_3_2", 6, ed_inputs.ring_bonds(6), 3, 2),
+    ("rect2x4_2_3", 8, ed_inputs.torus_bonds(2, 4), 2, 3),
+    ("ring12_3_3", 12, ed_inputs.ring_bonds(12), 3, 3),
+    ("torus4x4_5_5", 16, ed_inputs.torus_bonds(4, 4), 5, 5),
+    ("ring16_8_7", 16, ed_inputs.ring_bonds(16), 8, 7),
+    ("empty_full", 5, ed_inputs.ring_bonds(5), 0, 5),
+    ("single_site", 1, np.zeros((0, 2), np.int32), 1, 0),
+    ("doubled_pair", 2, ed_inputs.ring_bonds(2), 1, 1),
+    ("random_bonds", 9, np.array([[0, 5], [3, 8], [1, 2], [7, 0], [6, 4], [2, 8], [5, 1]]), 4, 3),
+]
+
+
+@pytest.mark.parametrize("name,L,bonds,nu,nd", TABLE_CASES, ids=[c[0] for c in TABLE_CASES])
+def test_basis_tables_bit_exact(ed, name, L, bonds, nu, nd):
+    b = ed.ed_build_basis(L, bonds, nu, nd)
+    try:
+        du, dd, d = ed.ed_basis_dims(b)
+        assert (du, dd, d) == (math.comb(L, nu), math.comb(L, nd), math.comb(L, nu) * math.comb(L, nd))
+        tb = ed.ed_basis_tables(b)
+        for N, dim, bits_ptr, hop_ptr, mh in ((nu, du, tb["up_bits"], tb["hop_up"], tb["maxhops_up"]),
+                                              (nd, dd, tb["dn_bits"], tb["hop_dn"], tb["maxhops_dn"])):
+            states, lists = _oracle_tables(L, N, bonds)
+            bits = dev_to_numpy(bits_ptr, dim, "<u4")
+            assert np.array_equal(bits.astype(np.int64), states)
+            assert mh == max(len(x) for x in lists)
+            if mh == 0:
+                continue
+            hop = dev_to_numpy(hop_ptr, mh * dim, "<u4").reshape(mh, dim)
+            for r in range(dim):
+                for k in range(mh):
+                    e = int(hop[k, r])
+                    if k < len(lists[r]):
+                        tgt, sgn = lists[r][k]
+                        assert (e & 0x3FFFFFFF) == tgt and (e >> 31) == (1 if sgn < 0 else 0), (r, k)
+                        assert (e >> 30) & 1 == 0
+                    else:
+                        assert e == dim, (r, k)
+    finally:
+        ed.ed_basis_destroy(b)
+
+
+HV_CASES = [
+    (5, ed_inputs.ring_bonds(5), 2, 2, 1.0, 3.0),
+    (6, ed_inputs.ring_bonds(6), 3, 2, 0.7, 2.5),
+    (8, ed_inputs.torus_bonds(2, 4), 2, 3, 1.0, 4.0),
+    (12, ed_inputs.ring_bonds(12), 3, 3, 1.0, 4.0),
+    (9, np.array([[0, 5], [3, 8], [1, 2], [7, 0], [6, 4], [2, 8], [5, 1]]), 4, 3, 1.3, -1.5),
+    (8, ed_inputs.ring_bonds(8), 0, 3, 1.0, 2.0),
+    (4, ed_inputs.ring_bonds(4), 4, 4, 1.0, 2.0),
+]
+
+
+def _hv_bound(case, x, rows, eps, extra=4.0):
+    L, bonds, nu, nd, t, U = case
+    absy = hamiltonian.hv_abs_rows(L, bonds, nu, nd, t, U, x, rows)
+    nh = 2 * len(bonds) + 2
+    return extra * nh * eps * absy + 1e-300
+
+
+@pytest.mark.parametrize("case", HV_CASES)
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_hv_small_elementwise(ed, case, dtype):
+    L, bonds, nu, nd, t, U = case
+    b = ed.ed_build_basis(L, bonds, nu, nd)
+    try:
+        dim = ed.ed_basis_dims(b)[2]
+        x = ed_inputs.uniform_pm1(21, dim)
+        tdt = torch.float64 if dtype == "f64" else torch.float32
+        xd = torch.tensor(x, device="cuda", dtype=tdt)
+        yd = torch.empty_like(xd)
+        ed.ed_hv(b, t, U, xd, yd)
+        xr = xd.double().cpu().numpy()
+        rows = np.arange(dim)
+        ref = hamiltonian.hv_rows(L, bonds, nu, nd, t, U, xr, rows)
+        eps = EPS64 if dtype == "f64" else EPS32
+        bound = _hv_bound(case, xr, rows, eps)
+        err = np.abs(yd.double().cpu().numpy() - ref)
+        assert np.all(err <= bound), float((err / bound).max())
+    finally:
+        ed.ed_basis_destroy(b)
+
+
+FULL = [("torus4x4_5_5", "f64"), ("ring16_8_8", "f32"), ("ring16_8_8", "f64")]
+
+
+@pytest.mark.parametrize("name,dtype", FULL)
+def test_hv_full_size_sampled(ed, name, dtype):
+    """Full-size workloads: sampled rows (both ends, sub-vector borders, random) against
+    the oracle's matrix-free rows."""
+    w = ed_inputs.workload(name)
+    L, bonds, nu, nd, t, U = w["n_sites"], w["bonds"], w["n_up"], w["n_dn"], w["t"], w["U"]
+    b = ed.ed_build_basis(L, bonds, nu, nd)
+    try:
+        du, dd, dim = ed.ed_basis_dims(b)
+        tdt = torch.float64 if dtype == "f64" else torch.float32
+        x = ed_inputs.uniform_pm1(w["seed"], dim)
+        xd = torch.from_numpy(x).to(device="cuda", dtype=tdt)
+        del x
+        yd = torch.empty_like(xd)
+        ed.ed_hv(b, t, U, xd, yd)
+        torch.cuda.synchronize()
+        rng = np.random.default_rng(5)
+        rows = np.unique(np.concatenate([
+            [0, 1, dim - 1, dim - 2], np.arange(0, dim, dd)[:50], np.arange(dd - 1, dim, dd)[-50:],
+            rng.integers(0, dim, 3000)]))
+        xr = xd.double().cpu().numpy()
+        ref = hamiltonian.hv_rows(L, bonds, nu, nd, t, U, xr, rows)
+        got = yd[torch.from_numpy(rows).cuda()].double().cpu().numpy()
+        bound = _hv_bound((L, bonds, nu, nd, t, U), xr, rows, EPS64 if dtype == "f64" else EPS32)
+        err = np.abs(got - ref)
+        assert np.all(err <= bound), float((err / bound).max())
+    finally:
+        ed.ed_basis_destroy(b)
+
+
+def test_start_vector_matches_generator(ed):
+    n = 100003
+    ref = olz.normalized_start(ed_inputs.start_vector_raw(77, n))
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    ed.ed_start_vector(n, 77, out)
+    got = out.cpu().numpy()
+    assert np.all(np.abs(got - ref) <= 2 * EPS64 * np.abs(ref))
+    o32 = torch.empty(n, dtype=torch.float32, device="cuda")
+    ed.ed_start_vector(n, 77, o32)
+    g32 = o32.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(g32 - ref) <= 1.0000001 * EPS32 * np.abs(ref) * 2)
+
+
+# --------------------------------------------------------------------------- Lanczos
+def _solve(ed, L, bonds, nu, nd, t, U, dtype="f64", seed=1, max_steps=300, tol=1e-13, f1=None):
+    b = ed.ed_build_basis(L, bonds, nu, nd)
+    try:
+        return ed.ed_lanczos_solve(b, t, U, ed.make_opts(max_steps=max_steps, tol=tol, seed=seed,
+                                                         dtype=dtype), f1=f1)
+    finally:
+        ed.ed_basis_destroy(b)
+
+
+@pytest.mark.parametrize("U", [0.0, 4.0])
+def test_lanczos_ring12_fp64(ed, U):
+    L, bonds = 12, ed_inputs.ring_bonds(12)
+    res = _solve(ed, L, bonds, 3, 3, 1.0, U, seed=1, max_steps=200, tol=1e-12)
+    if U == 0.0:
+        ref = -4 * (1 + math.sqrt(3))
+    else:
+        H = hamiltonian.hamiltonian_csr(L, bonds, 3, 3, 1.0, U)
+        f1 = olz.normalized_start(ed_inputs.start_vector_raw(1, H.shape[0]))
+        ref = olz.lanczos(lambda v: H @ v, f1, max_steps=300, tol=1e-14).E0
+    assert res["status"] in (0, 1)
+    assert abs(res["E0"] - ref) <= 1e-10 * abs(ref), (res["E0"], ref)
+
+
+def test_lanczos_ring12_fp32(ed):
+    L, bonds = 12, ed_inputs.ring_bonds(12)
+    H = hamiltonian.hamiltonian_csr(L, bonds, 3, 3, 1.0, 4.0)
+    f1 = olz.normalized_start(ed_inputs.start_vector_raw(1, H.shape[0]))
+    ref = olz.lanczos(lambda v: H @ v, f1, max_steps=300, tol=1e-14).E0
+    res = _solve(ed, L, bonds, 3, 3, 1.0, 4.0, dtype="f32", max_steps=300, tol=1e-9)
+    assert abs(res["E0"] - ref) <= 1e-6 * abs(ref), (res["E0"], ref)
+
+
+RANDOM_CASES = []
+_rng = np.random.default_rng(123)
+for _k in range(8):
+    _L = int(_rng.integers(4, 9))
+    _nb = int(_rng.integers(_L - 1, 2 * _L))
+    _pairs = set()
+    while len(_pairs) < _nb:
+        i, j = (int(v) for v in _rng.integers(0, _L, 2))
+        if i != j:
+            _pairs.add((i, j))
+    _nu = int(_rng.integers(0, _L + 1))
+    _nd = int(_rng.integers(0, _L + 1))
+    RANDOM_CASES.append((_L, np.array(sorted(_pairs)), _nu, _nd, 1.0, float(_rng.uniform(-2, 8))))
+
+
+@pytest.mark.parametrize("case", RANDOM_CASES)
+def test_lanczos_random_lattices_vs_dense(ed, case):
+    L, bonds, nu, nd, t, U = case
+    if math.comb(L, nu) * math.comb(L, nd) > 2000:
+        pytest.skip("dense reference limited to dim <= 2000")
+    ref = dense.spectrum(L, bonds, nu, nd, t, U)[0]
+    res = _solve(ed, L, bonds, nu, nd, t, U, seed=3)
+    assert abs(res["E0"] - ref) <= 1e-10 * max(1.0, abs(ref)), (res, ref)
+
+
+@pytest.mark.parametrize("U", [0.0, 4.0, 8.0])
+def test_two_site_closed_form(ed, U):
+    res = _solve(ed, 2, np.array([[0, 1]]), 1, 1, 1.0, U, seed=4)
+    assert abs(res["E0"] - (U - math.sqrt(U * U + 16)) / 2) <= 1e-12
+
+
+def test_breakdown_on_eigenvector(ed):
+    case = (2, np.array([[0, 1]]), 1, 1, 1.0, 0.0)
+    E0, psi = dense.ground_state(*case)
+    f1 = torch.tensor(psi, device="cuda")
+    res = _solve(ed, *case, f1=f1)
+    assert res["status"] == ed.ED_BREAKDOWN and res["steps"] == 1
+    assert abs(res["E0"] - (-2.0)) <= 1e-14
+
+
+def test_alpha_beta_follow_oracle(ed):
+    """First steps of Algorithm 1 from the same start vector (no reorthogonalisation on
+    either side): a_j and b_{j+1} agree to rounding level."""
+    L, bonds, nu, nd, t, U = 8, ed_inputs.torus_bonds(2, 4), 3, 3, 1.0, 4.0
+    H = hamiltonian.hamiltonian_csr(L, bonds, nu, nd, t, U)
+    f1 = olz.normalized_start(ed_inputs.start_vector_raw(6, H.shape[0]))
+    ref = olz.lanczos(lambda v: H @ v, f1, max_steps=12, reorth=False, fixed_steps=True)
+    res = _solve(ed, L, bonds, nu, nd, t, U, max_steps=12, tol=0.0,
+                 f1=torch.tensor(f1, device="cuda"))
+    assert res["steps"] == 12
+    assert np.allclose(res["alpha"], ref.alpha, rtol=1e-11, atol=1e-11)
+    assert np.allclose(res["beta"], ref.beta, rtol=1e-11, atol=1e-11)
+
+
+def test_step_api_matches_solve(ed):
+    L, bonds, nu, nd, t, U = 6, ed_inputs.ring_bonds(6), 3, 3, 1.0, 2.0
+    b = ed.ed_build_basis(L, bonds, nu, nd)
+    try:
+        opts = ed.make_opts(max_steps=10, tol=0.0, seed=8)
+        full = ed.ed_lanczos_solve(b, t, U, opts)
+        st = ed.ed_lanczos_init(b, opts)
+        try:
+            a, bb = [], []
+            for _ in range(10):
+                s, aj, bj = ed.ed_lanczos_step(st, t, U)
+                a.append(aj)
+                bb.append(bj)
+            E, j = ed.ed_lanczos_energy(st)
+        finally:
+            ed.ed_lanczos_destroy(st)
+        assert j == 10
+        assert np.array_equal(np.array(a), full["alpha"]) and np.array_equal(np.array(bb), full["beta"])
+        assert E == full["E0"]
+    finally:
+        ed.ed_basis_destroy(b)
+
+
+@pytest.mark.parametrize("name,dtype,expect,tol", [
+    ("torus4x4_5_5", "f64", -24.0, 1e-10),
+    ("ring16_8_8", "f32", -20.109357968503396, 1e-6),
+])
+def test_full_size_U0_closed_form(ed, name, dtype, expect, tol):
+    """U = 0 at full size: E0 = sum of the lowest single-particle levels."""
+    w = ed_inputs.workload(name)
+    eps = np.linalg.eigvalsh(_hop_matrix(w["n_sites"], w["bonds"]))
+    assert abs(eps[:w["n_up"]].sum() + eps[:w["n_dn"]].sum() - expect) < 1e-12
+    res = _solve(ed, w["n_sites"], w["bonds"], w["n_up"], w["n_dn"], 1.0, 0.0, dtype=dtype,
+                 seed=w["seed"], max_steps=300, tol=1e-12 if dtype == "f64" else 1e-9)
+    assert abs(res["E0"] - expect) <= tol * abs(expect), res["E0"]
+
+
+def _hop_matrix(L, bonds):
+    h = np.zeros((L, L))
+    for i, j in bonds:
+        h[i, j] -= 1
+        h[j, i] -= 1
+    return h
