@@ -48,7 +48,17 @@ typedef enum {
                                 the last estimate is still returned */
 } ed_status;
 
-typedef enum { ED_F64 = 0, ED_F32 = 1 } ed_dtype;
+/* Vector precision.
+ *  ED_F64         FP64-accurate: FP64 inputs and outputs; the Lanczos vectors are kept as
+ *                 int64 fixed point with one FP64 scale per vector (each element rounded to
+ *                 2^-(vb) of the vector's largest element, vb >= 53 for lattices with fewer
+ *                 than 510 hops per state), hop sums and dot products exact in integers.
+ *                 GB300 executes FP64 arithmetic at about 1/70 of its FP32 rate; this path
+ *                 runs no FP64 instruction per vector element.
+ *  ED_F32         FP32 vectors and FP32 H.v arithmetic; a_j, b_j, dot-product accumulation
+ *                 and the tridiagonal eigensolve in FP64.
+ *  ED_F64_NATIVE  FP64 vectors and FP64 arithmetic throughout (the plain method). */
+typedef enum { ED_F64 = 0, ED_F32 = 1, ED_F64_NATIVE = 2 } ed_dtype;
 
 /* Lattice (Sec. 2.1): n_sites in [1, 32]; bonds is a HOST array [n_bonds][2] of site
  * pairs (i != j, both in range), read during ed_build_basis only. t_bond must be NULL
@@ -72,9 +82,8 @@ typedef struct {
  *             eigenvalue of T_j); tol <= 0 runs exactly max_steps steps.
  *  reorth     0 = none (Algorithm 1 as printed). Other values are reserved.
  *  seed       SplitMix64 seed of the random start vector when f1 == NULL.
- *  dtype      ED_F64: FP64-accurate vectors and arithmetic.
- *             ED_F32: FP32 vectors and H.v; alpha, beta, dot products and the
- *             tridiagonal eigensolve stay in FP64.
+ *  dtype      see ed_dtype; f1 vectors are FP64 for ED_F64 and ED_F64_NATIVE, FP32 for
+ *             ED_F32.
  *  schedule   kernel schedule id, -1 = library default. */
 typedef struct {
   int32_t max_steps;
@@ -114,9 +123,10 @@ ed_status ed_basis_tables(const ed_basis* basis, const uint32_t** up_bits,
 
 void ed_basis_destroy(ed_basis* basis);
 
-/* ed_hv - y = H x (the product on line 4 of Algorithm 1; Sec. 4 Eqs. 5-6 split it into the
- * up part, which mixes sub-vectors, and the down part, which acts inside each). x and y are
- * DEVICE arrays of dim elements of `dtype`, distinct and 16-byte aligned. Asynchronous. */
+/* ed_hv - y = H x (the product of Algorithm 1's first update; Sec. 4 Eqs. 5-6 split it into
+ * the up part, which mixes sub-vectors, and the down part, which acts inside each). x and y
+ * are DEVICE arrays of dim elements (FP64 for ED_F64 and ED_F64_NATIVE, which both compute
+ * in FP64 here; FP32 for ED_F32), distinct and 16-byte aligned. Asynchronous. */
 ed_status ed_hv(const ed_basis* basis, const ed_params* params, ed_dtype dtype, const void* x,
                 void* y, void* stream);
 

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libed.so")
 
 ED_OK, ED_BREAKDOWN = 0, 1
 ED_ERR_ARG, ED_ERR_OOM, ED_ERR_CUDA, ED_ERR_TIMEOUT, ED_ERR_NOT_CONVERGED = -1, -2, -3, -4, -5
-ED_F64, ED_F32 = 0, 1
+ED_F64, ED_F32, ED_F64_NATIVE = 0, 1, 2
 ED_MAX_STEPS = 1000
 
 
@@ -95,7 +95,7 @@ def _ptr(t, dtype_code=None, numel=None):
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
         raise ValueError("expected a contiguous CUDA tensor")
     if dtype_code is not None:
-        want = torch.float64 if dtype_code == ED_F64 else torch.float32
+        want = torch.float32 if dtype_code == ED_F32 else torch.float64
         if t.dtype != want:
             raise ValueError(f"expected {want}, got {t.dtype}")
     if numel is not None and t.numel() != numel:
@@ -104,6 +104,8 @@ def _ptr(t, dtype_code=None, numel=None):
 
 
 def dtype_code(dtype) -> int:
+    if dtype in (ED_F64_NATIVE, "f64n", "f64_native"):
+        return ED_F64_NATIVE
     if dtype in (ED_F64, "f64", "float64", "fp64"):
         return ED_F64
     if dtype in (ED_F32, "f32", "float32", "fp32"):

@@ -236,7 +236,7 @@ static ed_status prepare_t(const ed_basis* b) {
 }
 
 ed_status hv_prepare(const ed_basis* b, ed_dtype dtype) {
-  return dtype == ED_F64 ? prepare_t<double>(b) : prepare_t<float>(b);
+  return dtype == ED_F32 ? prepare_t<float>(b) : prepare_t<double>(b);
 }
 
 int64_t hv_max_grid(const ed_basis* b) {
@@ -259,16 +259,17 @@ extern "C" ed_status ed_hv(const ed_basis* b, const ed_params* p, ed_dtype dtype
   clear_error();
   ED_CHECK_ARG(b != nullptr && p != nullptr, "ed_hv: basis or params is NULL");
   ED_CHECK_ARG(x != nullptr && y != nullptr, "ed_hv: x or y is NULL");
-  ED_CHECK_ARG(dtype == ED_F64 || dtype == ED_F32, "ed_hv: unknown dtype %d", (int)dtype);
+  ED_CHECK_ARG(dtype == ED_F64 || dtype == ED_F32 || dtype == ED_F64_NATIVE,
+               "ed_hv: unknown dtype %d", (int)dtype);
   ED_CHECK_ARG(aligned16(x) && aligned16(y), "ed_hv: x and y must be 16-byte aligned");
-  const size_t es = dtype == ED_F64 ? 8 : 4;
+  const size_t es = dtype == ED_F32 ? 4 : 8;
   const char* xb = (const char*)x;
   const char* yb = (const char*)y;
   ED_CHECK_ARG(xb + b->dim * es <= yb || yb + b->dim * es <= xb, "ed_hv: x and y overlap");
   cudaStream_t s = (cudaStream_t)stream;
-  const ed_status r = hv_prepare(b, dtype);
+  const ed_status r = hv_prepare(b, dtype == ED_F32 ? ED_F32 : ED_F64_NATIVE);
   if (r != ED_OK) return r;
-  if (dtype == ED_F64)
+  if (dtype != ED_F32)
     return launch_hv<double>(b, p->t, p->U, (const double*)x, (double*)y, b->dn.dim, s);
   return launch_hv<float>(b, p->t, p->U, (const float*)x, (float*)y, b->dn.dim, s);
 }

@@ -77,6 +77,11 @@ struct LzScalars {
   int last_E0_step;
   int pad_;
   double scale[2];
+  // FP64-accurate (fixed-point) runs: buffer i holds int64 X_i with f = scale[i] * X_i.
+  long long fx_max[2];          // max |X_i| of each buffer
+  long long fx_a, fx_b, fx_c;   // H.v epilogue W = round((a S + b n X + c P) 2^fx_k)
+  int fx_k, fx_r;               // ... and W's scale s_w = scale[cur] * 2^fx_r
+  double fx_sw;
   double alpha[ED_MAX_STEPS + 2];
   double beta[ED_MAX_STEPS + 2];
   double E0[ED_MAX_STEPS + 2];
@@ -100,6 +105,26 @@ ed_status launch_hv(const ed_basis* b, double t, double U, const T* x, T* y, int
 // Set the kernel attributes launch_hv relies on (dynamic shared memory size); call before
 // the first launch on a device and outside stream capture.
 ed_status hv_prepare(const ed_basis* b, ed_dtype dtype);
+
+// FP64-accurate Lanczos path (int64 fixed point, ed_fixed.cu).
+struct FxRun {
+  int vb;      // vector bound exponent: |X| <= 2^vb
+  int hops;    // maxhops_up + maxhops_dn
+  int nmax;    // max doubly occupied sites = min(n_up, n_dn)
+};
+FxRun fx_make(const ed_basis* b);
+// Start vector of SplitMix64 `seed` (exact in fixed point) into X (layout rows x ld), and
+// the run's initial scalars (scale[0], fx_max[0]). part: >= 4 * 4 * sm_count longs.
+ed_status fx_start(const ed_basis* b, const FxRun& fx, uint64_t seed, long long* X, int64_t ld,
+                   LzScalars* S, long long* part, cudaStream_t s);
+// Caller FP64 vector f1 (dense) converted to fixed point (exponent from max |f1|).
+ed_status fx_copy_in(const ed_basis* b, const FxRun& fx, const double* f1, long long* X,
+                     int64_t ld, LzScalars* S, long long* part, cudaStream_t s);
+// One step of Algorithm 1 on the fixed-point buffers (cur holds f_j, the other f_{j-1}).
+ed_status fx_step(const ed_basis* b, const FxRun& fx, double t, double U, long long* const B[2],
+                  int cur, int64_t ld, LzScalars* S, long long* pa, long long* pb,
+                  cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
+ed_status fx_prepare(const ed_basis* b);
 
 // Upper bound on the number of CTAs launch_hv uses (size of the partial-sum buffer).
 int64_t hv_max_grid(const ed_basis* b);

@@ -17,11 +17,10 @@
 #include <vector>
 
 #include "ed_internal.cuh"
+#include "ed_lanczos_dev.cuh"
 
 namespace ed {
 
-constexpr int kRedThreads = 256;
-constexpr double kBreakdownRel = 1e-13;
 
 // ------------------------------------------------------------------ start vector
 // SplitMix64 (Steele, Lea & Flood 2014): the (i+1)-th output of the generator seeded with
@@ -110,65 +109,6 @@ lz_update_kernel(LzScalars* S, int cur, const T* __restrict__ bcur, T* __restric
   if (threadIdx.x == 0) pb[blockIdx.x] = v;
 }
 
-// ------------------------------------------------------------------ Sturm bisection
-// Number of eigenvalues of T_m below x (a: 1-based diagonal a[1..m], b: b[2..m]):
-// negative pivots of the LDL^T factorisation of T - x I.
-__device__ int sturm_count(const double* a, const double* b, int m, double x) {
-  int cnt = 0;
-  double d = 1.0;
-  for (int i = 1; i <= m; ++i) {
-    const double off = (i > 1) ? b[i] * b[i] / d : 0.0;
-    d = (a[i] - x) - off;
-    if (d == 0.0) d = -2.2250738585072014e-308;
-    cnt += d < 0.0;
-  }
-  return cnt;
-}
-
-// lambda_min(T_m) by block-parallel multisection: each round evaluates the Sturm count at
-// blockDim.x interior points of the bracket and keeps the sub-interval holding the first
-// eigenvalue, until the bracket stops shrinking in FP64. Returns the upper end (valid in
-// every thread).
-__device__ double sturm_lowest(const double* a, const double* b, int m) {
-  __shared__ double lo_s, hi_s;
-  __shared__ int first_s;
-  if (threadIdx.x == 0) {
-    double lo = INFINITY, hi = -INFINITY;
-    for (int i = 1; i <= m; ++i) {
-      const double r = (i > 1 ? fabs(b[i]) : 0.0) + (i < m ? fabs(b[i + 1]) : 0.0);
-      lo = fmin(lo, a[i] - r);
-      hi = fmax(hi, a[i] + r);
-    }
-    const double span = fmax(fmax(fabs(lo), fabs(hi)), 1e-300);
-    lo_s = lo - 1e-15 * span - 1e-300;
-    hi_s = hi + 1e-15 * span + 1e-300;
-  }
-  __syncthreads();
-  const int P = blockDim.x;
-  for (int round = 0; round < 64; ++round) {
-    const double lo = lo_s, hi = hi_s;
-    const double w = (hi - lo) / (double)(P + 1);
-    if (threadIdx.x == 0) first_s = P;
-    __syncthreads();
-    const double x = lo + w * (double)(threadIdx.x + 1);
-    const bool valid = x > lo && x < hi;
-    if (valid && sturm_count(a, b, m, x) >= 1) atomicMin(&first_s, (int)threadIdx.x);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const int k = first_s;
-      const double nhi = (k < P) ? lo + w * (double)(k + 1) : hi;
-      const double nlo = (k > 0) ? lo + w * (double)k : lo;
-      lo_s = fmax(nlo, lo);
-      hi_s = fmin(nhi, hi);
-    }
-    __syncthreads();
-    if (!(lo_s < hi_s) || (lo_s == lo && hi_s == hi)) break;
-    const double mid = 0.5 * (lo_s + hi_s);
-    if (!(mid > lo_s && mid < hi_s)) break;
-  }
-  return hi_s;
-}
-
 __global__ void __launch_bounds__(kRedThreads)
 lz_finish_kernel(LzScalars* S, int cur, const double* __restrict__ pb, int nb) {
   __shared__ double red[33];
@@ -178,35 +118,11 @@ lz_finish_kernel(LzScalars* S, int cur, const double* __restrict__ pb, int nb) {
   const double b2 = block_sum_array(pb, nb, red);
   if (threadIdx.x == 0) {
     const double beta = sqrt(b2);
-    const double a = S->alpha[j];
-    const double ts = fmax(S->tscale, fabs(a) + S->beta[j]);
-    S->tscale = ts;
-    S->beta[j + 1] = beta;
-    int st = 0;
-    if (!(beta > kBreakdownRel * fmax(1.0, ts))) st = 1;
-    else S->scale[1 - cur] = 1.0 / beta;
-    S->j = j;
-    stop_s = st;
-    S->status = 0;
+    stop_s = finish_record_beta(S, j, beta);
+    if (stop_s == 0) S->scale[1 - cur] = 1.0 / beta;
   }
   __syncthreads();
-  int st = stop_s;
-  const bool check = st != 0 || j >= S->max_steps || (j % S->check_every) == 0;
-  if (check) {
-    const double E = sturm_lowest(S->alpha, S->beta, j);
-    if (threadIdx.x == 0) {
-      S->E0[j] = E;
-      if (st == 0 && S->tol > 0.0 && S->last_E0_step > 0 &&
-          fabs(E - S->last_E0) <= S->tol * fmax(fabs(E), 1.0))
-        st = 2;
-      S->last_E0 = E;
-      S->last_E0_step = j;
-    }
-  }
-  if (threadIdx.x == 0) {
-    if (st == 0 && j >= S->max_steps) st = 3;
-    S->status = st;
-  }
+  finish_tail(S, j, stop_s);
 }
 
 __global__ void __launch_bounds__(kRedThreads)
@@ -247,6 +163,8 @@ struct ed_lanczos {
   int64_t npa = 0, npb = 0;
   int hv_grid = 0;
   bool stopped = false;
+  bool fx = false;     // ED_F64: int64 fixed-point buffers (ed_fixed.cu)
+  FxRun fxr{};
   cudaGraphExec_t graph = nullptr;
 };
 
@@ -254,11 +172,18 @@ static ed_status lz_launch_step(ed_lanczos* st, const ed_params* p, cudaStream_t
                                 cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
   const ed_basis* b = st->basis;
   const int c = st->cur;
+  if (st->fx) {
+    long long* const B[2] = {(long long*)st->B[0], (long long*)st->B[1]};
+    ed_status r = fx_step(b, st->fxr, p->t, p->U, B, c, st->ld, st->S, (long long*)st->pa,
+                          (long long*)st->pb, s, ev0, ev1);
+    if (r == ED_OK) st->cur = 1 - c;
+    return r;
+  }
   LzHvArgs lz{st->S, c, st->pa};
   int grid = 0;
   ed_status r;
   if (ev0) ED_TRY_CUDA(cudaEventRecord(ev0, s));
-  if (st->opts.dtype == ED_F64)
+  if (st->opts.dtype == ED_F64_NATIVE)
     r = launch_hv<double>(b, p->t, p->U, (const double*)st->B[c], (double*)st->B[1 - c], st->ld,
                           s, &lz, &grid);
   else
@@ -267,7 +192,7 @@ static ed_status lz_launch_step(ed_lanczos* st, const ed_params* p, cudaStream_t
   if (r != ED_OK) return r;
   if (ev1) ED_TRY_CUDA(cudaEventRecord(ev1, s));
   const int ug = red_grid(st->n);
-  if (st->opts.dtype == ED_F64)
+  if (st->opts.dtype == ED_F64_NATIVE)
     lz_update_kernel<double><<<ug, kRedThreads, 0, s>>>(
         st->S, c, (const double*)st->B[c], (double*)st->B[1 - c], st->n, st->pa, grid, st->pb);
   else
@@ -284,7 +209,8 @@ static ed_status check_opts(const ed_opts* o) {
   ED_CHECK_ARG(o != nullptr, "opts is NULL");
   ED_CHECK_ARG(o->max_steps >= 1 && o->max_steps <= ED_MAX_STEPS,
                "max_steps = %d outside [1, %d]", o->max_steps, ED_MAX_STEPS);
-  ED_CHECK_ARG(o->dtype == ED_F64 || o->dtype == ED_F32, "unknown dtype %d", (int)o->dtype);
+  ED_CHECK_ARG(o->dtype == ED_F64 || o->dtype == ED_F32 || o->dtype == ED_F64_NATIVE,
+               "unknown dtype %d", (int)o->dtype);
   ED_CHECK_ARG(o->reorth == 0, "reorth = %d is not supported (0 = none)", o->reorth);
   ED_CHECK_ARG(std::isfinite(o->tol), "tol is not finite");
   return ED_OK;
@@ -295,13 +221,14 @@ extern "C" ed_status ed_start_vector(int64_t dim, uint64_t seed, ed_dtype dtype,
   clear_error();
   ED_CHECK_ARG(dim >= 1, "ed_start_vector: dim < 1");
   ED_CHECK_ARG(out != nullptr && aligned16(out), "ed_start_vector: out NULL or not 16-byte aligned");
-  ED_CHECK_ARG(dtype == ED_F64 || dtype == ED_F32, "ed_start_vector: unknown dtype");
+  ED_CHECK_ARG(dtype == ED_F64 || dtype == ED_F32 || dtype == ED_F64_NATIVE,
+               "ed_start_vector: unknown dtype");
   cudaStream_t s = (cudaStream_t)stream;
   const int g = red_grid(dim);
   double* part = nullptr;
   ED_TRY_CUDA(cudaMallocAsync((void**)&part, g * sizeof(double), s));
   start_norm_kernel<<<g, kRedThreads, 0, s>>>(seed, dim, part);
-  if (dtype == ED_F64)
+  if (dtype != ED_F32)
     start_write_kernel<double><<<g, kRedThreads, 0, s>>>(seed, dim, dim, dim, part, g, (double*)out);
   else
     start_write_kernel<float><<<g, kRedThreads, 0, s>>>(seed, dim, dim, dim, part, g, (float*)out);
@@ -345,11 +272,14 @@ static ed_status lz_init(const ed_basis* b, const ed_opts* o, const void* f1, cu
   st->opts = *o;
   cudaGetDevice(&st->device);
   st->stream = s;
-  st->esize = o->dtype == ED_F64 ? 8 : 4;
+  st->esize = o->dtype == ED_F32 ? 4 : 8;
+  st->fx = o->dtype == ED_F64;
+  if (st->fx) st->fxr = fx_make(b);
   st->ld = (b->dn.dim + 31) / 32 * 32;
   st->n = b->up.dim * st->ld;
-  st->npa = hv_max_grid(b);
-  st->npb = (int64_t)sm_count() * 4;
+  // partial sums: one double per CTA, or four int64 words per CTA on the fixed-point path
+  st->npa = hv_max_grid(b) * (st->fx ? 4 : 1);
+  st->npb = (int64_t)sm_count() * 4 * (st->fx ? 4 : 1);
   auto fail = [&](ed_status e) {
     ed_lanczos_destroy(st);
     return e;
@@ -385,9 +315,19 @@ static ed_status lz_init(const ed_basis* b, const ed_opts* o, const void* f1, cu
   const int64_t dim = b->dim, cols = b->dn.dim;
   const int g = red_grid(dim);
   if ((int64_t)g > st->npb) return fail(ED_ERR_ARG);
+  if (st->fx) {
+    ed_status fr = f1 == nullptr
+        ? fx_start(b, st->fxr, o->seed, (long long*)st->B[0], st->ld, st->S, (long long*)st->pb, s)
+        : fx_copy_in(b, st->fxr, (const double*)f1, (long long*)st->B[0], st->ld, st->S,
+                     (long long*)st->pb, s);
+    if (fr != ED_OK) return fail(fr);
+    st->cur = 0;
+    *out = st;
+    return ED_OK;
+  }
   if (f1 == nullptr) {
     start_norm_kernel<<<g, kRedThreads, 0, s>>>(o->seed, dim, st->pb);
-    if (o->dtype == ED_F64)
+    if (o->dtype == ED_F64_NATIVE)
       start_write_kernel<double><<<g, kRedThreads, 0, s>>>(o->seed, dim, cols, st->ld, st->pb, g,
                                                            (double*)st->B[0]);
     else
@@ -395,7 +335,7 @@ static ed_status lz_init(const ed_basis* b, const ed_opts* o, const void* f1, cu
                                                           (float*)st->B[0]);
     init_scalars_kernel<<<1, 32, 0, s>>>(st->S, st->pb, g, 0);
   } else {
-    if (o->dtype == ED_F64)
+    if (o->dtype == ED_F64_NATIVE)
       copy_in_kernel<double><<<g, kRedThreads, 0, s>>>((const double*)f1, dim, cols, st->ld,
                                                        (double*)st->B[0], st->pb);
     else
@@ -418,7 +358,11 @@ extern "C" ed_status ed_lanczos_init(const ed_basis* b, const ed_opts* o, const 
   clear_error();
   ED_CHECK_ARG(out != nullptr, "ed_lanczos_init: out is NULL");
   ed_status r = lz_init(b, o, f1, (cudaStream_t)stream, ED_MAX_STEPS + 1, true, out);
-  if (r == ED_OK) r = hv_prepare(b, o->dtype);
+  if (r == ED_OK) r = o->dtype == ED_F64 ? fx_prepare(b) : hv_prepare(b, o->dtype);
+  if (r != ED_OK && *out) {
+    ed_lanczos_destroy(*out);
+    *out = nullptr;
+  }
   return r;
 }
 
@@ -521,7 +465,8 @@ extern "C" ed_status ed_lanczos_solve(const ed_basis* b, const ed_params* p, con
     return cleanup(ED_ERR_CUDA);
   }
   if ((r = lz_init(b, o, f1, s, 1, false, &st)) != ED_OK) return cleanup(r);
-  if ((r = hv_prepare(b, o->dtype)) != ED_OK) return cleanup(r);
+  if ((r = (o->dtype == ED_F64 ? fx_prepare(b) : hv_prepare(b, o->dtype))) != ED_OK)
+    return cleanup(r);
   // capture two steps (the buffer roles alternate) and replay
   cudaGraph_t g = nullptr;
   if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {

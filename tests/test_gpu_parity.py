@@ -174,15 +174,20 @@ def _solve(ed, L, bonds, nu, nd, t, U, dtype="f64", seed=1, max_steps=300, tol=1
     b = ed.ed_build_basis(L, bonds, nu, nd)
     try:
         return ed.ed_lanczos_solve(b, t, U, ed.make_opts(max_steps=max_steps, tol=tol, seed=seed,
-                                                         dtype=dtype), f1=f1)
+                                                         dtype=dtype), f1=f1,
+                                   raise_not_converged=False)
     finally:
         ed.ed_basis_destroy(b)
 
 
+F64_KINDS = ["f64", "f64n"]   # fixed-point FP64-accurate path, native FP64 path
+
+
+@pytest.mark.parametrize("dtype", F64_KINDS)
 @pytest.mark.parametrize("U", [0.0, 4.0])
-def test_lanczos_ring12_fp64(ed, U):
+def test_lanczos_ring12_fp64(ed, U, dtype):
     L, bonds = 12, ed_inputs.ring_bonds(12)
-    res = _solve(ed, L, bonds, 3, 3, 1.0, U, seed=1, max_steps=200, tol=1e-12)
+    res = _solve(ed, L, bonds, 3, 3, 1.0, U, seed=1, max_steps=200, tol=1e-12, dtype=dtype)
     if U == 0.0:
         ref = -4 * (1 + math.sqrt(3))
     else:
@@ -217,32 +222,39 @@ for _k in range(8):
     RANDOM_CASES.append((_L, np.array(sorted(_pairs)), _nu, _nd, 1.0, float(_rng.uniform(-2, 8))))
 
 
+@pytest.mark.parametrize("dtype", F64_KINDS)
 @pytest.mark.parametrize("case", RANDOM_CASES)
-def test_lanczos_random_lattices_vs_dense(ed, case):
+def test_lanczos_random_lattices_vs_dense(ed, case, dtype):
     L, bonds, nu, nd, t, U = case
     if math.comb(L, nu) * math.comb(L, nd) > 2000:
         pytest.skip("dense reference limited to dim <= 2000")
     ref = dense.spectrum(L, bonds, nu, nd, t, U)[0]
-    res = _solve(ed, L, bonds, nu, nd, t, U, seed=3)
+    res = _solve(ed, L, bonds, nu, nd, t, U, seed=3, dtype=dtype)
     assert abs(res["E0"] - ref) <= 1e-10 * max(1.0, abs(ref)), (res, ref)
 
 
+@pytest.mark.parametrize("dtype", F64_KINDS + ["f32"])
 @pytest.mark.parametrize("U", [0.0, 4.0, 8.0])
-def test_two_site_closed_form(ed, U):
-    res = _solve(ed, 2, np.array([[0, 1]]), 1, 1, 1.0, U, seed=4)
+def test_two_site_closed_form(ed, U, dtype):
+    res = _solve(ed, 2, np.array([[0, 1]]), 1, 1, 1.0, U, seed=4, dtype=dtype)
+    if dtype == "f32":
+        assert abs(res["E0"] - (U - math.sqrt(U * U + 16)) / 2) <= 1e-6
+        return
     assert abs(res["E0"] - (U - math.sqrt(U * U + 16)) / 2) <= 1e-12
 
 
-def test_breakdown_on_eigenvector(ed):
+@pytest.mark.parametrize("dtype", F64_KINDS)
+def test_breakdown_on_eigenvector(ed, dtype):
     case = (2, np.array([[0, 1]]), 1, 1, 1.0, 0.0)
     E0, psi = dense.ground_state(*case)
     f1 = torch.tensor(psi, device="cuda")
-    res = _solve(ed, *case, f1=f1)
+    res = _solve(ed, *case, f1=f1, dtype=dtype)
     assert res["status"] == ed.ED_BREAKDOWN and res["steps"] == 1
     assert abs(res["E0"] - (-2.0)) <= 1e-14
 
 
-def test_alpha_beta_follow_oracle(ed):
+@pytest.mark.parametrize("dtype", F64_KINDS)
+def test_alpha_beta_follow_oracle(ed, dtype):
     """First steps of Algorithm 1 from the same start vector (no reorthogonalisation on
     either side): a_j and b_{j+1} agree to rounding level."""
     L, bonds, nu, nd, t, U = 8, ed_inputs.torus_bonds(2, 4), 3, 3, 1.0, 4.0
@@ -250,17 +262,18 @@ def test_alpha_beta_follow_oracle(ed):
     f1 = olz.normalized_start(ed_inputs.start_vector_raw(6, H.shape[0]))
     ref = olz.lanczos(lambda v: H @ v, f1, max_steps=12, reorth=False, fixed_steps=True)
     res = _solve(ed, L, bonds, nu, nd, t, U, max_steps=12, tol=0.0,
-                 f1=torch.tensor(f1, device="cuda"))
+                 f1=torch.tensor(f1, device="cuda"), dtype=dtype)
     assert res["steps"] == 12
     assert np.allclose(res["alpha"], ref.alpha, rtol=1e-11, atol=1e-11)
     assert np.allclose(res["beta"], ref.beta, rtol=1e-11, atol=1e-11)
 
 
-def test_step_api_matches_solve(ed):
+@pytest.mark.parametrize("dtype", F64_KINDS + ["f32"])
+def test_step_api_matches_solve(ed, dtype):
     L, bonds, nu, nd, t, U = 6, ed_inputs.ring_bonds(6), 3, 3, 1.0, 2.0
     b = ed.ed_build_basis(L, bonds, nu, nd)
     try:
-        opts = ed.make_opts(max_steps=10, tol=0.0, seed=8)
+        opts = ed.make_opts(max_steps=10, tol=0.0, seed=8, dtype=dtype)
         full = ed.ed_lanczos_solve(b, t, U, opts)
         st = ed.ed_lanczos_init(b, opts)
         try:
@@ -281,7 +294,9 @@ def test_step_api_matches_solve(ed):
 
 @pytest.mark.parametrize("name,dtype,expect,tol", [
     ("torus4x4_5_5", "f64", -24.0, 1e-10),
+    ("torus4x4_5_5", "f64n", -24.0, 1e-10),
     ("ring16_8_8", "f32", -20.109357968503396, 1e-6),
+    ("ring16_8_8", "f64", -20.109357968503396, 1e-10),
 ])
 def test_full_size_U0_closed_form(ed, name, dtype, expect, tol):
     """U = 0 at full size: E0 = sum of the lowest single-particle levels."""
@@ -299,3 +314,19 @@ def _hop_matrix(L, bonds):
         h[i, j] -= 1
         h[j, i] -= 1
     return h
+
+
+def test_fixed_point_matches_native_fp64_from_seeded_start(ed):
+    """The FP64-accurate fixed-point run and the native FP64 run from the same seeded device
+    start vector produce the same a_j, b_j to rounding level."""
+    L, bonds, nu, nd, t, U = 12, ed_inputs.ring_bonds(12), 3, 3, 1.0, 4.0
+    b = ed.ed_build_basis(L, bonds, nu, nd)
+    try:
+        out = {}
+        for dt in F64_KINDS:
+            out[dt] = ed.ed_lanczos_solve(b, t, U, ed.make_opts(max_steps=15, tol=0.0, seed=1,
+                                                                dtype=dt))
+        assert np.allclose(out["f64"]["alpha"], out["f64n"]["alpha"], rtol=1e-11, atol=1e-12)
+        assert np.allclose(out["f64"]["beta"], out["f64n"]["beta"], rtol=1e-11, atol=1e-12)
+    finally:
+        ed.ed_basis_destroy(b)
