@@ -189,7 +189,8 @@ def bench_ours(args):
             dist.barrier()
 
     # ---------------------------------------------------------------- device-resident
-    opts = ed.make_opts(max_steps=ed.ED_MAX_STEPS, tol=0.0, seed=w["seed"], dtype=dtype)
+    opts = ed.make_opts(max_steps=ed.ED_MAX_STEPS, tol=0.0, seed=w["seed"], dtype=dtype,
+                        schedule=args.schedule)
     st = ed.ed_lanczos_init(basis, opts)
     ed.ed_lanczos_run(st, t, U, W)
     torch.cuda.synchronize()
@@ -223,7 +224,7 @@ def bench_ours(args):
     f1_host = torch.from_numpy(ed_inputs.start_vector_raw(w["seed"], dim)).to(
         torch.float64 if dtype == "f64" else torch.float32).pin_memory()
     f1_dev = torch.empty(dim, dtype=f1_host.dtype, device="cuda")
-    eopts = ed.make_opts(max_steps=K, tol=0.0, seed=w["seed"], dtype=dtype)
+    eopts = ed.make_opts(max_steps=K, tol=0.0, seed=w["seed"], dtype=dtype, schedule=args.schedule)
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -288,6 +289,7 @@ def main():
     ap.add_argument("--cpu-reps", type=int, default=8)
     ap.add_argument("--ref-rows", type=int, default=100000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--schedule", type=int, default=-1, help="H.v kernel variant (-1: default)")
     args = ap.parse_args()
     if args.impl == "reference":
         return bench_reference(args)

@@ -1,5 +1,6 @@
 // Basis construction (Sec. 2.1): combinadic unranking of each species' bit strings and the
 // per-state hop tables (target rank + fermion sign), built on the device.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -102,6 +103,8 @@ __global__ void hop_kernel(const uint32_t* __restrict__ bits, int64_t dim,
   }
 }
 
+constexpr int64_t kMaxOrderedRows = 4000000;  // host RCM up to this many up states
+
 static uint64_t binom_host(int n, int k) {
   if (k < 0 || k > n) return 0;
   uint64_t c = 1;
@@ -133,6 +136,71 @@ static ed_status build_species(SpeciesTables& sp, int n_sites, int n, const int2
                                           h, nullptr);
     ED_TRY_CUDA(cudaGetLastError());
   }
+  return ED_OK;
+}
+
+// Reverse Cuthill-McKee order of the hop graph of one species (host, from the device
+// table): breadth-first search from a low-degree vertex of a far end (two sweeps), each
+// vertex's unvisited neighbours taken by increasing degree (ties by index), every
+// connected component in turn, the result reversed. Deterministic.
+static ed_status rcm_order(const SpeciesTables& sp, cudaStream_t s, std::vector<int32_t>& order) {
+  const int64_t n = sp.dim;
+  const int mh = sp.maxhops;
+  order.resize(n);
+  if (mh == 0 || n < 3) {
+    for (int64_t i = 0; i < n; ++i) order[i] = (int32_t)i;
+    return ED_OK;
+  }
+  std::vector<int32_t> tab((size_t)mh * n);
+  ED_TRY_CUDA(cudaMemcpyAsync(tab.data(), sp.hop, tab.size() * 4, cudaMemcpyDeviceToHost, s));
+  ED_TRY_CUDA(cudaStreamSynchronize(s));
+  std::vector<int32_t> deg(n, 0);
+  auto nb = [&](int64_t v, int k) { return (int64_t)((uint32_t)tab[(size_t)k * n + v] & kTargetMask); };
+  for (int64_t v = 0; v < n; ++v)
+    for (int k = 0; k < mh && nb(v, k) < n; ++k) ++deg[v];
+  // stamp[v] == cur marks v as visited by the current search; taken[v] marks vertices
+  // already placed in the order
+  std::vector<int32_t> stamp(n, 0);
+  std::vector<char> taken(n, 0);
+  int32_t cur = 0;
+  std::vector<int32_t> out;
+  out.reserve(n);
+  std::vector<int32_t> nbuf, visit;
+  auto bfs = [&](int64_t root) {
+    ++cur;
+    visit.clear();
+    visit.push_back((int32_t)root);
+    stamp[root] = cur;
+    for (size_t h = 0; h < visit.size(); ++h) {
+      const int64_t v = visit[h];
+      nbuf.clear();
+      for (int k = 0; k < mh && nb(v, k) < n; ++k) {
+        const int64_t w = nb(v, k);
+        if (stamp[w] != cur && !taken[w]) {
+          stamp[w] = cur;
+          nbuf.push_back((int32_t)w);
+        }
+      }
+      std::sort(nbuf.begin(), nbuf.end(), [&](int32_t a, int32_t b) {
+        return deg[a] != deg[b] ? deg[a] < deg[b] : a < b;
+      });
+      visit.insert(visit.end(), nbuf.begin(), nbuf.end());
+    }
+  };
+  for (int64_t start = 0; start < n; ++start) {
+    if (taken[start]) continue;
+    // component of `start`: its lowest-degree vertex, then the last vertex of a search from
+    // there (a far end of the component) as the root
+    bfs(start);
+    int64_t root = visit[0];
+    for (int32_t v : visit)
+      if (deg[v] < deg[root] || (deg[v] == deg[root] && v < root)) root = v;
+    bfs(root);
+    bfs(visit.back());
+    for (int32_t v : visit) taken[v] = 1;
+    out.insert(out.end(), visit.begin(), visit.end());
+  }
+  for (int64_t i = 0; i < n; ++i) order[i] = out[n - 1 - i];
   return ED_OK;
 }
 
@@ -201,6 +269,15 @@ extern "C" ed_status ed_build_basis(const ed_lattice* L, int32_t n_up, int32_t n
   if ((st = build_species(B->dn, L->n_sites, n_dn, d_bonds, L->n_bonds, B->binom, d_count, s)) != ED_OK)
     return fail(st);
   B->dim = B->up.dim * B->dn.dim;
+  if (B->up.dim <= kMaxOrderedRows && B->up.maxhops > 0) {
+    std::vector<int32_t> order;
+    if ((st = rcm_order(B->up, s, order)) != ED_OK) return fail(st);
+    if (cudaMalloc((void**)&B->up_order, order.size() * 4) != cudaSuccess ||
+        cudaMemcpyAsync(B->up_order, order.data(), order.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      set_error("ed_build_basis: row order upload failed");
+      return fail(ED_ERR_CUDA);
+    }
+  }
   if (cudaStreamSynchronize(s) != cudaSuccess) {
     set_error("ed_build_basis: %s", cudaGetErrorString(cudaGetLastError()));
     return fail(ED_ERR_CUDA);
@@ -244,6 +321,7 @@ extern "C" void ed_basis_destroy(ed_basis* B) {
   free_species(B->up);
   free_species(B->dn);
   if (B->binom) cudaFree(B->binom);
+  if (B->up_order) cudaFree(B->up_order);
   if (prev != B->device) cudaSetDevice(prev);
   delete B;
 }

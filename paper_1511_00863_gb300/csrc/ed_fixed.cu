@@ -486,13 +486,17 @@ ed_status fx_copy_in(const ed_basis* b, const FxRun& fx, const double* f1, long 
 
 ed_status fx_step(const ed_basis* b, const FxRun& fx, double t, double U, long long* const B[2],
                   int cur, int64_t ld, LzScalars* S, long long* pa, long long* pb,
-                  cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
+                  cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, const Hv2Plan* plan) {
   fx_plan_kernel<<<1, 32, 0, s>>>(S, cur, t, U, fx.hops, fx.nmax, fx.vb);
   if (ev0) ED_TRY_CUDA(cudaEventRecord(ev0, s));
   const FxHvArgs a = fx_args(b, ld);
-  const int R = fx_rows(b);
+  const int R = plan ? -1 : fx_rows(b);
   int grid;
-  if (R == 2) {
+  if (plan) {
+    grid = hv2_grid(plan);
+    ed_status r = hv2_launch(plan, b, t, U, B[cur], B[1 - cur], S, cur, pa, s);
+    if (r != ED_OK) return r;
+  } else if (R == 2) {
     grid = (int)((b->up.dim + 1) / 2);
     fx_hv_staged_kernel<2><<<grid, kFxThreads, fx_smem<2>(b), s>>>(a, B[cur], B[1 - cur], S, pa);
   } else if (R == 1) {

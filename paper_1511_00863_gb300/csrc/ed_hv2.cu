@@ -1,0 +1,463 @@
+// Lanczos-fused H.v for the library's own (padded) vectors: the step that dominates a
+// Lanczos iteration (Sec. 4: the product on the first line of Algorithm 1's loop).
+//
+//   w = s_cur H B_cur - b_j s_prev B_prev, written over B_prev, plus per-CTA partial sums
+//   of w . f_j; H = H_up (x) I + I (x) H_dn + U D  (Sec. 2.1 Eq. 3, Sec. 4 Eqs. 5-6).
+//
+// Layout: B[u * ld + d], ld = dim_dn rounded up to 32 (pads hold 0 and stay 0).
+// One CTA owns R consecutive up rows; each thread owns V consecutive d per iteration.
+//  * The R rows are staged once into shared memory, interleaved so that one vector load
+//    (R elements, 16 bytes for 4 x FP32 or 2 x int64) serves every row for a given d.
+//    (A variant that also stages the negated rows, folding the fermion sign into the
+//    table offset, is kept behind the NEG template flag.)
+//  * Down part: a per-run table gives, for hop k of state d, the byte offset of the
+//    target inside the staged rows (sign in bit 31 for FP32; padding -> a zero slot).
+//    Consecutive threads read consecutive table entries (coalesced vector loads).
+//  * Up part: each row's hop list is sorted by sign into shared memory once per CTA; the
+//    threads then stream the neighbour rows with V-wide coalesced loads (L2-resident reuse).
+//  * Diagonal: U popc(up[u] & dn[d]) x on the integer pipe.
+// FP32 accumulates in FP32 (dot products compensated, FP64 per CTA). The int64 variant is
+// the FP64-accurate path of ed_fixed.cu: exact hop sums, W = round((a S + b n X + c P) 2^k).
+#include <cstring>
+
+#include "ed_fixed.cuh"
+#include "ed_internal.cuh"
+
+namespace ed {
+
+template <typename E, int N>
+struct alignas(sizeof(E) * N) Pack {
+  E v[N];
+};
+
+// Streaming (evict-first) access for the f_{j-1} / w stream, so the rows of f_j that
+// neighbouring up rows will gather stay resident in L2.
+template <typename E, int N>
+__device__ __forceinline__ Pack<E, N> ldcs_pack(const Pack<E, N>* p) {
+  Pack<E, N> r;
+  if constexpr (sizeof(Pack<E, N>) == 16) {
+    const int4 v = __ldcs(reinterpret_cast<const int4*>(p));
+    memcpy(&r, &v, 16);
+  } else if constexpr (sizeof(Pack<E, N>) == 8) {
+    const long long v = __ldcs(reinterpret_cast<const long long*>(p));
+    memcpy(&r, &v, 8);
+  } else {
+    const int v = __ldcs(reinterpret_cast<const int*>(p));
+    memcpy(&r, &v, 4);
+  }
+  return r;
+}
+template <typename E, int N>
+__device__ __forceinline__ void stcs_pack(Pack<E, N>* p, const Pack<E, N>& r) {
+  if constexpr (sizeof(Pack<E, N>) == 16) {
+    int4 v;
+    memcpy(&v, &r, 16);
+    __stcs(reinterpret_cast<int4*>(p), v);
+  } else if constexpr (sizeof(Pack<E, N>) == 8) {
+    long long v;
+    memcpy(&v, &r, 8);
+    __stcs(reinterpret_cast<long long*>(p), v);
+  } else {
+    int v;
+    memcpy(&v, &r, 4);
+    __stcs(reinterpret_cast<int*>(p), v);
+  }
+}
+
+struct Hv2Args {
+  const uint32_t* __restrict__ up_bits;
+  const uint32_t* __restrict__ dn_bits;  // padded to ld (pads 0)
+  const uint32_t* __restrict__ dtab;     // [maxhops_dn][ld] byte offsets
+  const int32_t* __restrict__ hop_up;    // basis table [maxhops_up][dim_up]
+  const int32_t* __restrict__ order;     // up-row visit order (NULL = rank order)
+  int64_t dim_up;
+  int ld, maxhops_up, maxhops_dn;
+  float t, U;  // FP32 variant
+};
+
+template <typename E, int R, int V, bool NEG, int T>
+__global__ void __launch_bounds__(T)
+hv2_kernel(Hv2Args a, const E* __restrict__ x, E* __restrict__ y, const LzScalars* __restrict__ S,
+           int cur, void* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int npos_s[R], nneg_s[R];
+  __shared__ double red[33];
+  if (S->status != 0) return;
+  const int ld = a.ld;
+  const int MH = a.maxhops_up > 0 ? a.maxhops_up : 1;
+  Pack<E, R>* xs = reinterpret_cast<Pack<E, R>*>(smem);
+  Pack<E, R>* xsn = xs + (ld + 1);  // negated copy (NEG only)
+  int64_t* upoff = reinterpret_cast<int64_t*>(
+      smem + ((size_t)(NEG ? 2 : 1) * (ld + 1) * sizeof(Pack<E, R>) + 15) / 16 * 16);
+  uint32_t* upraw = reinterpret_cast<uint32_t*>(upoff + R * MH);
+  const int64_t g0 = (int64_t)blockIdx.x * R;
+  int64_t urow[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int64_t g = g0 + r;
+    urow[r] = g < a.dim_up ? (a.order ? (int64_t)a.order[g] : g) : a.dim_up;  // dim_up = none
+  }
+
+  // ---- stage the R rows (one d per thread: R coalesced loads, one vector store)
+  for (int d = threadIdx.x; d <= ld; d += T) {
+    Pack<E, R> p;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t u = urow[r];
+      p.v[r] = (d < ld && u < a.dim_up) ? x[u * ld + d] : E(0);
+    }
+    xs[d] = p;
+    if (NEG) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) p.v[r] = -p.v[r];
+      xsn[d] = p;
+    }
+  }
+  // ---- up-hop lists: raw entries, then per row positives first, negatives after
+  for (int i = threadIdx.x; i < R * a.maxhops_up; i += T) {
+    const int r = i / a.maxhops_up, k = i - r * a.maxhops_up;
+    int64_t u = a.dim_up;
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr)
+      if (rr == r) u = urow[rr];
+    upraw[i] = (u < a.dim_up) ? (uint32_t)a.hop_up[(int64_t)k * a.dim_up + u] : (uint32_t)a.dim_up;
+  }
+  __syncthreads();
+  if (threadIdx.x < R) {
+    const int r = threadIdx.x;
+    int np = 0, nn = 0;
+    for (int k = 0; k < a.maxhops_up; ++k) {
+      const uint32_t e = upraw[r * a.maxhops_up + k];
+      const int64_t tg = (int64_t)(e & kTargetMask);
+      if (tg >= a.dim_up) break;
+      if (!(e & kSignBit)) upoff[r * MH + np++] = tg * ld;
+    }
+    for (int k = 0; k < a.maxhops_up; ++k) {
+      const uint32_t e = upraw[r * a.maxhops_up + k];
+      const int64_t tg = (int64_t)(e & kTargetMask);
+      if (tg >= a.dim_up) break;
+      if (e & kSignBit) upoff[r * MH + np + nn++] = tg * ld;
+    }
+    npos_s[r] = np;
+    nneg_s[r] = nn;
+  }
+  __syncthreads();
+
+  uint32_t ub[R];
+  int npos[R], nneg[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    ub[r] = (urow[r] < a.dim_up) ? a.up_bits[urow[r]] : 0u;
+    npos[r] = npos_s[r];
+    nneg[r] = nneg_s[r];
+  }
+  // per-run scalars
+  float sc = 1.f, bsp = 0.f;
+  long long ca = 0, cb = 0, cc = 0;
+  int ck = 0;
+  if constexpr (sizeof(E) == 4) {
+    const int j = S->j + 1;
+    sc = (float)S->scale[cur];
+    bsp = (float)(S->beta[j] * S->scale[1 - cur]);
+  } else {
+    ca = S->fx_a;
+    cb = S->fx_b;
+    cc = S->fx_c;
+    ck = S->fx_k;
+  }
+  const unsigned char* xsb = smem;
+  DotAcc<float> dotf;
+  I192 doti;
+  i192_zero(doti);
+
+  for (int d0 = threadIdx.x * V; d0 < ld; d0 += T * V) {
+    E acc[R][V];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[r][v] = E(0);
+    // ---- down part: gathers inside the staged rows
+    const uint32_t* tp = a.dtab + d0;
+#pragma unroll 2
+    for (int k = 0; k < a.maxhops_dn; ++k) {
+      const Pack<uint32_t, V> e = *reinterpret_cast<const Pack<uint32_t, V>*>(tp + (size_t)k * ld);
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        if constexpr (sizeof(E) == 4) {
+          const uint32_t ev = e.v[v];
+          const Pack<E, R> q = *reinterpret_cast<const Pack<E, R>*>(xsb + (ev & 0x7FFFFFFFu));
+          const float c = __int_as_float(0x3f800000u | (ev & 0x80000000u));
+#pragma unroll
+          for (int r = 0; r < R; ++r) acc[r][v] = (E)fmaf(c, (float)q.v[r], (float)acc[r][v]);
+        } else if constexpr (NEG) {
+          const Pack<E, R> q = *reinterpret_cast<const Pack<E, R>*>(xsb + e.v[v]);
+#pragma unroll
+          for (int r = 0; r < R; ++r) acc[r][v] += q.v[r];
+        } else {
+          const uint32_t ev = e.v[v];
+          const Pack<E, R> q = *reinterpret_cast<const Pack<E, R>*>(xsb + (ev & 0x7FFFFFFFu));
+          const long long m = (long long)((int32_t)ev >> 31);  // 0 or -1
+#pragma unroll
+          for (int r = 0; r < R; ++r) acc[r][v] += ((long long)q.v[r] ^ m) - m;
+        }
+      }
+    }
+    // ---- up part: neighbouring rows, V-wide coalesced loads
+    const E* xb = x + d0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t* uo = upoff + r * MH;
+#pragma unroll 8
+      for (int k = 0; k < npos[r]; ++k) {
+        const Pack<E, V> q = *reinterpret_cast<const Pack<E, V>*>(xb + uo[k]);
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[r][v] += q.v[v];
+      }
+#pragma unroll 4
+      for (int k = 0; k < nneg[r]; ++k) {
+        const Pack<E, V> q = *reinterpret_cast<const Pack<E, V>*>(xb + uo[npos[r] + k]);
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[r][v] -= q.v[v];
+      }
+    }
+    // ---- diagonal and the Lanczos epilogue
+    const Pack<uint32_t, V> db = *reinterpret_cast<const Pack<uint32_t, V>*>(a.dn_bits + d0);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t u = urow[r];
+      if (u >= a.dim_up) continue;
+      E* yp = y + u * ld + d0;
+      const Pack<E, V> P = ldcs_pack(reinterpret_cast<const Pack<E, V>*>(yp));
+      Pack<E, V> W;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const E xc = xs[d0 + v].v[r];
+        const int n = __popc(ub[r] & db.v[v]);
+        if constexpr (sizeof(E) == 4) {
+          const float hx = fmaf(-a.t, (float)acc[r][v], a.U * (float)n * (float)xc);
+          const float w = fmaf(sc, hx, -bsp * (float)P.v[v]);
+          W.v[v] = (E)w;
+          dotf.add(w, sc * (float)xc);
+        } else {
+          const long long xi = (long long)xc;
+          const i128 p = (i128)ca * (long long)acc[r][v] + (i128)cb * (xi * n) +
+                         (i128)cc * (long long)P.v[v];
+          const long long w = round_shift(p, ck);
+          W.v[v] = (E)w;
+          i192_add(doti, (i128)w * xi);
+        }
+      }
+      stcs_pack(reinterpret_cast<Pack<E, V>*>(yp), W);
+    }
+  }
+  if constexpr (sizeof(E) == 4) {
+    const double v = block_sum(dotf.get(), red);
+    if (threadIdx.x == 0) reinterpret_cast<double*>(partial)[blockIdx.x] = v;
+  } else {
+    // same record layout as the fixed-point reductions: (lo, lo >> 64, hi, max)
+    __shared__ unsigned long long sm[32][3];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const I192 w = i192_shfl_down(doti, o);
+      i192_add(doti, w);
+    }
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+      sm[wid][0] = (unsigned long long)doti.lo;
+      sm[wid][1] = (unsigned long long)(doti.lo >> 64);
+      sm[wid][2] = (unsigned long long)doti.hi;
+    }
+    __syncthreads();
+    if (wid == 0) {
+      I192 s;
+      i192_zero(s);
+      if (lane < T / 32) {
+        s.lo = ((u128)sm[lane][1] << 64) | (u128)sm[lane][0];
+        s.hi = (long long)sm[lane][2];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const I192 w = i192_shfl_down(s, o);
+        i192_add(s, w);
+      }
+      if (lane == 0) {
+        long long* out = reinterpret_cast<long long*>(partial) + 4 * blockIdx.x;
+        out[0] = (long long)(unsigned long long)s.lo;
+        out[1] = (long long)(unsigned long long)(s.lo >> 64);
+        out[2] = s.hi;
+        out[3] = 0;
+      }
+    }
+  }
+}
+
+// Per-run down table: byte offsets of hop targets inside the staged rows.
+__global__ void hv2_table_kernel(const int32_t* __restrict__ hop_dn, const uint32_t* __restrict__ dn_bits,
+                                 int64_t dim_dn, int ld, int maxhops, uint32_t elem_bytes,
+                                 uint32_t neg_region, int sign_bit, uint32_t* __restrict__ dtab,
+                                 uint32_t* __restrict__ dn_pad) {
+  const int64_t total = (int64_t)maxhops * ld;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total + ld;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i >= total) {
+      const int64_t d = i - total;
+      dn_pad[d] = d < dim_dn ? dn_bits[d] : 0u;
+      continue;
+    }
+    const int64_t k = i / ld, d = i - k * ld;
+    uint32_t off = (uint32_t)ld * elem_bytes;  // zero slot
+    if (d < dim_dn) {
+      const uint32_t e = (uint32_t)hop_dn[k * dim_dn + d];
+      const uint32_t tg = e & kTargetMask;
+      if (tg < (uint32_t)dim_dn) {
+        off = tg * elem_bytes;
+        if (e & kSignBit) off = sign_bit ? (off | kSignBit) : off + neg_region;
+      }
+    }
+    dtab[i] = off;
+  }
+}
+
+// ------------------------------------------------------------------ host side
+struct Hv2Plan {
+  int kind = 0;  // 0: not usable; otherwise an index into the launch switch
+  size_t smem = 0;
+  int grid = 0;
+  int ld = 0;
+  uint32_t* dtab = nullptr;
+  uint32_t* dn_pad = nullptr;
+};
+
+static int optin_smem() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v;
+}
+
+template <typename E, int R, bool NEG>
+static size_t hv2_smem(const ed_basis* b, int ld) {
+  const int MH = b->up.maxhops > 0 ? b->up.maxhops : 1;
+  return ((size_t)(NEG ? 2 : 1) * (ld + 1) * sizeof(E) * R + 15) / 16 * 16 + (size_t)R * MH * 12;
+}
+
+// Variants (schedule ids): 1-3 FP32 with R = 4, 2, 1 rows per CTA; 4-5 int64 with R = 2, 1
+// (sign by xor); 6-7 int64 with the negated copy staged, R = 1 and 2.
+#define HV2_KINDS(X)                      \
+  X(1, float, 4, 4, false, 256)           \
+  X(2, float, 2, 4, false, 256)           \
+  X(3, float, 1, 4, false, 256)           \
+  X(4, long long, 2, 2, false, 256)       \
+  X(5, long long, 1, 2, false, 256)       \
+  X(6, long long, 1, 2, true, 256)        \
+  X(7, long long, 2, 2, true, 512)
+
+void hv2_free(Hv2Plan* p) {
+  if (!p) return;
+  if (p->dtab) cudaFree(p->dtab);
+  if (p->dn_pad) cudaFree(p->dn_pad);
+  delete p;
+}
+
+// Choose the kernel variant for this basis and element type, build the per-run tables.
+static bool kind_info(int kind, const ed_basis* b, int ld, size_t* sm, int* R, bool* fx, bool* neg) {
+  switch (kind) {
+#define HV2_INFO(K, E, R_, V, NEG, T)                            \
+    case K:                                                      \
+      *sm = hv2_smem<E, R_, NEG>(b, ld);                         \
+      *R = R_;                                                   \
+      *fx = sizeof(E) == 8;                                      \
+      *neg = NEG;                                                \
+      return true;
+    HV2_KINDS(HV2_INFO)
+#undef HV2_INFO
+    default:
+      return false;
+  }
+}
+
+ed_status hv2_build(const ed_basis* b, bool fixed_point, int ld, int schedule, cudaStream_t s,
+                    Hv2Plan** out) {
+  *out = nullptr;
+  const size_t lim = (size_t)optin_smem();
+  static const int pref_f32[] = {1, 2, 3}, pref_fx[] = {6, 4, 5, 7};
+  const int* pref = fixed_point ? pref_fx : pref_f32;
+  const int npref = fixed_point ? 4 : 3;
+  int kind = 0, R = 1;
+  size_t sm = 0;
+  bool neg = false;
+  for (int i = -1; i < npref && !kind; ++i) {
+    const int k = i < 0 ? schedule : pref[i];
+    size_t smk;
+    int Rk;
+    bool fxk, negk;
+    if (k <= 0 || !kind_info(k, b, ld, &smk, &Rk, &fxk, &negk)) continue;
+    if (fxk != fixed_point || smk > lim || b->up.dim < Rk) continue;
+    kind = k, R = Rk, sm = smk, neg = negk;
+  }
+  if (!kind) return ED_OK;  // caller falls back to the general kernels
+  Hv2Plan* p = new Hv2Plan();
+  p->kind = kind;
+  p->smem = sm;
+  p->ld = ld;
+  p->grid = (int)((b->up.dim + R - 1) / R);
+  const int mh = b->dn.maxhops;
+  if (cudaMalloc((void**)&p->dtab, (size_t)(mh > 0 ? mh : 1) * ld * 4) != cudaSuccess ||
+      cudaMalloc((void**)&p->dn_pad, (size_t)ld * 4) != cudaSuccess) {
+    hv2_free(p);
+    set_error("H.v tables: out of device memory");
+    return ED_ERR_OOM;
+  }
+  const uint32_t elem_bytes = (uint32_t)((fixed_point ? 8 : 4) * R);
+  const uint32_t neg_region = (uint32_t)((ld + 1) * elem_bytes);
+  const int64_t total = (int64_t)mh * ld + ld;
+  int grid = (int)((total + 255) / 256);
+  if (grid > sm_count() * 8) grid = sm_count() * 8;
+  hv2_table_kernel<<<grid, 256, 0, s>>>(b->dn.hop, b->dn.bits, b->dn.dim, ld, mh, elem_bytes,
+                                        neg_region, neg ? 0 : 1, p->dtab, p->dn_pad);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+#define HV2_ATTR(K, E, R_, V, NEG, T)                                                    \
+    if (kind == K)                                                                        \
+      e = cudaFuncSetAttribute(hv2_kernel<E, R_, V, NEG, T>,                             \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    HV2_KINDS(HV2_ATTR)
+#undef HV2_ATTR
+  }
+  if (e != cudaSuccess) {
+    hv2_free(p);
+    set_error("H.v tables: %s", cudaGetErrorString(e));
+    return ED_ERR_CUDA;
+  }
+  *out = p;
+  return ED_OK;
+}
+
+int hv2_grid(const Hv2Plan* p) { return p ? p->grid : 0; }
+int hv2_kind(const Hv2Plan* p) { return p ? p->kind : 0; }
+
+ed_status hv2_launch(const Hv2Plan* p, const ed_basis* b, double t, double U, const void* x,
+                     void* y, const LzScalars* S, int cur, void* partial, cudaStream_t s) {
+  Hv2Args a;
+  a.up_bits = b->up.bits;
+  a.dn_bits = p->dn_pad;
+  a.dtab = p->dtab;
+  a.hop_up = b->up.hop;
+  a.order = b->up_order;
+  a.dim_up = b->up.dim;
+  a.ld = p->ld;
+  a.maxhops_up = b->up.maxhops;
+  a.maxhops_dn = b->dn.maxhops;
+  a.t = (float)t;
+  a.U = (float)U;
+#define HV2_LAUNCH(K, E, R_, V, NEG, T)                                                    \
+  if (p->kind == K)                                                                         \
+    hv2_kernel<E, R_, V, NEG, T><<<p->grid, T, p->smem, s>>>(a, (const E*)x, (E*)y, S, cur, \
+                                                             partial);
+  HV2_KINDS(HV2_LAUNCH)
+#undef HV2_LAUNCH
+  ED_TRY_CUDA(cudaGetLastError());
+  return ED_OK;
+}
+
+}  // namespace ed

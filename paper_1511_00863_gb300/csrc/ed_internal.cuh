@@ -54,6 +54,10 @@ struct ed_basis {
   int64_t dim = 0;
   ed::SpeciesTables up, dn;
   uint32_t* binom = nullptr;  // device copy of C(n, k), n, k <= 32
+  // Order in which H.v kernels visit the up rows (reverse Cuthill-McKee order of the
+  // up-species hop graph), so that rows sharing up-neighbours are processed close in
+  // time and the neighbours stay resident in L2. NULL = rank order.
+  int32_t* up_order = nullptr;
 };
 
 namespace ed {
@@ -123,8 +127,19 @@ ed_status fx_copy_in(const ed_basis* b, const FxRun& fx, const double* f1, long 
 // One step of Algorithm 1 on the fixed-point buffers (cur holds f_j, the other f_{j-1}).
 ed_status fx_step(const ed_basis* b, const FxRun& fx, double t, double U, long long* const B[2],
                   int cur, int64_t ld, LzScalars* S, long long* pa, long long* pb,
-                  cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
+                  cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, const struct Hv2Plan* plan);
 ed_status fx_prepare(const ed_basis* b);
+
+// Lanczos-fused H.v on the library's padded vectors (ed_hv2.cu). hv2_build leaves *out
+// NULL when no variant fits in shared memory (the general kernels are used then).
+struct Hv2Plan;
+// schedule: -1 = default variant, else a variant id (see ed_hv2.cu) if it fits.
+ed_status hv2_build(const ed_basis* b, bool fixed_point, int ld, int schedule, cudaStream_t s,
+                    Hv2Plan** out);
+void hv2_free(Hv2Plan* p);
+int hv2_grid(const Hv2Plan* p);
+ed_status hv2_launch(const Hv2Plan* p, const ed_basis* b, double t, double U, const void* x,
+                     void* y, const LzScalars* S, int cur, void* partial, cudaStream_t s);
 
 // Upper bound on the number of CTAs launch_hv uses (size of the partial-sum buffer).
 int64_t hv_max_grid(const ed_basis* b);

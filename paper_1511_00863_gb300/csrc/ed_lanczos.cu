@@ -165,6 +165,7 @@ struct ed_lanczos {
   bool stopped = false;
   bool fx = false;     // ED_F64: int64 fixed-point buffers (ed_fixed.cu)
   FxRun fxr{};
+  Hv2Plan* plan = nullptr;  // fused H.v on the padded layout (ed_hv2.cu), if it fits
   cudaGraphExec_t graph = nullptr;
 };
 
@@ -175,7 +176,7 @@ static ed_status lz_launch_step(ed_lanczos* st, const ed_params* p, cudaStream_t
   if (st->fx) {
     long long* const B[2] = {(long long*)st->B[0], (long long*)st->B[1]};
     ed_status r = fx_step(b, st->fxr, p->t, p->U, B, c, st->ld, st->S, (long long*)st->pa,
-                          (long long*)st->pb, s, ev0, ev1);
+                          (long long*)st->pb, s, ev0, ev1, st->plan);
     if (r == ED_OK) st->cur = 1 - c;
     return r;
   }
@@ -183,7 +184,10 @@ static ed_status lz_launch_step(ed_lanczos* st, const ed_params* p, cudaStream_t
   int grid = 0;
   ed_status r;
   if (ev0) ED_TRY_CUDA(cudaEventRecord(ev0, s));
-  if (st->opts.dtype == ED_F64_NATIVE)
+  if (st->plan) {
+    grid = hv2_grid(st->plan);
+    r = hv2_launch(st->plan, b, p->t, p->U, st->B[c], st->B[1 - c], st->S, c, st->pa, s);
+  } else if (st->opts.dtype == ED_F64_NATIVE)
     r = launch_hv<double>(b, p->t, p->U, (const double*)st->B[c], (double*)st->B[1 - c], st->ld,
                           s, &lz, &grid);
   else
@@ -248,6 +252,7 @@ extern "C" void ed_lanczos_destroy(ed_lanczos* st) {
   if (prev != st->device) cudaSetDevice(st->device);
   if (st->stream) cudaStreamSynchronize(st->stream);
   if (st->graph) cudaGraphExecDestroy(st->graph);
+  if (st->plan) hv2_free(st->plan);
   for (int i = 0; i < 2; ++i)
     if (st->B[i]) cudaFree(st->B[i]);
   if (st->S) cudaFree(st->S);
@@ -300,6 +305,10 @@ static ed_status lz_init(const ed_basis* b, const ed_opts* o, const void* f1, cu
   }
   for (int i = 0; i < 2; ++i)
     if (cudaMemsetAsync(st->B[i], 0, st->n * st->esize, s) != cudaSuccess) return fail(ED_ERR_CUDA);
+  if (o->dtype != ED_F64_NATIVE) {
+    ed_status pr = hv2_build(b, st->fx, (int)st->ld, o->schedule, s, &st->plan);
+    if (pr != ED_OK) return fail(pr);
+  }
   LzScalars h;
   memset(&h, 0, sizeof(h));
   h.check_every = check_every < 1 ? 1 : check_every;
