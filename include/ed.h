@@ -136,6 +136,22 @@ ed_status ed_hv(const ed_basis* basis, const ed_params* params, ed_dtype dtype, 
  * the normalised FP64 values to nearest. `out` is a DEVICE array of dim elements. */
 ed_status ed_start_vector(int64_t dim, uint64_t seed, ed_dtype dtype, void* out, void* stream);
 
+/* ed_start_vector_noalloc - the same start vector as ed_start_vector, computed without
+ * allocating any device memory. The paper has no counterpart; this entry point exists for
+ * callers that must not allocate device memory while they run, for instance an application
+ * whose memory pool already owns the device, or a latency-critical loop that cannot accept
+ * the synchronisation a device allocation may cause.
+ * Its scratch (the partial sums of the squared norm) is a fixed array of 4096 doubles
+ * (32 KB) in the library's static device memory, present on every device that loads the
+ * library until the process exits. Sizes needing more partial sums than that are rejected
+ * with ED_ERR_ARG (on a GB300, 4 x 152 = 608 are used for any dim). The first call on a
+ * device looks up the array's device address with that device current; make that first
+ * call before any stream capture. All calls share the array: calls that overlap on the GPU
+ * race; consecutive calls on one stream are safe (each call writes every slot it reads).
+ * Arguments, layout and errors as ed_start_vector. */
+ed_status ed_start_vector_noalloc(int64_t dim, uint64_t seed, ed_dtype dtype, void* out,
+                                  void* stream);
+
 /* ed_lanczos_init - allocate a Lanczos state for `basis` with f_1 = f1 (a DEVICE vector of
  * dim elements of opts->dtype, normalised by the library) or, if f1 == NULL, the
  * ed_start_vector of opts->seed. The state owns its work vectors until destroy. */

@@ -56,6 +56,7 @@ _SIGS = {
     "ed_basis_destroy": (None, [c_void_p]),
     "ed_hv": (c_int, [c_void_p, POINTER(ed_params), c_int, c_void_p, c_void_p, c_void_p]),
     "ed_start_vector": (c_int, [c_int64, c_uint64, c_int, c_void_p, c_void_p]),
+    "ed_start_vector_noalloc": (c_int, [c_int64, c_uint64, c_int, c_void_p, c_void_p]),
     "ed_lanczos_init": (c_int, [c_void_p, POINTER(ed_opts), c_void_p, c_void_p, POINTER(c_void_p)]),
     "ed_lanczos_step": (c_int, [c_void_p, POINTER(ed_params), POINTER(c_double), POINTER(c_double)]),
     "ed_lanczos_run": (c_int, [c_void_p, POINTER(ed_params), c_int32, POINTER(ctypes.c_float)]),
@@ -158,6 +159,13 @@ def ed_hv(basis, t: float, U: float, x, y, stream=None) -> None:
 def ed_start_vector(dim: int, seed: int, out, stream=None) -> None:
     code = dtype_code(out.dtype)
     _check(_lib.ed_start_vector(dim, seed, code, _ptr(out, code, dim), _stream(stream)))
+
+
+def ed_start_vector_noalloc(dim: int, seed: int, out, stream=None) -> None:
+    """ed_start_vector without any device allocation (scratch in static device memory);
+    for callers that must not allocate device memory while they run."""
+    code = dtype_code(out.dtype)
+    _check(_lib.ed_start_vector_noalloc(dim, seed, code, _ptr(out, code, dim), _stream(stream)))
 
 
 # ------------------------------------------------------------------------ Lanczos

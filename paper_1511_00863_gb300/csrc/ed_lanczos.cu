@@ -14,6 +14,7 @@
 // between batches of replays.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "ed_internal.cuh"
@@ -242,6 +243,62 @@ extern "C" ed_status ed_start_vector(int64_t dim, uint64_t seed, ed_dtype dtype,
     set_error("ed_start_vector: %s", cudaGetErrorString(e));
     return ED_ERR_CUDA;
   }
+  return ED_OK;
+}
+
+// ------------------------------------------------------------------ no-allocation variant
+// Scratch of ed_start_vector_noalloc: the per-CTA partial sums of the squared norm. One
+// copy per device that loads the library, kept until the process exits; every call shares
+// it, so calls that overlap on the GPU race. Each call writes all the slots it reads, so
+// nothing needs clearing between calls.
+constexpr int kNoAllocPartials = 4096;
+static __device__ __align__(256) double g_start_partials[kNoAllocPartials];
+
+// Device address of g_start_partials on the current device (in host code the symbol names
+// a host-side stand-in, not device memory). Resolved once per device, with that device
+// current, on the first call there.
+static ed_status noalloc_scratch(double** out) {
+  static std::mutex mu;
+  static double* addr[64] = {nullptr};
+  int dev = 0;
+  ED_TRY_CUDA(cudaGetDevice(&dev));
+  ED_CHECK_ARG(dev >= 0 && dev < 64, "ed_start_vector_noalloc: device ordinal %d not supported", dev);
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_start_partials);
+    if (e != cudaSuccess || p == nullptr) {
+      set_error("ed_start_vector_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return ED_ERR_CUDA;
+    }
+    addr[dev] = (double*)p;
+  }
+  *out = addr[dev];
+  return ED_OK;
+}
+
+extern "C" ed_status ed_start_vector_noalloc(int64_t dim, uint64_t seed, ed_dtype dtype, void* out,
+                                             void* stream) {
+  clear_error();
+  ED_CHECK_ARG(dim >= 1, "ed_start_vector_noalloc: dim < 1");
+  ED_CHECK_ARG(out != nullptr && aligned16(out),
+               "ed_start_vector_noalloc: out NULL or not 16-byte aligned");
+  ED_CHECK_ARG(dtype == ED_F64 || dtype == ED_F32 || dtype == ED_F64_NATIVE,
+               "ed_start_vector_noalloc: unknown dtype");
+  const int g = red_grid(dim);
+  ED_CHECK_ARG(g <= kNoAllocPartials,
+               "ed_start_vector_noalloc: needs %d partial sums, the static scratch holds %d", g,
+               kNoAllocPartials);
+  double* part = nullptr;
+  const ed_status r = noalloc_scratch(&part);
+  if (r != ED_OK) return r;
+  cudaStream_t s = (cudaStream_t)stream;
+  start_norm_kernel<<<g, kRedThreads, 0, s>>>(seed, dim, part);
+  if (dtype != ED_F32)
+    start_write_kernel<double><<<g, kRedThreads, 0, s>>>(seed, dim, dim, dim, part, g, (double*)out);
+  else
+    start_write_kernel<float><<<g, kRedThreads, 0, s>>>(seed, dim, dim, dim, part, g, (float*)out);
+  ED_TRY_CUDA(cudaGetLastError());
   return ED_OK;
 }
 
