@@ -185,6 +185,29 @@ ed_status ed_lanczos_solve(const ed_basis* basis, const ed_params* params, const
                            const void* f1, void* stream, double* E0, int32_t* steps,
                            double* alpha, double* beta);
 
+/* ed_lanczos_solve_batched - Algorithm 1 for n independent instances (basis i with
+ * params[i], a HOST array of n) in one persistent cooperative kernel launch, captured in a
+ * CUDA graph. opts apply to every instance (dtype must be ED_F32: FP32 vectors and H.v,
+ * FP64 a_j, b_j, dot-product accumulation and tridiagonal solve; start vector of opts->seed
+ * for every instance). The convergence test of opts is evaluated every 4 steps.
+ * opts->schedule picks how instances are packed onto groups of CTAs (0..4); -1 lets the
+ * library time every schedule on this batch with a short run and keep the fastest (cached
+ * per process for the same batch shape). Outputs (HOST arrays of n, steps/status optional):
+ * E0[i], steps[i], status[i] (0 running, 1 breakdown, 2 converged, 3 max_steps) and
+ * *schedule_used. Returns ED_ERR_NOT_CONVERGED if some instance hit max_steps with tol > 0,
+ * ED_ERR_TIMEOUT if a group barrier's bounded wait ran out. Synchronises `stream`. */
+ed_status ed_lanczos_solve_batched(int32_t n, const ed_basis* const* bases,
+                                   const ed_params* params, const ed_opts* opts, void* stream,
+                                   double* E0, int32_t* steps, int32_t* status,
+                                   int32_t* schedule_used);
+
+/* ed_selftest_barrier_timeout - failure-detection self-test of the bounded group barrier
+ * used by ed_lanczos_solve_batched: a cooperative launch of `ctas` CTAs (2..64) in which
+ * the last CTA never arrives at the barrier; the others must give up after timeout_ms
+ * (1..5000) of the GPU's global timer. Returns ED_ERR_TIMEOUT when the bounded wait worked
+ * (the context stays usable), ED_OK if the barrier completed, or an error. */
+ed_status ed_selftest_barrier_timeout(int32_t ctas, int32_t timeout_ms, void* stream);
+
 /* ed_last_error - message of the last failing call on this thread ("" if none). */
 const char* ed_last_error(void);
 

@@ -65,6 +65,10 @@ _SIGS = {
     "ed_lanczos_solve": (c_int, [c_void_p, POINTER(ed_params), POINTER(ed_opts), c_void_p, c_void_p,
                                  POINTER(c_double), POINTER(c_int32), POINTER(c_double),
                                  POINTER(c_double)]),
+    "ed_lanczos_solve_batched": (c_int, [c_int32, POINTER(c_void_p), POINTER(ed_params),
+                                         POINTER(ed_opts), c_void_p, POINTER(c_double),
+                                         POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)]),
+    "ed_selftest_barrier_timeout": (c_int, [c_int32, c_int32, c_void_p]),
     "ed_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -222,6 +226,29 @@ def ed_lanczos_solve(basis, t: float, U: float, opts: ed_opts, f1=None, stream=N
         _check(s)
     n = steps.value
     return dict(status=s, E0=E0.value, steps=n, alpha=np.array(alpha[:n]), beta=np.array(beta[:n]))
+
+
+def ed_lanczos_solve_batched(bases, ts, Us, opts: ed_opts, stream=None,
+                             raise_not_converged: bool = True) -> dict:
+    """All instances in one persistent launch; ts, Us: per-instance parameters."""
+    n = len(bases)
+    arr = (c_void_p * n)(*[b.value if isinstance(b, c_void_p) else b for b in bases])
+    params = (ed_params * n)(*[ed_params(float(t), float(u)) for t, u in zip(ts, Us)])
+    E0 = (c_double * n)()
+    steps = (c_int32 * n)()
+    status = (c_int32 * n)()
+    used = c_int32()
+    s = _lib.ed_lanczos_solve_batched(n, arr, params, byref(opts), _stream(stream), E0, steps,
+                                      status, byref(used))
+    if s < 0 and not (s == ED_ERR_NOT_CONVERGED and not raise_not_converged):
+        _check(s)
+    return dict(status=s, E0=np.array(E0[:]), steps=np.array(steps[:]),
+                inst_status=np.array(status[:]), schedule=used.value)
+
+
+def ed_selftest_barrier_timeout(ctas: int = 4, timeout_ms: int = 50, stream=None) -> int:
+    """Returns the raw status: ED_ERR_TIMEOUT means the bounded wait ran out as intended."""
+    return _lib.ed_selftest_barrier_timeout(ctas, timeout_ms, _stream(stream))
 
 
 def ed_last_error() -> str:

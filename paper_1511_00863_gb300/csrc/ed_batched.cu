@@ -1,0 +1,640 @@
+// Batched Lanczos (Sec. 2.2, Algorithm 1) over many independent (lattice, filling, U)
+// instances in ONE persistent cooperative kernel launch, captured in a CUDA graph.
+//
+// Instances are packed onto groups of co-resident CTAs by a schedule (sch_*): an instance
+// whose dimension reaches a threshold gets a group of several CTAs, smaller instances run
+// one after another inside single-CTA groups (only __syncthreads needed there). Groups
+// with several CTAs synchronise through a global-memory barrier whose spin is bounded:
+// when it runs out the kernel records ED_ERR_TIMEOUT for the batch and returns.
+// Per instance and step (FP32 vectors, FP64 scalars, as the single-instance ED_F32 path):
+//   phase 1: w = s_c H B_c - b_j s_p B_p (written over B_p), partial sums of w . f_j
+//   phase 2: a_j, q = w - a_j f_j, partial sums of q . q
+//   phase 3: b_{j+1}, scale of f_{j+1}, every `check` steps E0(j) = lambda_min(T_j) by
+//            Sturm bisection (leader CTA), convergence / breakdown / max_steps.
+// Gathers read global memory directly (instances are small; their vectors stay in L2).
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ed_internal.cuh"
+#include "ed_lanczos_dev.cuh"
+
+namespace ed {
+
+constexpr int kBThreads = 256;
+
+struct BInst {
+  const uint32_t* upb;
+  const uint32_t* dnb;
+  const int32_t* hu;
+  const int32_t* hd;
+  int dim_up, dim_dn, mhu, mhd;
+  float* B0;
+  float* B1;
+  double t, U;
+};
+
+// Per-instance results and Lanczos scalars (1-based a_j, b_j like LzScalars).
+struct BState {
+  int j, status;
+  double scale[2];
+  double tscale;
+  double last_E0;
+  int last_E0_step;
+  int pad_;
+};
+
+struct BGroup {
+  int first_cta, ncta;
+  int inst_begin, inst_end;  // range in the instance order list
+};
+
+struct BArgs {
+  const BInst* inst;
+  BState* st;
+  double* alpha;  // [n_inst][max_steps + 2]
+  double* beta;   // [n_inst][max_steps + 2]
+  double* E0;     // [n_inst][max_steps + 2]
+  const int* order;
+  const BGroup* groups;
+  const int* group_of_cta;
+  double* part_a;  // [grid]
+  double* part_b;  // [grid]
+  unsigned* bar_count;  // [n_groups]
+  unsigned* bar_gen;    // [n_groups]
+  int* error;
+  int max_steps, check;
+  double tol;
+  uint64_t seed;
+  long long max_spin;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Barrier of the `g` CTAs of one group. The wait is bounded by `max_spin` nanoseconds of
+// the global timer; on expiry (or when another group already failed) it sets *error and
+// returns false, and the caller returns from the kernel.
+__device__ bool group_barrier(unsigned* count, unsigned* gen, int g, long long max_spin, int* error) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (g > 1) {
+    if (threadIdx.x == 0) {
+      int ok = 1;
+      const unsigned my_gen = atomicAdd(gen, 0u);
+      __threadfence();
+      const unsigned arrived = atomicAdd(count, 1u);
+      if (arrived == (unsigned)g - 1u) {
+        atomicExch(count, 0u);
+        __threadfence();
+        atomicAdd(gen, 1u);
+      } else {
+        const unsigned long long t0 = global_ns();
+        const long long max_iter = (max_spin >> 6) + 1000000;  // backstop if the timer stalls
+        long long it = 0;
+        while (atomicAdd(gen, 0u) == my_gen) {
+          if ((long long)(global_ns() - t0) > max_spin || ++it > max_iter ||
+              *(volatile int*)error != 0) {
+            ok = 0;
+            atomicExch(error, 1);
+            break;
+          }
+          __nanosleep(128);
+        }
+      }
+      __threadfence();
+      ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+  }
+  return true;
+}
+
+// Loads of data that other CTAs of the group wrote during this launch go to L2 (the L1 of
+// this SM is not coherent with their stores).
+__device__ __forceinline__ float ld_shared_f(const float* p, bool multi) { return multi ? __ldcg(p) : *p; }
+
+__device__ __forceinline__ double bstart_element(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  return 2.0 * ((double)(z >> 11) * 0x1.0p-53) - 1.0;
+}
+
+// Group-wide sum of the group's CTA partials (fixed order), every thread gets it.
+__device__ __forceinline__ double group_sum(const double* part, int first, int g, double* red) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < g; i += blockDim.x) v += __ldcg(part + first + i);
+  v = block_sum(v, red);
+  if (threadIdx.x == 0) red[32] = v;
+  __syncthreads();
+  v = red[32];
+  __syncthreads();
+  return v;
+}
+
+__global__ void __launch_bounds__(kBThreads)
+batched_lanczos_kernel(BArgs a) {
+  __shared__ double red[33];
+  __shared__ int stop_s;
+  const int gi = a.group_of_cta[blockIdx.x];
+  const BGroup G = a.groups[gi];
+  const int c = blockIdx.x - G.first_cta, g = G.ncta;
+  const bool leader = c == 0;
+  const bool multi = g > 1;
+  const int stride = a.max_steps + 2;
+  unsigned* bc = a.bar_count + gi;
+  unsigned* bg = a.bar_gen + gi;
+  for (int oi = G.inst_begin; oi < G.inst_end; ++oi) {
+    const int id = a.order[oi];
+    const BInst I = a.inst[id];
+    BState* S = a.st + id;
+    double* al = a.alpha + (size_t)id * stride;
+    double* be = a.beta + (size_t)id * stride;
+    double* e0 = a.E0 + (size_t)id * stride;
+    const int dim = I.dim_up * I.dim_dn;
+    const int64_t gt = (int64_t)g * blockDim.x;
+    const int64_t t0 = (int64_t)c * blockDim.x + threadIdx.x;
+    // ---- start vector: raw SplitMix64 values, FP64 norm, normalised then rounded
+    {
+      double v = 0.0;
+      for (int64_t e = t0; e < dim; e += gt) {
+        const double x = bstart_element(a.seed, (uint64_t)e);
+        v = fma(x, x, v);
+      }
+      v = block_sum(v, red);
+      if (threadIdx.x == 0) a.part_a[blockIdx.x] = v;
+      if (!group_barrier(bc, bg, g, a.max_spin, a.error)) return;
+      const double inv = 1.0 / sqrt(group_sum(a.part_a, G.first_cta, g, red));
+      for (int64_t e = t0; e < dim; e += gt) {
+        I.B0[e] = (float)(bstart_element(a.seed, (uint64_t)e) * inv);
+        I.B1[e] = 0.f;
+      }
+      if (leader && threadIdx.x == 0) {
+        S->j = 0;
+        S->status = 0;
+        S->scale[0] = 1.0;
+        S->scale[1] = 0.0;
+        S->tscale = 0.0;
+        S->last_E0_step = 0;
+        S->last_E0 = 0.0;
+        be[1] = 0.0;
+      }
+      if (!group_barrier(bc, bg, g, a.max_spin, a.error)) return;
+    }
+    int cur = 0;
+    for (int j = 1; j <= a.max_steps; ++j) {
+      float* xc = cur ? I.B1 : I.B0;
+      float* xp = cur ? I.B0 : I.B1;
+      // ---- phase 1: fused H.v
+      const float sc = (float)__ldcg(&S->scale[cur]);
+      const float bsp = (float)(__ldcg(&be[j]) * __ldcg(&S->scale[1 - cur]));
+      const float tt = (float)I.t, UU = (float)I.U;
+      DotAcc<float> dot;
+      for (int64_t e = t0; e < dim; e += gt) {
+        const int u = (int)(e / I.dim_dn), d = (int)(e - (int64_t)u * I.dim_dn);
+        const float* xr = xc + (int64_t)u * I.dim_dn;
+        float acc = 0.f;
+        for (int k = 0; k < I.mhd; ++k) {
+          const uint32_t en = (uint32_t)I.hd[(int64_t)k * I.dim_dn + d];
+          const uint32_t tg = en & kTargetMask;
+          if (tg >= (uint32_t)I.dim_dn) break;
+          const float v = ld_shared_f(xr + tg, multi);
+          acc += (en & kSignBit) ? -v : v;
+        }
+        for (int k = 0; k < I.mhu; ++k) {
+          const uint32_t en = (uint32_t)I.hu[(int64_t)k * I.dim_up + u];
+          const uint32_t tg = en & kTargetMask;
+          if (tg >= (uint32_t)I.dim_up) break;
+          const float v = ld_shared_f(xc + (int64_t)tg * I.dim_dn + d, multi);
+          acc += (en & kSignBit) ? -v : v;
+        }
+        const float xv = xr[d];
+        const float hx = fmaf(-tt, acc, UU * (float)__popc(I.upb[u] & I.dnb[d]) * xv);
+        const float w = fmaf(sc, hx, -bsp * xp[e]);
+        xp[e] = w;
+        dot.add(w, sc * xv);
+      }
+      {
+        const double v = block_sum(dot.get(), red);
+        if (threadIdx.x == 0) a.part_a[blockIdx.x] = v;
+      }
+      if (!group_barrier(bc, bg, g, a.max_spin, a.error)) return;
+      // ---- phase 2: a_j, update
+      const double alpha = group_sum(a.part_a, G.first_cta, g, red);
+      if (leader && threadIdx.x == 0) al[j] = alpha;
+      const float coef = (float)(alpha * __ldcg(&S->scale[cur]));
+      DotAcc<float> q2;
+      for (int64_t e = t0; e < dim; e += gt) {
+        const float q = xp[e] - coef * xc[e];
+        xp[e] = q;
+        q2.add(q, q);
+      }
+      {
+        const double v = block_sum(q2.get(), red);
+        if (threadIdx.x == 0) a.part_b[blockIdx.x] = v;
+      }
+      if (!group_barrier(bc, bg, g, a.max_spin, a.error)) return;
+      // ---- phase 3: b_{j+1}, E0(j), stop test (leader), then everyone reads the status
+      const double b2 = group_sum(a.part_b, G.first_cta, g, red);
+      if (leader) {
+        if (threadIdx.x == 0) {
+          const double beta = sqrt(b2);
+          const double ts = fmax(S->tscale, fabs(alpha) + be[j]);
+          S->tscale = ts;
+          be[j + 1] = beta;
+          S->j = j;
+          int st = (beta > kBreakdownRel * fmax(1.0, ts)) ? 0 : 1;
+          if (st == 0) S->scale[1 - cur] = 1.0 / beta;
+          stop_s = st;
+        }
+        __syncthreads();
+        int st = stop_s;
+        if (st != 0 || j >= a.max_steps || (j % a.check) == 0) {
+          const double E = sturm_lowest(al, be, j);
+          if (threadIdx.x == 0) {
+            e0[j] = E;
+            if (st == 0 && a.tol > 0.0 && S->last_E0_step > 0 &&
+                fabs(E - S->last_E0) <= a.tol * fmax(fabs(E), 1.0))
+              st = 2;
+            S->last_E0 = E;
+            S->last_E0_step = j;
+          }
+        }
+        if (threadIdx.x == 0) {
+          if (st == 0 && j >= a.max_steps) st = 3;
+          S->status = st;
+          __threadfence();
+        }
+      }
+      if (!group_barrier(bc, bg, g, a.max_spin, a.error)) return;
+      if (__ldcg(&S->status) != 0) break;
+      cur = 1 - cur;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ schedules
+// A schedule maps instances to CTA groups: instances with dim >= big get `gbig` CTAs,
+// with dim >= mid get `gmid` CTAs, the rest are queued on single-CTA groups; queues are
+// balanced by estimated work (dim x hops x 1), longest first.
+struct Sched {
+  int big, gbig, mid, gmid;
+};
+static const Sched kScheds[] = {
+    {1 << 30, 1, 1 << 30, 1},  // 0: one CTA per queue, everything queued
+    {200000, 8, 20000, 2},     // 1
+    {100000, 16, 10000, 4},    // 2
+    {400000, 32, 40000, 4},    // 3
+    {50000, 8, 5000, 2},       // 4
+};
+constexpr int kNumScheds = (int)(sizeof(kScheds) / sizeof(kScheds[0]));
+
+struct Plan {
+  std::vector<BGroup> groups;
+  std::vector<int> group_of_cta;
+  std::vector<int> order;
+  int grid = 0;
+};
+
+static Plan make_plan(const std::vector<long long>& work, const std::vector<int>& dims,
+                      const Sched& sc, int max_ctas) {
+  const int n = (int)dims.size();
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  std::sort(idx.begin(), idx.end(), [&](int a, int b) { return work[a] != work[b] ? work[a] > work[b] : a < b; });
+  Plan p;
+  int ctas = 0;
+  std::vector<int> big_ids, small_ids;
+  for (int i : idx) {
+    const int gsz = dims[i] >= sc.big ? sc.gbig : (dims[i] >= sc.mid ? sc.gmid : 1);
+    if (gsz > 1 && ctas + gsz <= max_ctas / 2) {
+      BGroup G{ctas, gsz, (int)p.order.size(), (int)p.order.size() + 1};
+      p.order.push_back(i);
+      p.groups.push_back(G);
+      ctas += gsz;
+    } else {
+      small_ids.push_back(i);
+    }
+  }
+  // single-CTA queues for the rest: as many queues as CTAs remain, longest-processing-first
+  int nq = std::max(1, std::min((int)small_ids.size(), max_ctas - ctas));
+  std::vector<std::vector<int>> q(nq);
+  std::vector<long long> load(nq, 0);
+  for (int i : small_ids) {
+    int best = 0;
+    for (int k = 1; k < nq; ++k)
+      if (load[k] < load[best]) best = k;
+    q[best].push_back(i);
+    load[best] += work[i];
+  }
+  for (int k = 0; k < nq; ++k) {
+    if (q[k].empty()) continue;
+    BGroup G{ctas, 1, (int)p.order.size(), (int)p.order.size() + (int)q[k].size()};
+    for (int i : q[k]) p.order.push_back(i);
+    p.groups.push_back(G);
+    ctas += 1;
+  }
+  p.grid = ctas;
+  p.group_of_cta.resize(ctas);
+  for (int gi = 0; gi < (int)p.groups.size(); ++gi)
+    for (int c = 0; c < p.groups[gi].ncta; ++c) p.group_of_cta[p.groups[gi].first_cta + c] = gi;
+  return p;
+}
+
+// Autotuned schedule per batch signature (dims and hop counts), cached per process.
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tune_cache;
+
+}  // namespace ed
+
+using namespace ed;
+
+namespace {
+
+struct BatchRun {
+  int n = 0;
+  std::vector<BInst> hinst;
+  std::vector<int> dims;
+  std::vector<long long> work;
+  float* vec = nullptr;
+  BInst* d_inst = nullptr;
+  BState* d_state = nullptr;
+  double* d_scal = nullptr;  // alpha | beta | E0
+  int* d_misc = nullptr;     // error flag
+  ~BatchRun() {
+    if (vec) cudaFree(vec);
+    if (d_inst) cudaFree(d_inst);
+    if (d_state) cudaFree(d_state);
+    if (d_scal) cudaFree(d_scal);
+    if (d_misc) cudaFree(d_misc);
+  }
+};
+
+struct PlanDev {
+  BGroup* groups = nullptr;
+  int* goc = nullptr;
+  int* order = nullptr;
+  double* part = nullptr;
+  unsigned* bar = nullptr;
+  ~PlanDev() {
+    if (groups) cudaFree(groups);
+    if (goc) cudaFree(goc);
+    if (order) cudaFree(order);
+    if (part) cudaFree(part);
+    if (bar) cudaFree(bar);
+  }
+};
+
+ed_status upload_plan(const Plan& p, PlanDev& d, cudaStream_t s) {
+  ED_TRY_CUDA(cudaMalloc((void**)&d.groups, p.groups.size() * sizeof(BGroup)));
+  ED_TRY_CUDA(cudaMalloc((void**)&d.goc, p.group_of_cta.size() * sizeof(int)));
+  ED_TRY_CUDA(cudaMalloc((void**)&d.order, p.order.size() * sizeof(int)));
+  ED_TRY_CUDA(cudaMalloc((void**)&d.part, 2 * (size_t)p.grid * sizeof(double)));
+  ED_TRY_CUDA(cudaMalloc((void**)&d.bar, 2 * p.groups.size() * sizeof(unsigned)));
+  ED_TRY_CUDA(cudaMemcpyAsync(d.groups, p.groups.data(), p.groups.size() * sizeof(BGroup), cudaMemcpyHostToDevice, s));
+  ED_TRY_CUDA(cudaMemcpyAsync(d.goc, p.group_of_cta.data(), p.group_of_cta.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  ED_TRY_CUDA(cudaMemcpyAsync(d.order, p.order.data(), p.order.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  ED_TRY_CUDA(cudaMemsetAsync(d.bar, 0, 2 * p.groups.size() * sizeof(unsigned), s));
+  return ED_OK;
+}
+
+// One cooperative launch of the whole batch, captured in a CUDA graph and replayed once.
+ed_status run_plan(BatchRun& R, const Plan& p, const ed_opts* o, int check, cudaStream_t s,
+                   float* ms_out) {
+  PlanDev d;
+  ed_status st = upload_plan(p, d, s);
+  if (st != ED_OK) return st;
+  ED_TRY_CUDA(cudaMemsetAsync(R.d_misc, 0, sizeof(int), s));
+  BArgs a;
+  a.inst = R.d_inst;
+  a.st = R.d_state;
+  const size_t stride = (size_t)o->max_steps + 2;
+  a.alpha = R.d_scal;
+  a.beta = R.d_scal + stride * R.n;
+  a.E0 = R.d_scal + 2 * stride * R.n;
+  a.order = d.order;
+  a.groups = d.groups;
+  a.group_of_cta = d.goc;
+  a.part_a = d.part;
+  a.part_b = d.part + p.grid;
+  a.bar_count = d.bar;
+  a.bar_gen = d.bar + p.groups.size();
+  a.error = R.d_misc;
+  a.max_steps = o->max_steps;
+  a.check = check;
+  a.tol = o->tol;
+  a.seed = o->seed;
+  a.max_spin = 1000000000LL;  // a group barrier waits at most 1 s
+  void* args[] = {&a};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ED_TRY_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  cudaError_t le = cudaLaunchCooperativeKernel((const void*)batched_lanczos_kernel, p.grid,
+                                               kBThreads, args, 0, s);
+  cudaError_t ce = cudaStreamEndCapture(s, &graph);
+  if (le != cudaSuccess || ce != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    set_error("batched Lanczos: capture of the cooperative launch failed: %s",
+              cudaGetErrorString(le != cudaSuccess ? le : ce));
+    return ED_ERR_CUDA;
+  }
+  cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) {
+    set_error("batched Lanczos: graph instantiate failed: %s", cudaGetErrorString(ie));
+    return ED_ERR_CUDA;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  cudaError_t ge = cudaGraphLaunch(exec, s);
+  cudaEventRecord(e1, s);
+  cudaError_t se = cudaStreamSynchronize(s);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGraphExecDestroy(exec);
+  if (ge != cudaSuccess || se != cudaSuccess) {
+    set_error("batched Lanczos: %s", cudaGetErrorString(ge != cudaSuccess ? ge : se));
+    return ED_ERR_CUDA;
+  }
+  int err = 0;
+  ED_TRY_CUDA(cudaMemcpy(&err, R.d_misc, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    set_error("batched Lanczos: a group barrier timed out");
+    return ED_ERR_TIMEOUT;
+  }
+  if (ms_out) *ms_out = ms;
+  return ED_OK;
+}
+
+}  // namespace
+
+namespace ed {
+// Self-test kernel of the bounded group barrier: CTA `absent` never arrives, so the other
+// CTAs of the group must give up after `limit_ns` and flag the error.
+__global__ void barrier_selftest_kernel(unsigned* bar, int* error, int absent, long long limit_ns) {
+  if ((int)blockIdx.x == absent) return;
+  group_barrier(bar, bar + 1, gridDim.x, limit_ns, error);
+}
+}  // namespace ed
+
+extern "C" ed_status ed_selftest_barrier_timeout(int32_t ctas, int32_t timeout_ms, void* stream) {
+  clear_error();
+  ED_CHECK_ARG(ctas >= 2 && ctas <= 64 && timeout_ms >= 1 && timeout_ms <= 5000,
+               "ed_selftest_barrier_timeout: ctas in [2, 64], timeout_ms in [1, 5000]");
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned* bar = nullptr;
+  int* err = nullptr;
+  ED_TRY_CUDA(cudaMallocAsync((void**)&bar, 2 * sizeof(unsigned), s));
+  ED_TRY_CUDA(cudaMallocAsync((void**)&err, sizeof(int), s));
+  ED_TRY_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
+  ED_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  int absent = ctas - 1;
+  long long limit = (long long)timeout_ms * 1000000LL;
+  void* args[] = {&bar, &err, &absent, &limit};
+  ED_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)barrier_selftest_kernel, ctas, 32, args, 0, s));
+  int h = 0;
+  ED_TRY_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  ED_TRY_CUDA(cudaStreamSynchronize(s));
+  cudaFreeAsync(bar, s);
+  cudaFreeAsync(err, s);
+  if (h) {
+    set_error("group barrier wait ran out after %d ms (as the self-test intends)", timeout_ms);
+    return ED_ERR_TIMEOUT;
+  }
+  return ED_OK;
+}
+
+extern "C" ed_status ed_lanczos_solve_batched(int32_t n, const ed_basis* const* bases,
+                                              const ed_params* params, const ed_opts* o,
+                                              void* stream, double* E0, int32_t* steps,
+                                              int32_t* status, int32_t* schedule_used) {
+  clear_error();
+  ED_CHECK_ARG(n >= 1 && bases && params && o && E0, "ed_lanczos_solve_batched: bad arguments");
+  ED_CHECK_ARG(o->dtype == ED_F32, "ed_lanczos_solve_batched: dtype must be ED_F32");
+  ED_CHECK_ARG(o->max_steps >= 1 && o->max_steps <= ED_MAX_STEPS, "max_steps out of range");
+  ED_CHECK_ARG(o->schedule >= -1 && o->schedule < kNumScheds, "schedule %d out of range", o->schedule);
+  cudaStream_t user = (cudaStream_t)stream;
+  cudaStream_t s = nullptr;
+  ED_TRY_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  struct StreamGuard {
+    cudaStream_t s;
+    ~StreamGuard() { cudaStreamDestroy(s); }
+  } guard{s};
+  {
+    cudaEvent_t ev;
+    ED_TRY_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaEventRecord(ev, user);
+    cudaStreamWaitEvent(s, ev, 0);
+    cudaEventDestroy(ev);
+  }
+  BatchRun R;
+  R.n = n;
+  R.hinst.resize(n);
+  R.dims.resize(n);
+  R.work.resize(n);
+  size_t total = 0;
+  for (int i = 0; i < n; ++i) {
+    const ed_basis* b = bases[i];
+    ED_CHECK_ARG(b != nullptr, "ed_lanczos_solve_batched: basis %d is NULL", i);
+    ED_CHECK_ARG(b->dim < (1LL << 31), "ed_lanczos_solve_batched: instance %d too large", i);
+    R.dims[i] = (int)b->dim;
+    R.work[i] = (long long)b->dim * (b->up.maxhops + b->dn.maxhops + 4);
+    total += 2 * (size_t)((b->dim + 3) / 4 * 4);
+  }
+  ED_TRY_CUDA(cudaMalloc((void**)&R.vec, total * sizeof(float)));
+  size_t off = 0;
+  for (int i = 0; i < n; ++i) {
+    const ed_basis* b = bases[i];
+    BInst& I = R.hinst[i];
+    I.upb = b->up.bits;
+    I.dnb = b->dn.bits;
+    I.hu = b->up.hop;
+    I.hd = b->dn.hop;
+    I.dim_up = (int)b->up.dim;
+    I.dim_dn = (int)b->dn.dim;
+    I.mhu = b->up.maxhops;
+    I.mhd = b->dn.maxhops;
+    const size_t dpad = (size_t)(b->dim + 3) / 4 * 4;
+    I.B0 = R.vec + off;
+    I.B1 = R.vec + off + dpad;
+    off += 2 * dpad;
+    I.t = params[i].t;
+    I.U = params[i].U;
+  }
+  const size_t stride = (size_t)o->max_steps + 2;
+  ED_TRY_CUDA(cudaMalloc((void**)&R.d_inst, n * sizeof(BInst)));
+  ED_TRY_CUDA(cudaMalloc((void**)&R.d_state, n * sizeof(BState)));
+  ED_TRY_CUDA(cudaMalloc((void**)&R.d_scal, 3 * stride * n * sizeof(double)));
+  ED_TRY_CUDA(cudaMalloc((void**)&R.d_misc, sizeof(int)));
+  ED_TRY_CUDA(cudaMemcpyAsync(R.d_inst, R.hinst.data(), n * sizeof(BInst), cudaMemcpyHostToDevice, s));
+  ED_TRY_CUDA(cudaMemsetAsync(R.d_scal, 0, 3 * stride * n * sizeof(double), s));
+
+  int dev = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  ED_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_lanczos_kernel,
+                                                            kBThreads, 0));
+  const int max_ctas = sm_count() * std::min(per_sm, 4);
+  const int check = 4;  // E0(j) every 4 steps (and at the stop step)
+  int sched = o->schedule;
+  if (sched < 0) {
+    // autotune: time every candidate schedule on this batch with a short run, keep the best
+    std::string key;
+    for (int i = 0; i < n; ++i) key += std::to_string(R.work[i]) + ",";
+    key += std::to_string(max_ctas);
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) sched = it->second;
+    }
+    if (sched < 0) {
+      ed_opts ot = *o;
+      ot.max_steps = std::min(o->max_steps, 12);
+      ot.tol = 0.0;
+      float best = 1e30f;
+      for (int k = 0; k < kNumScheds; ++k) {
+        const Plan p = make_plan(R.work, R.dims, kScheds[k], max_ctas);
+        float ms = 0.f;
+        ed_status r = run_plan(R, p, &ot, ot.max_steps, s, &ms);
+        if (r != ED_OK) return r;
+        if (ms < best) best = ms, sched = k;
+      }
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune_cache[key] = sched;
+    }
+  }
+  const Plan p = make_plan(R.work, R.dims, kScheds[sched], max_ctas);
+  float ms = 0.f;
+  ed_status r = run_plan(R, p, o, check, s, &ms);
+  if (r != ED_OK) return r;
+  std::vector<BState> hs(n);
+  std::vector<double> hE(stride * n);
+  ED_TRY_CUDA(cudaMemcpy(hs.data(), R.d_state, n * sizeof(BState), cudaMemcpyDeviceToHost));
+  ED_TRY_CUDA(cudaMemcpy(hE.data(), R.d_scal + 2 * stride * n, stride * n * sizeof(double), cudaMemcpyDeviceToHost));
+  bool all_conv = true;
+  for (int i = 0; i < n; ++i) {
+    const int j = hs[i].j;
+    E0[i] = j >= 1 ? hE[(size_t)i * stride + j] : NAN;
+    if (steps) steps[i] = j;
+    if (status) status[i] = hs[i].status;
+    if (hs[i].status == 3 && o->tol > 0.0) all_conv = false;
+  }
+  if (schedule_used) *schedule_used = sched;
+  if (!all_conv) {
+    set_error("ed_lanczos_solve_batched: some instances reached max_steps before converging");
+    return ED_ERR_NOT_CONVERGED;
+  }
+  return ED_OK;
+}

@@ -11,16 +11,27 @@ constexpr int kRedThreads = 256;
 constexpr double kBreakdownRel = 1e-13;
 
 // ------------------------------------------------------------------ Sturm bisection
-// Number of eigenvalues of T_m below x (a: 1-based diagonal a[1..m], b: b[2..m]):
-// negative pivots of the LDL^T factorisation of T - x I.
+// Number of eigenvalues of T_m below x (a: 1-based diagonal a[1..m], b: b[2..m]) = number
+// of sign changes in the Sturm sequence p_0 = 1, p_i = (a_i - x) p_{i-1} - b_i^2 p_{i-2}
+// (p_i = det of the leading i x i block of T - x I). The pair (p_{i-1}, p_i) is rescaled by
+// exact powers of two to stay in range, so no division is needed; a zero p_i is given the
+// sign opposite to p_{i-1} (a vanishing pivot counted as negative).
 __device__ __forceinline__ int sturm_count(const double* a, const double* b, int m, double x) {
   int cnt = 0;
-  double d = 1.0;
+  double p2 = 0.0, p1 = 1.0;
   for (int i = 1; i <= m; ++i) {
-    const double off = (i > 1) ? b[i] * b[i] / d : 0.0;
-    d = (a[i] - x) - off;
-    if (d == 0.0) d = -2.2250738585072014e-308;
-    cnt += d < 0.0;
+    const double b2 = (i > 1) ? b[i] * b[i] : 0.0;
+    double p = fma(a[i] - x, p1, -b2 * p2);
+    if (p == 0.0) p = p1 > 0.0 ? -0x1.0p-1000 : 0x1.0p-1000;
+    cnt += (p < 0.0) != (p1 < 0.0);
+    p2 = p1;
+    p1 = p;
+    const int e = (int)((__double_as_longlong(p1) >> 52) & 0x7FF);
+    if (e > 1023 + 400 || e < 1023 - 400) {  // keep |p| near 1: scale both by 2^-(e-1023)
+      const int sh = 1023 - e;
+      p1 = ldexp(p1, sh);
+      p2 = ldexp(p2, sh);
+    }
   }
   return cnt;
 }

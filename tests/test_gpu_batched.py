@@ -1,0 +1,110 @@
+"""Batched persistent Lanczos (FP32 vectors, FP64 scalars) against the oracle, closed forms,
+the single-instance FP64-accurate solver, and across schedules; bounded-barrier self-test."""
+import math
+
+import numpy as np
+import pytest
+
+import ed_inputs
+from oracle import dense, hamiltonian, lanczos as olz
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-6
+
+
+@pytest.fixture(scope="module")
+def ed():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1511_00863_gb300 as m
+    return m
+
+
+def _dim(w):
+    return math.comb(w["n_sites"], w["n_up"]) * math.comb(w["n_sites"], w["n_dn"])
+
+
+def _oracle_E0(w):
+    L, b, nu, nd, t, U = w["n_sites"], w["bonds"], w["n_up"], w["n_dn"], w["t"], w["U"]
+    if _dim(w) <= 2000:
+        return dense.spectrum(L, b, nu, nd, t, U)[0]
+    H = hamiltonian.hamiltonian_csr(L, b, nu, nd, t, U)
+    f1 = olz.normalized_start(ed_inputs.start_vector_raw(9, H.shape[0]))
+    return olz.lanczos(lambda v: H @ v, f1, max_steps=400, tol=1e-14, reorth=False).E0
+
+
+def _run(ed, insts, schedule=-1, max_steps=400, tol=1e-9):
+    bases = [ed.ed_build_basis(w["n_sites"], w["bonds"], w["n_up"], w["n_dn"]) for w in insts]
+    try:
+        return ed.ed_lanczos_solve_batched(bases, [w["t"] for w in insts], [w["U"] for w in insts],
+                                           ed.make_opts(max_steps=max_steps, tol=tol, seed=4,
+                                                        dtype="f32", schedule=schedule),
+                                           raise_not_converged=False)
+    finally:
+        for b in bases:
+            ed.ed_basis_destroy(b)
+
+
+def test_batched_small_instances_vs_oracle(ed):
+    insts = [w for w in ed_inputs.batched_instances() if _dim(w) <= 6000][:40]
+    res = _run(ed, insts)
+    for w, E in zip(insts, res["E0"]):
+        ref = _oracle_E0(w)
+        assert abs(E - ref) <= TOL32 * max(1.0, abs(ref)), (w["name"], w["n_up"], w["n_dn"], E, ref)
+
+
+def test_batched_U0_closed_forms(ed):
+    insts = []
+    for L in (8, 10, 12):
+        for nu, nd in ((1, 2), (3, 3), (2, 4)):
+            insts.append(dict(n_sites=L, bonds=ed_inputs.ring_bonds(L), n_up=nu, n_dn=nd, t=1.0, U=0.0))
+    insts.append(dict(n_sites=12, bonds=ed_inputs.torus_bonds(3, 4), n_up=6, n_dn=6, t=1.0, U=0.0))
+    res = _run(ed, insts)
+    for w, E in zip(insts, res["E0"]):
+        h = np.zeros((w["n_sites"],) * 2)
+        for i, j in w["bonds"]:
+            h[i, j] -= 1
+            h[j, i] -= 1
+        eps = np.linalg.eigvalsh(h)
+        ref = eps[:w["n_up"]].sum() + eps[:w["n_dn"]].sum()
+        assert abs(E - ref) <= TOL32 * max(1.0, abs(ref)), (w, E, ref)
+
+
+def test_batched_full_workload_vs_fp64_solver(ed):
+    """All 256 instances in one launch; the largest ones checked against the single-instance
+    FP64-accurate solver (itself pinned to the oracle), a sample of small ones against the
+    oracle."""
+    insts = ed_inputs.batched_instances()
+    res = _run(ed, insts)
+    assert res["status"] in (0, ed.ED_ERR_NOT_CONVERGED)
+    order = np.argsort([_dim(w) for w in insts])
+    big = order[-6:]
+    for i in big:
+        w = insts[i]
+        b = ed.ed_build_basis(w["n_sites"], w["bonds"], w["n_up"], w["n_dn"])
+        try:
+            ref = ed.ed_lanczos_solve(b, w["t"], w["U"], ed.make_opts(max_steps=400, tol=1e-12, seed=4),
+                                      raise_not_converged=False)["E0"]
+        finally:
+            ed.ed_basis_destroy(b)
+        assert abs(res["E0"][i] - ref) <= TOL32 * max(1.0, abs(ref)), (i, res["E0"][i], ref)
+    for i in order[:20]:
+        ref = _oracle_E0(insts[i])
+        assert abs(res["E0"][i] - ref) <= TOL32 * max(1.0, abs(ref))
+
+
+def test_batched_schedules_agree(ed):
+    insts = ed_inputs.batched_instances()[:48]
+    out = [_run(ed, insts, schedule=s)["E0"] for s in range(5)]
+    for s in range(1, 5):
+        assert np.allclose(out[s], out[0], rtol=TOL32, atol=TOL32)
+
+
+def test_group_barrier_wait_is_bounded(ed):
+    st = ed.ed_selftest_barrier_timeout(ctas=4, timeout_ms=50)
+    assert st == ed.ED_ERR_TIMEOUT
+    # the context is still usable afterwards
+    x = torch.ones(16, device="cuda")
+    assert float(x.sum()) == 16.0
