@@ -201,6 +201,55 @@ ed_status ed_lanczos_solve_batched(int32_t n, const ed_basis* const* bases,
                                    double* E0, int32_t* steps, int32_t* status,
                                    int32_t* schedule_used);
 
+/* ed_lanczos_ground_state - the ground-state vector: Algorithm 1 to convergence (ED_F64
+ * only), the eigenvector y of T_m for its lowest eigenvalue (inverse iteration on the
+ * device), then the same Lanczos vectors regenerated from f1 and summed, psi = sum_j y_j
+ * f_j, exactly in int64 fixed point. psi: DEVICE array of dim FP64, normalised, with the
+ * sign fixed so that its largest-magnitude entry (lowest index on ties) is positive. E0 and
+ * steps as ed_lanczos_solve. The paper computes E0 only (Sec. 2.2); the vector is the
+ * training data of the learned start vector. */
+ed_status ed_lanczos_ground_state(const ed_basis* basis, const ed_params* params,
+                                  const ed_opts* opts, const void* f1, void* stream, double* psi,
+                                  double* E0, int32_t* steps);
+
+/* ---------------------------------------------------------------- learned start vector
+ * A small network predicts the ground-state amplitude of a basis state from its occupation
+ * bits and U; its predictions over the basis are used as f_1 of Algorithm 1 (no counterpart
+ * in the paper). Inputs x = (up bits, down bits, U/8) (2L+1 values); two hidden layers of 64
+ * tanh units; outputs (a, z); predicted amplitude sign(z) exp(a). Parameters are an FP32
+ * master copy, rounded to bfloat16 for every forward pass, FP32 accumulation. Layout (flat):
+ * W1 [(2L+1) x 64] input-major, b1 [64], W2 [64 x 64], b2 [64], W3 [64 x 2], b3 [2]. */
+typedef struct ed_mlp ed_mlp;
+
+/* ed_mlp_create - network for n_sites-site lattices, Glorot-uniform weights from SplitMix64
+ * `seed`, zero biases, zero Adam moments; all work of the handle goes to `stream`. */
+ed_status ed_mlp_create(int32_t n_sites, uint64_t seed, void* stream, ed_mlp** out);
+
+/* ed_mlp_params - DEVICE pointer to the FP32 master parameters (read/write) and their count. */
+ed_status ed_mlp_params(ed_mlp* mlp, float** params, int64_t* count);
+
+/* ed_mlp_loss_grad - loss of the batch (states idx[n], DEVICE int64 global indices of `basis`;
+ * target amplitudes target[n], DEVICE FP64) with per-sample weight weight_scale * target^2:
+ *   L = (1/n) sum_k w_k [(a_k - log|t_k|)^2 + log(1 + exp(-sign(t_k) z_k))]  (t_k = 0 skipped)
+ * *loss (HOST) and *grad (DEVICE, parameter layout, valid until the next call on the handle)
+ * = dL/d(rounded weights). Synchronises the handle's stream when loss != NULL. */
+ed_status ed_mlp_loss_grad(ed_mlp* mlp, const ed_basis* basis, double U, const int64_t* idx,
+                           const double* target, int64_t n, double weight_scale, double* loss,
+                           const float** grad);
+
+/* ed_mlp_train_step - one Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on
+ * `batch` basis states drawn uniformly (SplitMix64 `seed`) with targets from psi (DEVICE FP64
+ * ground-state vector of `basis` at interaction U) and weight_scale = dim. *loss (HOST,
+ * optional) = the batch loss before the step. */
+ed_status ed_mlp_train_step(ed_mlp* mlp, const ed_basis* basis, double U, const double* psi,
+                            int64_t batch, double lr, uint64_t seed, double* loss);
+
+/* ed_mlp_infer - out[i] = predicted amplitude of basis state i at interaction U, for every
+ * state of `basis` (DEVICE array of dim, FP32 for ED_F32 else FP64; not normalised). */
+ed_status ed_mlp_infer(ed_mlp* mlp, const ed_basis* basis, double U, ed_dtype dtype, void* out);
+
+void ed_mlp_destroy(ed_mlp* mlp);
+
 /* ed_selftest_barrier_timeout - failure-detection self-test of the bounded group barrier
  * used by ed_lanczos_solve_batched: a cooperative launch of `ctas` CTAs (2..64) in which
  * the last CTA never arrives at the barrier; the others must give up after timeout_ms

@@ -69,6 +69,16 @@ _SIGS = {
                                          POINTER(ed_opts), c_void_p, POINTER(c_double),
                                          POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)]),
     "ed_selftest_barrier_timeout": (c_int, [c_int32, c_int32, c_void_p]),
+    "ed_lanczos_ground_state": (c_int, [c_void_p, POINTER(ed_params), POINTER(ed_opts), c_void_p,
+                                        c_void_p, c_void_p, POINTER(c_double), POINTER(c_int32)]),
+    "ed_mlp_create": (c_int, [c_int32, c_uint64, c_void_p, POINTER(c_void_p)]),
+    "ed_mlp_params": (c_int, [c_void_p, POINTER(c_void_p), POINTER(c_int64)]),
+    "ed_mlp_loss_grad": (c_int, [c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_int64,
+                                 c_double, POINTER(c_double), POINTER(c_void_p)]),
+    "ed_mlp_train_step": (c_int, [c_void_p, c_void_p, c_double, c_void_p, c_int64, c_double,
+                                  c_uint64, POINTER(c_double)]),
+    "ed_mlp_infer": (c_int, [c_void_p, c_void_p, c_double, c_int, c_void_p]),
+    "ed_mlp_destroy": (None, [c_void_p]),
     "ed_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -249,6 +259,58 @@ def ed_lanczos_solve_batched(bases, ts, Us, opts: ed_opts, stream=None,
 def ed_selftest_barrier_timeout(ctas: int = 4, timeout_ms: int = 50, stream=None) -> int:
     """Returns the raw status: ED_ERR_TIMEOUT means the bounded wait ran out as intended."""
     return _lib.ed_selftest_barrier_timeout(ctas, timeout_ms, _stream(stream))
+
+
+def ed_lanczos_ground_state(basis, t: float, U: float, opts: ed_opts, psi, f1=None,
+                            stream=None, raise_not_converged: bool = True) -> dict:
+    dim = ed_basis_dims(basis)[2]
+    p = ed_params(t, U)
+    E0, steps = c_double(), c_int32()
+    s = _lib.ed_lanczos_ground_state(basis, byref(p), byref(opts), _ptr(f1, ED_F64, dim),
+                                     _stream(stream), _ptr(psi, ED_F64, dim), byref(E0), byref(steps))
+    if s < 0 and not (s == ED_ERR_NOT_CONVERGED and not raise_not_converged):
+        _check(s)
+    return dict(status=s, E0=E0.value, steps=steps.value)
+
+
+def ed_mlp_create(n_sites: int, seed: int, stream=None) -> c_void_p:
+    out = c_void_p()
+    _check(_lib.ed_mlp_create(n_sites, seed, _stream(stream), byref(out)))
+    return out
+
+
+def ed_mlp_params(mlp):
+    """(device pointer, count) of the FP32 master parameters."""
+    p, n = c_void_p(), c_int64()
+    _check(_lib.ed_mlp_params(mlp, byref(p), byref(n)))
+    return p.value, n.value
+
+
+def ed_mlp_loss_grad(mlp, basis, U: float, idx, target, weight_scale: float):
+    """Returns (loss, device pointer of the gradient)."""
+    n = idx.numel()
+    loss, g = c_double(), c_void_p()
+    if target.numel() != n or idx.dtype.itemsize != 8:
+        raise ValueError("idx (int64) and target (float64) must have the same length")
+    _check(_lib.ed_mlp_loss_grad(mlp, basis, U, _ptr(idx), _ptr(target, ED_F64, n), n,
+                                 weight_scale, byref(loss), byref(g)))
+    return loss.value, g.value
+
+
+def ed_mlp_train_step(mlp, basis, U: float, psi, batch: int, lr: float, seed: int) -> float:
+    loss = c_double()
+    _check(_lib.ed_mlp_train_step(mlp, basis, U, _ptr(psi, ED_F64), batch, lr, seed, byref(loss)))
+    return loss.value
+
+
+def ed_mlp_infer(mlp, basis, U: float, out) -> None:
+    code = dtype_code(out.dtype)
+    dim = ed_basis_dims(basis)[2]
+    _check(_lib.ed_mlp_infer(mlp, basis, U, code, _ptr(out, code, dim)))
+
+
+def ed_mlp_destroy(mlp) -> None:
+    _lib.ed_mlp_destroy(mlp)
 
 
 def ed_last_error() -> str:

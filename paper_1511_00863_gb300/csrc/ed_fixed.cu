@@ -404,6 +404,99 @@ fx_finish_kernel(LzScalars* S, int cur, const long long* __restrict__ pb, int nb
   finish_tail(S, j, stop_s);
 }
 
+// ------------------------------------------------------------------ ground-state vector
+// psi = sum_j y_j f_j accumulated in int64 with psi = 2^-60 P (|psi_i| stays below 4):
+// P_i += round(c X_i 2^k) with c 2^k = y_j s_cur 2^60. Also tracks the index of the
+// largest |P| (ties: lowest index) for the sign gauge.
+__global__ void __launch_bounds__(kFxThreads)
+fx_psi_accum_kernel(const LzScalars* __restrict__ S, int cur, const double* __restrict__ y, int jstep,
+                    const long long* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
+                    long long* __restrict__ P) {
+  const double c = y[jstep] * S->scale[cur] * 0x1.0p60;
+  long long m = 0;
+  int k = -1;
+  if (c != 0.0 && isfinite(c)) {
+    k = ilogb(c) - 61;
+    m = llrint(ldexp(c, -k));
+  }
+  const int64_t n = rows * cols;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / cols, cc = i - r * cols;
+    P[i] += round_shift((i128)m * X[r * ld + cc], k);
+  }
+}
+
+// Largest |P_i| and its lowest index: partial records (value, index) per CTA.
+__global__ void __launch_bounds__(kFxThreads)
+fx_psi_argmax_kernel(const long long* __restrict__ P, int64_t n, long long* __restrict__ part) {
+  __shared__ long long sv[kFxThreads];
+  __shared__ long long si[kFxThreads];
+  long long bv = -1, bi = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const long long v = P[i] < 0 ? -P[i] : P[i];
+    if (v > bv) {
+      bv = v;
+      bi = i;
+    }
+  }
+  sv[threadIdx.x] = bv;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      const long long v2 = sv[threadIdx.x + o], i2 = si[threadIdx.x + o];
+      if (v2 > sv[threadIdx.x] || (v2 == sv[threadIdx.x] && i2 < si[threadIdx.x])) {
+        sv[threadIdx.x] = v2;
+        si[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = sv[0];
+    part[2 * blockIdx.x + 1] = si[0];
+  }
+}
+
+// psi (FP64) = gauge * P 2^-60 / ||P 2^-60||, gauge making the largest entry positive.
+__global__ void __launch_bounds__(kFxThreads)
+fx_psi_out_kernel(const long long* __restrict__ P, int64_t n, const long long* __restrict__ amax,
+                  int namax, const long long* __restrict__ nrm_part, int nn, double* __restrict__ out) {
+  __shared__ long long best_i;
+  if (threadIdx.x == 0) {
+    long long bv = -1, bi = 0;
+    for (int b = 0; b < namax; ++b) {
+      const long long v = amax[2 * b], i = amax[2 * b + 1];
+      if (v > bv || (v == bv && i < bi)) {
+        bv = v;
+        bi = i;
+      }
+    }
+    best_i = bi;
+  }
+  I192 sum;
+  long long unused;
+  fx_sum_partials(nrm_part, nn, sum, unused);
+  const double nrm = sqrt(i192_to_double(sum));
+  const double g = (P[best_i] < 0 ? -1.0 : 1.0) / nrm;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (double)P[i] * g;
+}
+
+// Partial sums of P_i^2 (exact).
+__global__ void __launch_bounds__(kFxThreads)
+fx_psi_norm_kernel(const long long* __restrict__ P, int64_t n, long long* __restrict__ part) {
+  I192 acc;
+  i192_zero(acc);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    i192_add(acc, (i128)P[i] * P[i]);
+  fx_block_reduce(acc, 0, part + 4 * blockIdx.x);
+}
+
 // ------------------------------------------------------------------ host side
 static int fx_red_grid(int64_t n) {
   const int64_t want = (n + kFxThreads - 1) / kFxThreads;
@@ -442,6 +535,24 @@ static int fx_rows(const ed_basis* b) {
   if (fx_smem<2>(b) <= lim && b->up.dim >= 2) return 2;
   if (fx_smem<1>(b) <= lim) return 1;
   return 0;
+}
+
+ed_status fx_psi_accum(const ed_basis* b, const LzScalars* S, int cur, const double* y, int j,
+                       const long long* X, int64_t ld, long long* P, cudaStream_t s) {
+  fx_psi_accum_kernel<<<fx_red_grid(b->dim), kFxThreads, 0, s>>>(S, cur, y, j, X, b->up.dim,
+                                                                  b->dn.dim, ld, P);
+  ED_TRY_CUDA(cudaGetLastError());
+  return ED_OK;
+}
+
+ed_status fx_psi_finish(const ed_basis* b, const long long* P, long long* part, double* out,
+                        cudaStream_t s) {
+  const int g = fx_red_grid(b->dim);
+  fx_psi_argmax_kernel<<<g, kFxThreads, 0, s>>>(P, b->dim, part);
+  fx_psi_norm_kernel<<<g, kFxThreads, 0, s>>>(P, b->dim, part + 2 * g);
+  fx_psi_out_kernel<<<g, kFxThreads, 0, s>>>(P, b->dim, part, g, part + 2 * g, g, out);
+  ED_TRY_CUDA(cudaGetLastError());
+  return ED_OK;
 }
 
 ed_status fx_prepare(const ed_basis* b) {

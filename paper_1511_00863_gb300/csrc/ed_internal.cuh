@@ -129,6 +129,12 @@ ed_status fx_step(const ed_basis* b, const FxRun& fx, double t, double U, long l
                   int cur, int64_t ld, LzScalars* S, long long* pa, long long* pb,
                   cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, const struct Hv2Plan* plan);
 ed_status fx_prepare(const ed_basis* b);
+// Ground-state vector (ed_lanczos_ground_state): P += round(y_j scale[cur] 2^60 X_cur),
+// and the final normalised, sign-gauged FP64 vector. part: >= 6 * 4 * sm_count longs.
+ed_status fx_psi_accum(const ed_basis* b, const LzScalars* S, int cur, const double* y, int j,
+                       const long long* X, int64_t ld, long long* P, cudaStream_t s);
+ed_status fx_psi_finish(const ed_basis* b, const long long* P, long long* part, double* out,
+                        cudaStream_t s);
 
 // Lanczos-fused H.v on the library's padded vectors (ed_hv2.cu). hv2_build leaves *out
 // NULL when no variant fits in shared memory (the general kernels are used then).

@@ -137,6 +137,37 @@ lz_energy_kernel(const LzScalars* S, double* out) {
   if (threadIdx.x == 0) *out = E;
 }
 
+// Eigenvector y of T_m for its lowest eigenvalue lam by inverse iteration (two solves of
+// (T - sigma I) z = r with sigma just below lam, where T - sigma I is positive definite, so
+// the tridiagonal LU without pivoting is stable); one thread. y normalised, y[1..m].
+__global__ void lz_ritz_kernel(const LzScalars* S, int m, double lam, double* y, double* work) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double* a = S->alpha;
+  const double* b = S->beta;
+  double scale = fabs(lam);
+  for (int i = 1; i <= m; ++i) scale = fmax(scale, fabs(a[i]) + b[i] + b[i + 1]);
+  const double sigma = lam - 1e-10 * fmax(scale, 1e-300);
+  double* dpiv = work;           // pivots
+  double* z = work + (m + 2);    // right-hand side / solution
+  for (int i = 1; i <= m; ++i) y[i] = 1.0;
+  for (int it = 0; it < 3; ++it) {
+    // forward elimination of (T - sigma I) z = y
+    dpiv[1] = a[1] - sigma;
+    z[1] = y[1];
+    for (int i = 2; i <= m; ++i) {
+      const double l = b[i] / dpiv[i - 1];
+      dpiv[i] = (a[i] - sigma) - l * b[i];
+      z[i] = y[i] - l * z[i - 1];
+    }
+    z[m] = z[m] / dpiv[m];
+    for (int i = m - 1; i >= 1; --i) z[i] = (z[i] - b[i + 1] * z[i + 1]) / dpiv[i];
+    double nrm = 0.0;
+    for (int i = 1; i <= m; ++i) nrm = fma(z[i], z[i], nrm);
+    nrm = sqrt(nrm);
+    for (int i = 1; i <= m; ++i) y[i] = z[i] / nrm;
+  }
+}
+
 static int red_grid(int64_t n) {
   const int64_t want = (n + kRedThreads - 1) / kRedThreads;
   const int64_t cap = (int64_t)sm_count() * 4;
@@ -341,7 +372,7 @@ static ed_status lz_init(const ed_basis* b, const ed_opts* o, const void* f1, cu
   st->n = b->up.dim * st->ld;
   // partial sums: one double per CTA, or four int64 words per CTA on the fixed-point path
   st->npa = hv_max_grid(b) * (st->fx ? 4 : 1);
-  st->npb = (int64_t)sm_count() * 4 * (st->fx ? 4 : 1);
+  st->npb = (int64_t)sm_count() * 4 * (st->fx ? 6 : 1);
   auto fail = [&](ed_status e) {
     ed_lanczos_destroy(st);
     return e;
@@ -504,6 +535,72 @@ extern "C" ed_status ed_lanczos_energy(ed_lanczos* st, double* E0, int32_t* step
   ED_TRY_CUDA(cudaStreamSynchronize(st->stream));
   if (E0) *E0 = e;
   if (steps) *steps = j;
+  return ED_OK;
+}
+
+extern "C" ed_status ed_lanczos_ground_state(const ed_basis* b, const ed_params* p,
+                                             const ed_opts* o, const void* f1, void* stream,
+                                             double* psi, double* E0, int32_t* steps) {
+  clear_error();
+  ED_CHECK_ARG(b && p && o && psi && E0, "ed_lanczos_ground_state: NULL argument");
+  ED_CHECK_ARG(o->dtype == ED_F64, "ed_lanczos_ground_state: dtype must be ED_F64");
+  ED_CHECK_ARG(aligned16(psi), "ed_lanczos_ground_state: psi must be 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  ed_lanczos* st = nullptr;
+  long long* P = nullptr;
+  double* yd = nullptr;
+  auto cleanup = [&](ed_status e) {
+    if (st) ed_lanczos_destroy(st);
+    if (P) cudaFree(P);
+    if (yd) cudaFree(yd);
+    return e;
+  };
+  // ---- pass 1: Algorithm 1 to convergence (stepwise, E0 every step)
+  ed_status r = lz_init(b, o, f1, s, 1, false, &st);
+  if (r != ED_OK) return cleanup(r);
+  if ((r = fx_prepare(b)) != ED_OK) return cleanup(r);
+  int hdr[2] = {0, 0};
+  for (int done = 0; done < o->max_steps; done += 8) {
+    for (int i = 0; i < 8; ++i)
+      if ((r = lz_launch_step(st, p, s)) != ED_OK) return cleanup(r);
+    if (cudaMemcpyAsync(hdr, st->S, 2 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      set_error("ed_lanczos_ground_state: %s", cudaGetErrorString(cudaGetLastError()));
+      return cleanup(ED_ERR_CUDA);
+    }
+    if (hdr[1] != 0) break;
+  }
+  const int m = hdr[0];
+  const int status = hdr[1];
+  double lam = 0.0;
+  ED_TRY_CUDA(cudaMemcpy(&lam, &st->S->E0[m], sizeof(double), cudaMemcpyDeviceToHost));
+  // ---- Ritz vector of T_m on the device
+  if (cudaMalloc((void**)&yd, (size_t)(3 * (m + 2)) * sizeof(double)) != cudaSuccess)
+    return cleanup(ED_ERR_OOM);
+  lz_ritz_kernel<<<1, 32, 0, s>>>(st->S, m, lam, yd, yd + (m + 2));
+  ED_TRY_CUDA(cudaGetLastError());
+  // ---- pass 2: the same steps again from the same start, accumulating y_j f_j
+  ed_lanczos* st2 = nullptr;
+  if ((r = lz_init(b, o, f1, s, ED_MAX_STEPS + 1, true, &st2)) != ED_OK) return cleanup(r);
+  ed_lanczos_destroy(st);
+  st = st2;
+  if (cudaMalloc((void**)&P, (size_t)b->dim * sizeof(long long)) != cudaSuccess)
+    return cleanup(ED_ERR_OOM);
+  ED_TRY_CUDA(cudaMemsetAsync(P, 0, (size_t)b->dim * sizeof(long long), s));
+  for (int j = 1; j <= m; ++j) {
+    if ((r = fx_psi_accum(b, st->S, st->cur, yd, j, (const long long*)st->B[st->cur], st->ld, P, s)) != ED_OK)
+      return cleanup(r);
+    if (j < m && (r = lz_launch_step(st, p, s)) != ED_OK) return cleanup(r);
+  }
+  if ((r = fx_psi_finish(b, P, (long long*)st->pb, (double*)psi, s)) != ED_OK) return cleanup(r);
+  ED_TRY_CUDA(cudaStreamSynchronize(s));
+  *E0 = lam;
+  if (steps) *steps = m;
+  cleanup(ED_OK);
+  if (status == 3 && o->tol > 0.0) {
+    set_error("ed_lanczos_ground_state: not converged after %d steps", m);
+    return ED_ERR_NOT_CONVERGED;
+  }
   return ED_OK;
 }
 
