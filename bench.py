@@ -140,6 +140,145 @@ def _workload_config(name, dim, du, dd, dtype):
             "parallelism": "replicas (one independent Lanczos run per GPU)"}
 
 
+# ----------------------------------------------------------------------------- time to E0
+def _first_within(hist, ref, rel=1e-8):
+    import numpy as np
+    ok = np.nonzero(np.abs(np.asarray(hist) - ref) <= rel * abs(ref))[0]
+    return int(ok[0]) + 1 if len(ok) else None
+
+
+def _timed(fn):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, time.perf_counter() - t0
+
+
+def time_to_e0_headline(ed, basis, w, rel=1e-8):
+    """Steps and wall time for E0 within `rel` of the converged FP64-accurate value, on the
+    bench workload: FP64-accurate (int64 fixed point), native FP64, FP32."""
+    t, U, seed = w["t"], w["U"], w["seed"]
+    ref = ed.ed_lanczos_solve(basis, t, U, ed.make_opts(max_steps=800, tol=1e-14, seed=seed),
+                              raise_not_converged=False)
+    E_ref = ref["E0"]
+    out = {"E0_ref": E_ref, "rel": rel}
+    for name, dt in (("f64_fixed", "f64"), ("f64_native", "f64n"), ("f32", "f32")):
+        h = ref["E0_hist"] if dt == "f64" else ed.ed_lanczos_solve(
+            basis, t, U, ed.make_opts(max_steps=400, tol=0.0, seed=seed, dtype=dt),
+            raise_not_converged=False)["E0_hist"]
+        m = _first_within(h, E_ref, rel)
+        rec = {"steps": m, "best_rel_err": float(min(abs(x - E_ref) for x in h) / abs(E_ref))}
+        if m:
+            _, sec = _timed(lambda: ed.ed_lanczos_solve(
+                basis, t, U, ed.make_opts(max_steps=m, tol=0.0, seed=seed, dtype=dt)))
+            rec["seconds"] = sec
+        out[name] = rec
+    return out
+
+
+def learned_start_study(ed, rel=1e-8, train_steps=1500, batch=16384):
+    """L14 ring 7/7: ground states at U = 0, 0.5, ..., 8 train the network; at 16 held-out U
+    compare steps/time to E0 within `rel` from the random start and from the learned start."""
+    import numpy as np
+    import torch
+    w = ed_inputs.workload("ring14_7_7")
+    L, bonds, nu, nd = w["n_sites"], w["bonds"], w["n_up"], w["n_dn"]
+    basis = ed.ed_build_basis(L, bonds, nu, nd)
+    net = ed.ed_mlp_create(L, 5)
+    try:
+        dim = ed.ed_basis_dims(basis)[2]
+        grid = [0.5 * k for k in range(17)]
+        psis = []
+        def _gs():
+            for U in grid:
+                psi = torch.empty(dim, dtype=torch.float64, device="cuda")
+                ed.ed_lanczos_ground_state(basis, 1.0, U, ed.make_opts(max_steps=600, tol=1e-13, seed=5), psi,
+                                           raise_not_converged=False)
+                psis.append(psi)
+        _, t_gs = _timed(_gs)
+        losses = []
+        def _train():
+            for step in range(train_steps):
+                k = step % len(grid)
+                lr = 3e-3 * (0.5 * (1 + math.cos(math.pi * step / train_steps)))
+                losses.append(ed.ed_mlp_train_step(net, basis, grid[k], psis[k], batch, lr, 77 + step))
+        _, t_train = _timed(_train)
+        del psis
+        recs = []
+        f64 = torch.empty(dim, dtype=torch.float64, device="cuda")
+        f32 = torch.empty(dim, dtype=torch.float32, device="cuda")
+        for U in ed_inputs.heldout_U():
+            U = float(U)
+            ref = ed.ed_lanczos_solve(basis, 1.0, U, ed.make_opts(max_steps=800, tol=1e-14, seed=5),
+                                      raise_not_converged=False)
+            m_rand = _first_within(ref["E0_hist"], ref["E0"], rel)
+            ed.ed_mlp_infer(net, basis, U, f64)
+            lr_ = ed.ed_lanczos_solve(basis, 1.0, U, ed.make_opts(max_steps=800, tol=0.0, seed=5), f1=f64,
+                                      raise_not_converged=False)
+            m_lrn = _first_within(lr_["E0_hist"], ref["E0"], rel)
+            ed.ed_mlp_infer(net, basis, U, f32)
+            l32 = ed.ed_lanczos_solve(basis, 1.0, U, ed.make_opts(max_steps=400, tol=0.0, seed=5, dtype="f32"),
+                                      f1=f32, raise_not_converged=False)
+            m_32 = _first_within(l32["E0_hist"], ref["E0"], 1e-6)
+            if not (m_rand and m_lrn):
+                recs.append({"U": U, "steps_random": m_rand, "steps_learned": m_lrn, "s_random": float("nan"),
+                             "s_learned": float("nan")})
+                continue
+            _, t_rand = _timed(lambda: ed.ed_lanczos_solve(basis, 1.0, U, ed.make_opts(max_steps=m_rand, tol=0.0, seed=5)))
+            def _lrn():
+                ed.ed_mlp_infer(net, basis, U, f64)
+                return ed.ed_lanczos_solve(basis, 1.0, U, ed.make_opts(max_steps=m_lrn, tol=0.0, seed=5), f1=f64)
+            _, t_lrn = _timed(_lrn)
+            r = {"U": U, "steps_random": m_rand, "steps_learned": m_lrn, "s_random": t_rand, "s_learned": t_lrn,
+                 "f32_learned_steps_to_1e-6": m_32,
+                 "f32_learned_best_rel_err": float(np.min(np.abs(l32["E0_hist"] - ref["E0"])) / abs(ref["E0"]))}
+            if m_32:
+                def _l32():
+                    ed.ed_mlp_infer(net, basis, U, f32)
+                    return ed.ed_lanczos_solve(basis, 1.0, U, ed.make_opts(max_steps=m_32, tol=0.0, seed=5, dtype="f32"), f1=f32)
+                _, r["s_f32_learned_to_1e-6"] = _timed(_l32)
+            recs.append(r)
+        mean = lambda k: float(np.nanmean([np.nan if r[k] is None else r[k] for r in recs]))
+        return {"workload": "ring14_7_7 (dim 11,778,624), train U = 0, 0.5, ..., 8; 16 held-out U",
+                "ground_states_s": t_gs, "train_s": t_train, "train_steps": train_steps, "batch": batch,
+                "final_loss": float(np.mean(losses[-17:])), "rel": rel,
+                "mean_steps_random": mean("steps_random"), "mean_steps_learned": mean("steps_learned"),
+                "mean_s_random": mean("s_random"), "mean_s_learned": mean("s_learned"),
+                "per_U": recs}
+    finally:
+        ed.ed_mlp_destroy(net)
+        ed.ed_basis_destroy(basis)
+
+
+def batched_study(ed):
+    """256 instances: one batched FP32 launch vs sequential FP64-accurate solves."""
+    import numpy as np
+    insts = ed_inputs.batched_instances()
+    bases = [ed.ed_build_basis(w["n_sites"], w["bonds"], w["n_up"], w["n_dn"]) for w in insts]
+    try:
+        ts = [w["t"] for w in insts]
+        Us = [w["U"] for w in insts]
+        opts = ed.make_opts(max_steps=600, tol=1e-9, seed=4, dtype="f32", schedule=-1)
+        ed.ed_lanczos_solve_batched(bases, ts, Us, opts, raise_not_converged=False)   # autotune
+        res, t_b = _timed(lambda: ed.ed_lanczos_solve_batched(bases, ts, Us, opts, raise_not_converged=False))
+        def _seq():
+            return [ed.ed_lanczos_solve(b, t, U, ed.make_opts(max_steps=600, tol=1e-12, seed=4),
+                                        raise_not_converged=False)["E0"] for b, t, U in zip(bases, ts, Us)]
+        ref, t_s = _timed(_seq)
+        ref = np.array(ref)
+        err = np.abs(res["E0"] - ref) / np.maximum(1.0, np.abs(ref))
+        return {"instances": len(insts), "sum_dim": int(sum(ed.ed_basis_dims(b)[2] for b in bases)),
+                "batched_f32_s": t_b, "schedule": res["schedule"],
+                "batched_max_steps": int(res["steps"].max()), "sequential_f64_s": t_s,
+                "speedup": t_s / t_b, "max_rel_err_vs_f64": float(err.max()),
+                "median_rel_err_vs_f64": float(np.median(err))}
+    finally:
+        for b in bases:
+            ed.ed_basis_destroy(b)
+
+
 def bench_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -265,6 +404,10 @@ def bench_ours(args):
                     "E0": res["E0"], "api": "ed_lanczos_solve (f1 from pinned host memory)"},
             "gpu_launches": 3 * K,
             "clocks": clk}
+    if ws == 1 and not args.no_extras:
+        line["time_to_E0"] = time_to_e0_headline(ed, basis, w)
+        line["batched"] = batched_study(ed)
+        line["learned_start"] = learned_start_study(ed)
     if ws == 1 and not args.no_cpu_baseline:
         d = run_oracle_sample(args.workload, args.cpu_rows, args.cpu_reps)
         line["cpu_baseline"] = {"value": d["steps_per_s"], "unit": "lanczos_steps/s", "cores": 1,
@@ -289,6 +432,8 @@ def main():
     ap.add_argument("--cpu-reps", type=int, default=8)
     ap.add_argument("--ref-rows", type=int, default=100000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the time-to-E0, batched and learned-start studies")
     ap.add_argument("--schedule", type=int, default=-1, help="H.v kernel variant (-1: default)")
     args = ap.parse_args()
     if args.impl == "reference":

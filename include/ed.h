@@ -179,11 +179,12 @@ void ed_lanczos_destroy(ed_lanczos* st);
 
 /* ed_lanczos_solve - run Algorithm 1 from f1 (as in ed_lanczos_init) until the convergence
  * test of opts passes, b_{j+1} vanishes, or max_steps; returns E0 (HOST) and the steps
- * taken. alpha and beta (HOST, optional) receive a_1..a_m and b_2..b_{m+1}. Returns ED_OK,
- * ED_BREAKDOWN or ED_ERR_NOT_CONVERGED (E0 still set) or an error. Synchronises `stream`. */
+ * taken. alpha, beta, E0_hist (HOST, optional, max_steps entries) receive a_1..a_m,
+ * b_2..b_{m+1} and E0(1)..E0(m) (the lowest eigenvalue of T_j after every step). Returns
+ * ED_OK, ED_BREAKDOWN or ED_ERR_NOT_CONVERGED (E0 still set) or an error. Synchronises. */
 ed_status ed_lanczos_solve(const ed_basis* basis, const ed_params* params, const ed_opts* opts,
                            const void* f1, void* stream, double* E0, int32_t* steps,
-                           double* alpha, double* beta);
+                           double* alpha, double* beta, double* E0_hist);
 
 /* ed_lanczos_solve_batched - Algorithm 1 for n independent instances (basis i with
  * params[i], a HOST array of n) in one persistent cooperative kernel launch, captured in a

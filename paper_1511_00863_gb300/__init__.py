@@ -64,7 +64,7 @@ _SIGS = {
     "ed_lanczos_destroy": (None, [c_void_p]),
     "ed_lanczos_solve": (c_int, [c_void_p, POINTER(ed_params), POINTER(ed_opts), c_void_p, c_void_p,
                                  POINTER(c_double), POINTER(c_int32), POINTER(c_double),
-                                 POINTER(c_double)]),
+                                 POINTER(c_double), POINTER(c_double)]),
     "ed_lanczos_solve_batched": (c_int, [c_int32, POINTER(c_void_p), POINTER(ed_params),
                                          POINTER(ed_opts), c_void_p, POINTER(c_double),
                                          POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)]),
@@ -230,12 +230,14 @@ def ed_lanczos_solve(basis, t: float, U: float, opts: ed_opts, f1=None, stream=N
     E0, steps = c_double(), c_int32()
     alpha = (c_double * opts.max_steps)()
     beta = (c_double * opts.max_steps)()
+    hist = (c_double * opts.max_steps)()
     s = _lib.ed_lanczos_solve(basis, byref(p), byref(opts), _ptr(f1, opts.dtype, dim),
-                              _stream(stream), byref(E0), byref(steps), alpha, beta)
+                              _stream(stream), byref(E0), byref(steps), alpha, beta, hist)
     if s < 0 and not (s == ED_ERR_NOT_CONVERGED and not raise_not_converged):
         _check(s)
     n = steps.value
-    return dict(status=s, E0=E0.value, steps=n, alpha=np.array(alpha[:n]), beta=np.array(beta[:n]))
+    return dict(status=s, E0=E0.value, steps=n, alpha=np.array(alpha[:n]), beta=np.array(beta[:n]),
+                E0_hist=np.array(hist[:n]))
 
 
 def ed_lanczos_solve_batched(bases, ts, Us, opts: ed_opts, stream=None,

@@ -380,7 +380,7 @@ ed_status hv2_build(const ed_basis* b, bool fixed_point, int ld, int schedule, c
                     Hv2Plan** out) {
   *out = nullptr;
   const size_t lim = (size_t)optin_smem();
-  static const int pref_f32[] = {1, 2, 3}, pref_fx[] = {6, 4, 5, 7};
+  static const int pref_f32[] = {2, 1, 3}, pref_fx[] = {4, 5, 6, 7};
   const int* pref = fixed_point ? pref_fx : pref_f32;
   const int npref = fixed_point ? 4 : 3;
   int kind = 0, R = 1;

@@ -606,7 +606,7 @@ extern "C" ed_status ed_lanczos_ground_state(const ed_basis* b, const ed_params*
 
 extern "C" ed_status ed_lanczos_solve(const ed_basis* b, const ed_params* p, const ed_opts* o,
                                       const void* f1, void* stream, double* E0, int32_t* steps,
-                                      double* alpha, double* beta) {
+                                      double* alpha, double* beta, double* E0_hist) {
   clear_error();
   ED_CHECK_ARG(p != nullptr, "ed_lanczos_solve: params is NULL");
   ED_CHECK_ARG(E0 != nullptr, "ed_lanczos_solve: E0 is NULL");
@@ -684,6 +684,7 @@ extern "C" ed_status ed_lanczos_solve(const ed_basis* b, const ed_params* p, con
   for (int i = 1; i <= j; ++i) {
     if (alpha) alpha[i - 1] = h_alpha[i];
     if (beta) beta[i - 1] = h_beta[i + 1];
+    if (E0_hist) E0_hist[i - 1] = h_E[i];
   }
   const int status = hdr[1];
   cleanup(ED_OK);
