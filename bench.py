@@ -172,7 +172,7 @@ def time_to_e0_headline(ed, basis, w, rel=1e-8):
         rec = {"steps": m, "best_rel_err": float(min(abs(x - E_ref) for x in h) / abs(E_ref))}
         if m:
             _, sec = _timed(lambda: ed.ed_lanczos_solve(
-                basis, t, U, ed.make_opts(max_steps=m, tol=0.0, seed=seed, dtype=dt)))
+                basis, t, U, ed.make_opts(max_steps=m, tol=0.0, seed=seed, dtype=dt), history=False))
             rec["seconds"] = sec
         out[name] = rec
     return out
@@ -226,10 +226,12 @@ def learned_start_study(ed, rel=1e-8, train_steps=1500, batch=16384):
                 recs.append({"U": U, "steps_random": m_rand, "steps_learned": m_lrn, "s_random": float("nan"),
                              "s_learned": float("nan")})
                 continue
-            _, t_rand = _timed(lambda: ed.ed_lanczos_solve(basis, 1.0, U, ed.make_opts(max_steps=m_rand, tol=0.0, seed=5)))
+            _, t_rand = _timed(lambda: ed.ed_lanczos_solve(basis, 1.0, U, ed.make_opts(max_steps=m_rand, tol=0.0, seed=5),
+                                                           history=False))
             def _lrn():
                 ed.ed_mlp_infer(net, basis, U, f64)
-                return ed.ed_lanczos_solve(basis, 1.0, U, ed.make_opts(max_steps=m_lrn, tol=0.0, seed=5), f1=f64)
+                return ed.ed_lanczos_solve(basis, 1.0, U, ed.make_opts(max_steps=m_lrn, tol=0.0, seed=5), f1=f64,
+                                           history=False)
             _, t_lrn = _timed(_lrn)
             r = {"U": U, "steps_random": m_rand, "steps_learned": m_lrn, "s_random": t_rand, "s_learned": t_lrn,
                  "f32_learned_steps_to_1e-6": m_32,
@@ -237,7 +239,8 @@ def learned_start_study(ed, rel=1e-8, train_steps=1500, batch=16384):
             if m_32:
                 def _l32():
                     ed.ed_mlp_infer(net, basis, U, f32)
-                    return ed.ed_lanczos_solve(basis, 1.0, U, ed.make_opts(max_steps=m_32, tol=0.0, seed=5, dtype="f32"), f1=f32)
+                    return ed.ed_lanczos_solve(basis, 1.0, U, ed.make_opts(max_steps=m_32, tol=0.0, seed=5, dtype="f32"),
+                                               f1=f32, history=False)
                 _, r["s_f32_learned_to_1e-6"] = _timed(_l32)
             recs.append(r)
         mean = lambda k: float(np.nanmean([np.nan if r[k] is None else r[k] for r in recs]))

@@ -181,7 +181,10 @@ void ed_lanczos_destroy(ed_lanczos* st);
  * test of opts passes, b_{j+1} vanishes, or max_steps; returns E0 (HOST) and the steps
  * taken. alpha, beta, E0_hist (HOST, optional, max_steps entries) receive a_1..a_m,
  * b_2..b_{m+1} and E0(1)..E0(m) (the lowest eigenvalue of T_j after every step). Returns
- * ED_OK, ED_BREAKDOWN or ED_ERR_NOT_CONVERGED (E0 still set) or an error. Synchronises. */
+ * ED_OK, ED_BREAKDOWN or ED_ERR_NOT_CONVERGED (E0 still set) or an error. Synchronises.
+ * The basis keeps the work vectors and the captured CUDA graph of its last solve per
+ * (dtype, schedule) for later solves (released by ed_basis_destroy); concurrent solves on one
+ * basis from several threads are allowed (the extra ones use private workspaces). */
 ed_status ed_lanczos_solve(const ed_basis* basis, const ed_params* params, const ed_opts* opts,
                            const void* f1, void* stream, double* E0, int32_t* steps,
                            double* alpha, double* beta, double* E0_hist);

@@ -3,12 +3,14 @@
 The paper has no learned component; this is the oracle of the library's MLP (same
 definition, written plainly). A basis state s = (up bits, down bits) of an L-site lattice
 and the interaction U give the input features
-    x = (up bit 0..L-1, down bit 0..L-1, U / 8)                       (2L + 1 values)
+    x = (up bit 0..L-1, down bit 0..L-1, bf16(U / 8))                 (2L + 1 values)
 and the network
-    h1 = tanh(W1^T x + b1), h2 = tanh(W2^T h1 + b2), (a, z) = W3^T h2 + b3
+    h1 = tanh(W1^T x + b1), h2 = tanh(W2^T bf16(h1) + b2), (a, z) = W3^T h2 + b3
 with 64 hidden units per layer. The predicted start-vector entry is sign(z) exp(a)
 (z >= 0 counts as positive). The forward pass uses the weights rounded to bfloat16
-(round to nearest even), accumulates in FP64 here (FP32 on the GPU).
+(round to nearest even) and feeds the second layer the first layer's output rounded to
+bfloat16 (the operands of the GPU's bfloat16 tensor-core products); it accumulates in FP64
+here (FP32 on the GPU). The backward pass treats both roundings as the identity.
 
 Loss over a batch of states s_k with target amplitudes psi_k (samples drawn uniformly,
 weight w_k = c psi_k^2 with c = the basis dimension, so that E[w] = 1 for a normalised psi):
@@ -57,14 +59,15 @@ def bf16_round(x: np.ndarray) -> np.ndarray:
     return r.view(np.float32).astype(np.float64)
 
 
-def features(up_bits: np.ndarray, dn_bits: np.ndarray, n_sites: int, U: float) -> np.ndarray:
+def features(up_bits: np.ndarray, dn_bits: np.ndarray, n_sites: int, U: float,
+             round_inputs: bool = True) -> np.ndarray:
     up = np.asarray(up_bits, dtype=np.int64)
     dn = np.asarray(dn_bits, dtype=np.int64)
     x = np.zeros((len(up), n_inputs(n_sites)))
     for i in range(n_sites):
         x[:, i] = (up >> i) & 1
         x[:, n_sites + i] = (dn >> i) & 1
-    x[:, 2 * n_sites] = U / 8.0
+    x[:, 2 * n_sites] = bf16_round(np.float32(U / 8.0)) if round_inputs else U / 8.0
     return x
 
 
@@ -76,7 +79,8 @@ def _weights(params, n_sites, round_weights):
 def forward(params, x, n_sites, round_weights=True):
     W1, b1, W2, b2, W3, b3 = _weights(params, n_sites, round_weights)
     h1 = np.tanh(x @ W1 + b1)
-    h2 = np.tanh(h1 @ W2 + b2)
+    h1b = bf16_round(h1) if round_weights else h1
+    h2 = np.tanh(h1b @ W2 + b2)
     out = h2 @ W3 + b3
     return out[:, 0], out[:, 1], (x, h1, h2)
 
@@ -94,7 +98,8 @@ def loss_and_grad(params, x, psi, weight_scale, n_sites, round_weights=True):
     B = len(psi)
     psi = np.asarray(psi, dtype=np.float64)
     h1 = np.tanh(x @ W1 + b1)
-    h2 = np.tanh(h1 @ W2 + b2)
+    h1b = bf16_round(h1) if round_weights else h1
+    h2 = np.tanh(h1b @ W2 + b2)
     out = h2 @ W3 + b3
     a, z = out[:, 0], out[:, 1]
     live = psi != 0.0
@@ -108,7 +113,7 @@ def loss_and_grad(params, x, psi, weight_scale, n_sites, round_weights=True):
     gW3 = h2.T @ dout
     gb3 = dout.sum(0)
     g2 = (dout @ W3.T) * (1.0 - h2 * h2)
-    gW2 = h1.T @ g2
+    gW2 = h1b.T @ g2
     gb2 = g2.sum(0)
     g1 = (g2 @ W2.T) * (1.0 - h1 * h1)
     gW1 = x.T @ g1

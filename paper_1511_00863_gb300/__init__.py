@@ -224,20 +224,21 @@ def ed_lanczos_destroy(st) -> None:
 
 
 def ed_lanczos_solve(basis, t: float, U: float, opts: ed_opts, f1=None, stream=None,
-                     raise_not_converged: bool = True) -> dict:
+                     raise_not_converged: bool = True, history: bool = True) -> dict:
+    """history=False skips the per-step E0(j) (computed then only at the last step)."""
     dim = ed_basis_dims(basis)[2]
     p = ed_params(t, U)
     E0, steps = c_double(), c_int32()
     alpha = (c_double * opts.max_steps)()
     beta = (c_double * opts.max_steps)()
-    hist = (c_double * opts.max_steps)()
+    hist = (c_double * opts.max_steps)() if history else None
     s = _lib.ed_lanczos_solve(basis, byref(p), byref(opts), _ptr(f1, opts.dtype, dim),
                               _stream(stream), byref(E0), byref(steps), alpha, beta, hist)
     if s < 0 and not (s == ED_ERR_NOT_CONVERGED and not raise_not_converged):
         _check(s)
     n = steps.value
     return dict(status=s, E0=E0.value, steps=n, alpha=np.array(alpha[:n]), beta=np.array(beta[:n]),
-                E0_hist=np.array(hist[:n]))
+                E0_hist=np.array(hist[:n]) if history else None)
 
 
 def ed_lanczos_solve_batched(bases, ts, Us, opts: ed_opts, stream=None,

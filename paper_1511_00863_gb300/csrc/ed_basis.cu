@@ -318,6 +318,7 @@ extern "C" void ed_basis_destroy(ed_basis* B) {
   int prev = 0;
   cudaGetDevice(&prev);
   if (prev != B->device) cudaSetDevice(B->device);
+  lz_cache_free(B);
   free_species(B->up);
   free_species(B->dn);
   if (B->binom) cudaFree(B->binom);

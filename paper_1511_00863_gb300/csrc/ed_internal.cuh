@@ -58,6 +58,8 @@ struct ed_basis {
   // up-species hop graph), so that rows sharing up-neighbours are processed close in
   // time and the neighbours stay resident in L2. NULL = rank order.
   int32_t* up_order = nullptr;
+  // Workspaces of ed_lanczos_solve kept between calls (ed_lanczos.cu); freed with the basis.
+  mutable void* solve_cache = nullptr;
 };
 
 namespace ed {
@@ -66,6 +68,9 @@ inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 
 
 // Number of SMs of the current device (cached per device).
 int sm_count();
+
+// Free the solve workspaces cached on a basis (called by ed_basis_destroy).
+void lz_cache_free(const ed_basis* b);
 
 // Device-resident scalars of one Lanczos run (Algorithm 1). Index j is 1-based as in the
 // paper: alpha[j] = a_j, beta[j] = b_j (beta[1] = 0), E0[j] = lambda_min(T_j).

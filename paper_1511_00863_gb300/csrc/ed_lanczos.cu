@@ -195,6 +195,7 @@ struct ed_lanczos {
   int64_t npa = 0, npb = 0;
   int hv_grid = 0;
   bool stopped = false;
+  double graph_t = 0.0, graph_U = 0.0;  // parameters the captured graph was made with
   bool fx = false;     // ED_F64: int64 fixed-point buffers (ed_fixed.cu)
   FxRun fxr{};
   Hv2Plan* plan = nullptr;  // fused H.v on the padded layout (ed_hv2.cu), if it fits
@@ -353,13 +354,11 @@ extern "C" void ed_lanczos_destroy(ed_lanczos* st) {
 
 // check_every: compute E0(j) in the finish kernel every this many steps; step_mode: the
 // caller drives the loop, so only breakdown and max_steps stop the run (no tol test).
-static ed_status lz_init(const ed_basis* b, const ed_opts* o, const void* f1, cudaStream_t s,
-                         int check_every, bool step_mode, ed_lanczos** out) {
+static ed_status lz_alloc(const ed_basis* b, const ed_opts* o, cudaStream_t s, ed_lanczos** out) {
   *out = nullptr;
   ED_CHECK_ARG(b != nullptr, "basis is NULL");
   ed_status r = check_opts(o);
   if (r != ED_OK) return r;
-  ED_CHECK_ARG(f1 == nullptr || aligned16(f1), "f1 must be 16-byte aligned");
   ed_lanczos* st = new ed_lanczos();
   st->basis = b;
   st->opts = *o;
@@ -391,12 +390,25 @@ static ed_status lz_init(const ed_basis* b, const ed_opts* o, const void* f1, cu
     set_error("Lanczos scalars: out of device memory");
     return fail(ED_ERR_OOM);
   }
-  for (int i = 0; i < 2; ++i)
-    if (cudaMemsetAsync(st->B[i], 0, st->n * st->esize, s) != cudaSuccess) return fail(ED_ERR_CUDA);
   if (o->dtype != ED_F64_NATIVE) {
     ed_status pr = hv2_build(b, st->fx, (int)st->ld, o->schedule, s, &st->plan);
     if (pr != ED_OK) return fail(pr);
   }
+  *out = st;
+  return ED_OK;
+}
+
+// Start a run on an allocated state: zero both buffers (their pads must hold 0), load f_1
+// (caller vector or seeded start vector) and the run's scalars. check_every: compute E0(j)
+// every this many steps; step_mode: the caller drives the loop (no tol test).
+static ed_status lz_reset(ed_lanczos* st, const ed_opts* o, const void* f1, int check_every,
+                          bool step_mode) {
+  const ed_basis* b = st->basis;
+  cudaStream_t s = st->stream;
+  ED_CHECK_ARG(f1 == nullptr || aligned16(f1), "f1 must be 16-byte aligned");
+  st->opts = *o;
+  st->stopped = false;
+  for (int i = 0; i < 2; ++i) ED_TRY_CUDA(cudaMemsetAsync(st->B[i], 0, st->n * st->esize, s));
   LzScalars h;
   memset(&h, 0, sizeof(h));
   h.check_every = check_every < 1 ? 1 : check_every;
@@ -405,22 +417,16 @@ static ed_status lz_init(const ed_basis* b, const ed_opts* o, const void* f1, cu
   h.scale[0] = 1.0;
   h.scale[1] = 0.0;
   for (int i = 0; i < ED_MAX_STEPS + 2; ++i) h.E0[i] = NAN;
-  if (cudaMemcpyAsync(st->S, &h, sizeof(h), cudaMemcpyHostToDevice, s) != cudaSuccess) {
-    set_error("Lanczos scalars: copy failed");
-    return fail(ED_ERR_CUDA);
-  }
+  ED_TRY_CUDA(cudaMemcpyAsync(st->S, &h, sizeof(h), cudaMemcpyHostToDevice, s));
   const int64_t dim = b->dim, cols = b->dn.dim;
   const int g = red_grid(dim);
-  if ((int64_t)g > st->npb) return fail(ED_ERR_ARG);
+  ED_CHECK_ARG((int64_t)g <= st->npb, "internal: partial buffer too small");
+  st->cur = 0;
   if (st->fx) {
-    ed_status fr = f1 == nullptr
+    return f1 == nullptr
         ? fx_start(b, st->fxr, o->seed, (long long*)st->B[0], st->ld, st->S, (long long*)st->pb, s)
         : fx_copy_in(b, st->fxr, (const double*)f1, (long long*)st->B[0], st->ld, st->S,
                      (long long*)st->pb, s);
-    if (fr != ED_OK) return fail(fr);
-    st->cur = 0;
-    *out = st;
-    return ED_OK;
   }
   if (f1 == nullptr) {
     start_norm_kernel<<<g, kRedThreads, 0, s>>>(o->seed, dim, st->pb);
@@ -440,12 +446,23 @@ static ed_status lz_init(const ed_basis* b, const ed_opts* o, const void* f1, cu
                                                       (float*)st->B[0], st->pb);
     init_scalars_kernel<<<1, kRedThreads, 0, s>>>(st->S, st->pb, g, 1);
   }
-  cudaError_t e = cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error("Lanczos init: %s", cudaGetErrorString(e));
-    return fail(ED_ERR_CUDA);
+    return ED_ERR_CUDA;
   }
-  st->cur = 0;
+  return ED_OK;
+}
+
+static ed_status lz_init(const ed_basis* b, const ed_opts* o, const void* f1, cudaStream_t s,
+                         int check_every, bool step_mode, ed_lanczos** out) {
+  ed_lanczos* st = nullptr;
+  ed_status r = lz_alloc(b, o, s, &st);
+  if (r != ED_OK) return r;
+  if ((r = lz_reset(st, o, f1, check_every, step_mode)) != ED_OK) {
+    ed_lanczos_destroy(st);
+    return r;
+  }
   *out = st;
   return ED_OK;
 }
@@ -604,51 +621,67 @@ extern "C" ed_status ed_lanczos_ground_state(const ed_basis* b, const ed_params*
   return ED_OK;
 }
 
-extern "C" ed_status ed_lanczos_solve(const ed_basis* b, const ed_params* p, const ed_opts* o,
-                                      const void* f1, void* stream, double* E0, int32_t* steps,
-                                      double* alpha, double* beta, double* E0_hist) {
-  clear_error();
-  ED_CHECK_ARG(p != nullptr, "ed_lanczos_solve: params is NULL");
-  ED_CHECK_ARG(E0 != nullptr, "ed_lanczos_solve: E0 is NULL");
-  cudaStream_t user = (cudaStream_t)stream;
-  cudaStream_t s = nullptr;
-  ED_TRY_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-  cudaEvent_t ev = nullptr;
-  ed_lanczos* st = nullptr;
-  ed_status r = ED_OK;
-  auto cleanup = [&](ed_status e) {
-    if (st) ed_lanczos_destroy(st);
-    if (ev) cudaEventDestroy(ev);
-    cudaStreamDestroy(s);
-    return e;
+// ------------------------------------------------------------------ solve
+// ed_lanczos_solve keeps, per basis, one allocated state per (dtype, schedule) and its
+// instantiated two-step graph, so repeated solves skip allocation and capture; a solve that
+// finds the cache busy (another thread) uses a private state instead.
+struct SolveCache {
+  std::mutex mu;
+  cudaStream_t stream = nullptr;
+  struct Entry {
+    int dtype, schedule;
+    ed_lanczos* st;
   };
-  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventRecord(ev, user) != cudaSuccess || cudaStreamWaitEvent(s, ev, 0) != cudaSuccess) {
-    set_error("ed_lanczos_solve: stream ordering failed");
-    return cleanup(ED_ERR_CUDA);
-  }
-  if ((r = lz_init(b, o, f1, s, 1, false, &st)) != ED_OK) return cleanup(r);
-  if ((r = (o->dtype == ED_F64 ? fx_prepare(b) : hv_prepare(b, o->dtype))) != ED_OK)
-    return cleanup(r);
-  // capture two steps (the buffer roles alternate) and replay
-  cudaGraph_t g = nullptr;
-  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-    set_error("ed_lanczos_solve: stream capture failed");
-    return cleanup(ED_ERR_CUDA);
-  }
-  ed_status r1 = lz_launch_step(st, p, s);
-  ed_status r2 = r1 == ED_OK ? lz_launch_step(st, p, s) : r1;
-  cudaError_t ce = cudaStreamEndCapture(s, &g);
-  if (r2 != ED_OK || ce != cudaSuccess) {
-    if (g) cudaGraphDestroy(g);
-    if (r2 == ED_OK) set_error("ed_lanczos_solve: capture failed: %s", cudaGetErrorString(ce));
-    return cleanup(r2 != ED_OK ? r2 : ED_ERR_CUDA);
-  }
-  ce = cudaGraphInstantiate(&st->graph, g, 0);
-  cudaGraphDestroy(g);
-  if (ce != cudaSuccess) {
-    set_error("ed_lanczos_solve: graph instantiate failed: %s", cudaGetErrorString(ce));
-    return cleanup(ED_ERR_CUDA);
+  std::vector<Entry> entries;
+};
+static std::mutex g_cache_mu;
+
+namespace ed {
+void lz_cache_free(const ed_basis* b) {
+  SolveCache* C = (SolveCache*)b->solve_cache;
+  if (!C) return;
+  for (auto& e : C->entries) ed_lanczos_destroy(e.st);
+  if (C->stream) cudaStreamDestroy(C->stream);
+  delete C;
+  b->solve_cache = nullptr;
+}
+}  // namespace ed
+
+static ed_status solve_on(ed_lanczos* st, const ed_basis* b, const ed_params* p, const ed_opts* o,
+                          const void* f1, double* E0, int32_t* steps, double* alpha, double* beta,
+                          double* E0_hist) {
+  cudaStream_t s = st->stream;
+  // E0(j) every step when the convergence test or the history needs it, else at the stop
+  const int check = (o->tol > 0.0 || E0_hist) ? 1 : ED_MAX_STEPS + 1;
+  ed_status r = lz_reset(st, o, f1, check, false);
+  if (r != ED_OK) return r;
+  if ((r = (o->dtype == ED_F64 ? fx_prepare(b) : hv_prepare(b, o->dtype))) != ED_OK) return r;
+  if (!st->graph || st->graph_t != p->t || st->graph_U != p->U) {
+    if (st->graph) cudaGraphExecDestroy(st->graph);
+    st->graph = nullptr;
+    // capture two steps (the buffer roles alternate) and replay
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      set_error("ed_lanczos_solve: stream capture failed");
+      return ED_ERR_CUDA;
+    }
+    const ed_status r1 = lz_launch_step(st, p, s);
+    const ed_status r2 = r1 == ED_OK ? lz_launch_step(st, p, s) : r1;
+    cudaError_t ce = cudaStreamEndCapture(s, &g);
+    if (r2 != ED_OK || ce != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      if (r2 == ED_OK) set_error("ed_lanczos_solve: capture failed: %s", cudaGetErrorString(ce));
+      return r2 != ED_OK ? r2 : ED_ERR_CUDA;
+    }
+    ce = cudaGraphInstantiate(&st->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) {
+      st->graph = nullptr;
+      set_error("ed_lanczos_solve: graph instantiate failed: %s", cudaGetErrorString(ce));
+      return ED_ERR_CUDA;
+    }
+    st->graph_t = p->t;
+    st->graph_U = p->U;
   }
   int hdr[2] = {0, 0};
   int launched = 0;
@@ -657,28 +690,21 @@ extern "C" ed_status ed_lanczos_solve(const ed_basis* b, const ed_params* p, con
     int batch = (remaining + 1) / 2;
     if (batch > 8) batch = 8;
     if (batch < 1) batch = 1;
-    for (int i = 0; i < batch; ++i) {
-      if (cudaGraphLaunch(st->graph, s) != cudaSuccess) {
-        set_error("ed_lanczos_solve: graph launch failed");
-        return cleanup(ED_ERR_CUDA);
-      }
-    }
+    for (int i = 0; i < batch; ++i) ED_TRY_CUDA(cudaGraphLaunch(st->graph, s));
     launched += 2 * batch;
-    if (cudaMemcpyAsync(hdr, st->S, 2 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {
-      set_error("ed_lanczos_solve: %s", cudaGetErrorString(cudaGetLastError()));
-      return cleanup(ED_ERR_CUDA);
-    }
+    ED_TRY_CUDA(cudaMemcpyAsync(hdr, st->S, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    ED_TRY_CUDA(cudaStreamSynchronize(s));
     if (hdr[1] != 0 || launched >= o->max_steps) break;
   }
-  std::vector<double> h_alpha(ED_MAX_STEPS + 2), h_beta(ED_MAX_STEPS + 2), h_E(ED_MAX_STEPS + 2);
-  if (cudaMemcpy(h_alpha.data(), st->S->alpha, h_alpha.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
-      cudaMemcpy(h_beta.data(), st->S->beta, h_beta.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
-      cudaMemcpy(h_E.data(), st->S->E0, h_E.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
-    set_error("ed_lanczos_solve: result copy failed");
-    return cleanup(ED_ERR_CUDA);
-  }
   const int j = hdr[0];
+  std::vector<double> hv(3 * (size_t)(j + 2));
+  double* h_alpha = hv.data();
+  double* h_beta = h_alpha + (j + 2);
+  double* h_E = h_beta + (j + 2);
+  ED_TRY_CUDA(cudaMemcpyAsync(h_alpha, st->S->alpha, (j + 2) * 8, cudaMemcpyDeviceToHost, s));
+  ED_TRY_CUDA(cudaMemcpyAsync(h_beta, st->S->beta, (j + 2) * 8, cudaMemcpyDeviceToHost, s));
+  ED_TRY_CUDA(cudaMemcpyAsync(h_E, st->S->E0, (j + 2) * 8, cudaMemcpyDeviceToHost, s));
+  ED_TRY_CUDA(cudaStreamSynchronize(s));
   *E0 = j >= 1 ? h_E[j] : NAN;
   if (steps) *steps = j;
   for (int i = 1; i <= j; ++i) {
@@ -687,11 +713,63 @@ extern "C" ed_status ed_lanczos_solve(const ed_basis* b, const ed_params* p, con
     if (E0_hist) E0_hist[i - 1] = h_E[i];
   }
   const int status = hdr[1];
-  cleanup(ED_OK);
   if (status == 1) return ED_BREAKDOWN;
   if (status == 3 && o->tol > 0.0) {
     set_error("ed_lanczos_solve: not converged after %d steps", j);
     return ED_ERR_NOT_CONVERGED;
   }
   return ED_OK;
+}
+
+extern "C" ed_status ed_lanczos_solve(const ed_basis* b, const ed_params* p, const ed_opts* o,
+                                      const void* f1, void* stream, double* E0, int32_t* steps,
+                                      double* alpha, double* beta, double* E0_hist) {
+  clear_error();
+  ED_CHECK_ARG(b != nullptr && p != nullptr, "ed_lanczos_solve: basis or params is NULL");
+  ED_CHECK_ARG(E0 != nullptr, "ed_lanczos_solve: E0 is NULL");
+  ed_status r = check_opts(o);
+  if (r != ED_OK) return r;
+  cudaStream_t user = (cudaStream_t)stream;
+  SolveCache* C = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    if (!b->solve_cache) {
+      SolveCache* nc = new SolveCache();
+      if (cudaStreamCreateWithFlags(&nc->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete nc;
+        set_error("ed_lanczos_solve: stream creation failed");
+        return ED_ERR_CUDA;
+      }
+      b->solve_cache = nc;
+    }
+    C = (SolveCache*)b->solve_cache;
+  }
+  std::unique_lock<std::mutex> lk(C->mu, std::try_to_lock);
+  const bool cached = lk.owns_lock();
+  cudaStream_t s = C->stream;
+  if (!cached) ED_TRY_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  // the run starts after the work already queued on the caller's stream
+  cudaEvent_t ev = nullptr;
+  ED_TRY_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaEventRecord(ev, user);
+  cudaStreamWaitEvent(s, ev, 0);
+  cudaEventDestroy(ev);
+  ed_lanczos* st = nullptr;
+  if (cached) {
+    for (auto& e : C->entries)
+      if (e.dtype == (int)o->dtype && e.schedule == o->schedule) st = e.st;
+    if (!st) {
+      if ((r = lz_alloc(b, o, s, &st)) != ED_OK) return r;
+      C->entries.push_back({(int)o->dtype, o->schedule, st});
+    }
+    return solve_on(st, b, p, o, f1, E0, steps, alpha, beta, E0_hist);
+  }
+  if ((r = lz_alloc(b, o, s, &st)) != ED_OK) {
+    cudaStreamDestroy(s);
+    return r;
+  }
+  r = solve_on(st, b, p, o, f1, E0, steps, alpha, beta, E0_hist);
+  ed_lanczos_destroy(st);
+  cudaStreamDestroy(s);
+  return r;
 }

@@ -36,10 +36,10 @@ __device__ __forceinline__ int sturm_count(const double* a, const double* b, int
   return cnt;
 }
 
-// lambda_min(T_m) by block-parallel multisection: each round evaluates the Sturm count at
-// blockDim.x interior points of the bracket and keeps the sub-interval holding the first
-// eigenvalue, until the bracket stops shrinking in FP64. Returns the upper end (valid in
-// every thread).
+// lambda_min(T_m) by multisection: each round evaluates the Sturm count at 32 interior
+// points of the bracket (one warp; the FP64 work per round is what limits this on GB300) and
+// keeps the sub-interval holding the first eigenvalue, until the bracket stops shrinking in
+// FP64. Called by the whole block; returns the upper end (valid in every thread).
 __device__ __forceinline__ double sturm_lowest(const double* a, const double* b, int m) {
   __shared__ double lo_s, hi_s;
   __shared__ int first_s;
@@ -55,15 +55,17 @@ __device__ __forceinline__ double sturm_lowest(const double* a, const double* b,
     hi_s = hi + 1e-15 * span + 1e-300;
   }
   __syncthreads();
-  const int P = blockDim.x;
-  for (int round = 0; round < 64; ++round) {
+  const int P = 32;
+  for (int round = 0; round < 128; ++round) {
     const double lo = lo_s, hi = hi_s;
     const double w = (hi - lo) / (double)(P + 1);
     if (threadIdx.x == 0) first_s = P;
     __syncthreads();
-    const double x = lo + w * (double)(threadIdx.x + 1);
-    const bool valid = x > lo && x < hi;
-    if (valid && sturm_count(a, b, m, x) >= 1) atomicMin(&first_s, (int)threadIdx.x);
+    if (threadIdx.x < P) {
+      const double x = lo + w * (double)(threadIdx.x + 1);
+      const bool valid = x > lo && x < hi;
+      if (valid && sturm_count(a, b, m, x) >= 1) atomicMin(&first_s, (int)threadIdx.x);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
       const int k = first_s;

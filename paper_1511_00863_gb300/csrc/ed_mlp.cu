@@ -2,11 +2,13 @@
 // (and U) predicts the ground-state amplitude; its predictions over the whole basis become
 // f_1 of Algorithm 1 (Sec. 2.2). The paper has no learned component.
 //
-//   x = (up bits, down bits, U/8) in R^(2L+1); h1 = tanh(W1^T x + b1); h2 = tanh(W2^T h1 + b2);
+//   x = (up bits, down bits, bf16(U/8)) in R^(2L+1); h1 = tanh(W1^T x + b1);
+//   h2 = tanh(W2^T bf16(h1) + b2);
 //   (a, z) = W3^T h2 + b3; psi0 = sign(z) exp(a).       64 hidden units per layer.
 // Weights: FP32 master copy (Adam, Kingma & Ba 2015), rounded to bfloat16 (nearest even)
-// for every forward pass; FP32 accumulation. The input is sparse (N_up + N_dn set bits), so
-// the first layer adds the weight rows of the set bits instead of a dense product.
+// for every forward pass; FP32 accumulation. The U feature and the first layer's output
+// enter the next product rounded to bfloat16 (the operands of the tensor-core products of
+// the inference kernel); the backward pass treats these roundings as the identity.
 // Training: samples drawn uniformly from the basis with weight dim * psi^2; loss per sample
 // (a - log|psi|)^2 + log(1 + exp(-sign(psi) z)); deterministic per-CTA gradient partials
 // reduced in a fixed order.
@@ -51,53 +53,157 @@ __device__ __forceinline__ void load_weights(const float* __restrict__ params, i
   __syncthreads();
 }
 
-// First layer pre-activation for one state: b1 + rows of W1 for the set bits + (U/8) row.
-__device__ __forceinline__ void layer1(const float* sw, const MlpDims& d, uint32_t ub, uint32_t db,
-                                       float u8, float* h1) {
-  const float* W1 = sw + d.oW1;
-#pragma unroll 8
-  for (int o = 0; o < kH; ++o) h1[o] = sw[d.ob1 + o] + u8 * W1[(d.nin - 1) * kH + o];
-  while (ub) {
-    const int i = __ffs(ub) - 1;
-    ub &= ub - 1;
-#pragma unroll 8
-    for (int o = 0; o < kH; ++o) h1[o] += W1[i * kH + o];
-  }
-  while (db) {
-    const int i = __ffs(db) - 1;
-    db &= db - 1;
-#pragma unroll 8
-    for (int o = 0; o < kH; ++o) h1[o] += W1[(d.L + i) * kH + o];
-  }
-#pragma unroll 8
-  for (int o = 0; o < kH; ++o) h1[o] = tanhf(h1[o]);
+// ------------------------------------------------------------------ inference
+// BF16 tensor-core products (mma.sync m16n8k16, FP32 accumulation): a warp evaluates 16
+// basis states at a time. Thread (g = lane/4, q = lane%4) holds rows g and g+8 of every
+// fragment; the first layer's accumulator fragments are, after tanh and rounding, exactly
+// the A fragments of the second layer (its K index is the first layer's N index), so the
+// activations never leave registers.
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-// ------------------------------------------------------------------ inference
+__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, uint2 b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
+}
+
+constexpr int kMaxKT1 = (kMaxIn + 15) / 16;  // k-tiles of the first layer
+
+// B fragments of a K x 64 weight block (row-major W[k][n], rows >= K are zero) into shared
+// memory: frag[(kt * 8 + nt) * 32 + lane] = (W[k0..k0+1][n], W[k0+8..k0+9][n]) packed,
+// k0 = kt*16 + 2q, n = nt*8 + g.
+__device__ void build_frags(const float* W, int K, int KT, uint2* frag) {
+  for (int i = threadIdx.x; i < KT * 8 * 32; i += blockDim.x) {
+    const int lane = i & 31, nt = (i >> 5) & 7, kt = i >> 8;
+    const int g = lane >> 2, q = lane & 3;
+    const int n = nt * 8 + g, k0 = kt * 16 + 2 * q;
+    auto w = [&](int k) { return k < K ? W[k * kH + n] : 0.f; };
+    frag[i] = make_uint2(pack_bf16(w(k0), w(k0 + 1)), pack_bf16(w(k0 + 8), w(k0 + 9)));
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kMThreads)
 mlp_infer_kernel(const float* __restrict__ params, int L, float U, const uint32_t* __restrict__ upb,
                  const uint32_t* __restrict__ dnb, int64_t dim_dn, int64_t dim, T* __restrict__ out) {
+  __shared__ uint2 f1[kMaxKT1 * 8 * 32];
+  __shared__ uint2 f2[4 * 8 * 32];
+  __shared__ float sb1[kH], sb2[kH], sW3[2 * kH], sb3[2];
   extern __shared__ float sw[];
   const MlpDims d = mlp_dims(L);
-  load_weights(params, d.P, sw);
-  const float u8 = U * 0.125f;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < dim;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t u = e / dim_dn, dd = e - u * dim_dn;
-    float h1[kH];
-    layer1(sw, d, upb[u], dnb[dd], u8, h1);
-    float a = sw[d.ob3], z = sw[d.ob3 + 1];
-    for (int o = 0; o < kH; ++o) {
-      float s = sw[d.ob2 + o];
-#pragma unroll 16
-      for (int i = 0; i < kH; ++i) s = fmaf(h1[i], sw[d.oW2 + i * kH + o], s);
-      const float h2 = tanhf(s);
-      a = fmaf(h2, sw[d.oW3 + 2 * o], a);
-      z = fmaf(h2, sw[d.oW3 + 2 * o + 1], z);
+  const int KT1 = (d.nin + 15) / 16;
+  load_weights(params, d.P, sw);  // rounded weights
+  build_frags(sw + d.oW1, d.nin, KT1, f1);
+  build_frags(sw + d.oW2, kH, 4, f2);
+  for (int i = threadIdx.x; i < kH; i += blockDim.x) {
+    sb1[i] = sw[d.ob1 + i];
+    sb2[i] = sw[d.ob2 + i];
+    sW3[2 * i] = sw[d.oW3 + 2 * i];
+    sW3[2 * i + 1] = sw[d.oW3 + 2 * i + 1];
+  }
+  if (threadIdx.x < 2) sb3[threadIdx.x] = sw[d.ob3 + threadIdx.x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  const float u8 = bf16r(U * 0.125f);
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  for (int64_t base = wid * 16; base < dim; base += warps * 16) {
+    const int64_t e0 = base + g, e1 = base + g + 8;
+    uint32_t ub0 = 0, db0 = 0, ub1 = 0, db1 = 0;
+    if (e0 < dim) {
+      const int64_t u = e0 / dim_dn;
+      ub0 = upb[u];
+      db0 = dnb[e0 - u * dim_dn];
     }
-    const float v = expf(a);
-    out[e] = (T)(z >= 0.f ? v : -v);
+    if (e1 < dim) {
+      const int64_t u = e1 / dim_dn;
+      ub1 = upb[u];
+      db1 = dnb[e1 - u * dim_dn];
+    }
+    auto feat = [&](uint32_t ub, uint32_t db, int f) -> float {
+      if (f < L) return (float)((ub >> f) & 1u);
+      if (f < 2 * L) return (float)((db >> (f - L)) & 1u);
+      return f == 2 * L ? u8 : 0.f;
+    };
+    // ---- layer 1: acc[nt] = b1 + x W1 over KT1 k-tiles
+    float acc[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const float c0 = sb1[nt * 8 + 2 * q], c1 = sb1[nt * 8 + 2 * q + 1];
+      acc[nt][0] = c0;
+      acc[nt][1] = c1;
+      acc[nt][2] = c0;
+      acc[nt][3] = c1;
+    }
+    for (int kt = 0; kt < KT1; ++kt) {
+      const int c = kt * 16 + 2 * q;
+      uint32_t A[4];
+      A[0] = pack_bf16(feat(ub0, db0, c), feat(ub0, db0, c + 1));
+      A[1] = pack_bf16(feat(ub1, db1, c), feat(ub1, db1, c + 1));
+      A[2] = pack_bf16(feat(ub0, db0, c + 8), feat(ub0, db0, c + 9));
+      A[3] = pack_bf16(feat(ub1, db1, c + 8), feat(ub1, db1, c + 9));
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) mma_bf16(acc[nt], A, f1[(kt * 8 + nt) * 32 + lane]);
+    }
+    // ---- layer 2: A fragments from tanh(layer 1), acc2 = b2 + h1 W2
+    uint32_t A2[4][4];
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt) {
+      A2[kt][0] = pack_bf16(tanhf(acc[2 * kt][0]), tanhf(acc[2 * kt][1]));
+      A2[kt][1] = pack_bf16(tanhf(acc[2 * kt][2]), tanhf(acc[2 * kt][3]));
+      A2[kt][2] = pack_bf16(tanhf(acc[2 * kt + 1][0]), tanhf(acc[2 * kt + 1][1]));
+      A2[kt][3] = pack_bf16(tanhf(acc[2 * kt + 1][2]), tanhf(acc[2 * kt + 1][3]));
+    }
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const float c0 = sb2[nt * 8 + 2 * q], c1 = sb2[nt * 8 + 2 * q + 1];
+      acc[nt][0] = c0;
+      acc[nt][1] = c1;
+      acc[nt][2] = c0;
+      acc[nt][3] = c1;
+    }
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt)
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) mma_bf16(acc[nt], A2[kt], f2[(kt * 8 + nt) * 32 + lane]);
+    // ---- layer 3: partial dot products over this thread's 16 hidden units, then the 4 lanes
+    float a0 = 0.f, z0 = 0.f, a1 = 0.f, z1 = 0.f;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const int c = nt * 8 + 2 * q;
+      const float h00 = tanhf(acc[nt][0]), h01 = tanhf(acc[nt][1]);
+      const float h10 = tanhf(acc[nt][2]), h11 = tanhf(acc[nt][3]);
+      a0 = fmaf(h00, sW3[2 * c], fmaf(h01, sW3[2 * c + 2], a0));
+      z0 = fmaf(h00, sW3[2 * c + 1], fmaf(h01, sW3[2 * c + 3], z0));
+      a1 = fmaf(h10, sW3[2 * c], fmaf(h11, sW3[2 * c + 2], a1));
+      z1 = fmaf(h10, sW3[2 * c + 1], fmaf(h11, sW3[2 * c + 3], z1));
+    }
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+      z0 += __shfl_xor_sync(0xffffffffu, z0, o);
+      a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+      z1 += __shfl_xor_sync(0xffffffffu, z1, o);
+    }
+    if (q == 0) {
+      a0 += sb3[0];
+      z0 += sb3[1];
+      a1 += sb3[0];
+      z1 += sb3[1];
+      if (e0 < dim) {
+        const float v = expf(a0);
+        out[e0] = (T)(z0 >= 0.f ? v : -v);
+      }
+      if (e1 < dim) {
+        const float v = expf(a1);
+        out[e1] = (T)(z1 >= 0.f ? v : -v);
+      }
+    }
   }
 }
 
@@ -118,9 +224,10 @@ mlp_grad_kernel(const float* __restrict__ params, int L, float U, const uint32_t
   float* G2 = H2 + kTile * kH;          // [kTile][kH]
   float* G1 = G2 + kTile * kH;          // [kTile][kH]
   float* DO = G1 + kTile * kH;          // [kTile][2]
+  float* H1B = DO + 2 * kTile;          // [kTile][kH] bf16-rounded h1 (input of layer 2)
   __shared__ double lred[kMThreads];
   load_weights(params, d.P, sw);
-  const float u8 = U * 0.125f;
+  const float u8b = bf16r(U * 0.125f);
   // owned gradient entries: W2 (kH*kH), W1 (nin*kH), W3 (2*kH), b1, b2 (kH each), b3 (2)
   constexpr int kOwnW2 = kH * kH / kMThreads;  // 16
   float gW2[kOwnW2];
@@ -148,7 +255,7 @@ mlp_grad_kernel(const float* __restrict__ params, int L, float U, const uint32_t
         const int64_t u = g / dim_dn, dd = g - u * dim_dn;
         if (f < L) v = (float)((upb[u] >> f) & 1u);
         else if (f < 2 * L) v = (float)((dnb[dd] >> (f - L)) & 1u);
-        else v = u8;
+        else v = u8b;
       }
       X[sidx * kMaxIn + f] = v;
     }
@@ -157,13 +264,15 @@ mlp_grad_kernel(const float* __restrict__ params, int L, float U, const uint32_t
       const int sidx = i / kH, o = i - sidx * kH;
       float s = sw[d.ob1 + o];
       for (int f = 0; f < d.nin; ++f) s = fmaf(X[sidx * kMaxIn + f], sw[d.oW1 + f * kH + o], s);
-      H1[sidx * kH + o] = tanhf(s);
+      const float h = tanhf(s);
+      H1[sidx * kH + o] = h;
+      H1B[sidx * kH + o] = bf16r(h);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kTile * kH; i += blockDim.x) {
       const int sidx = i / kH, o = i - sidx * kH;
       float s = sw[d.ob2 + o];
-      for (int f = 0; f < kH; ++f) s = fmaf(H1[sidx * kH + f], sw[d.oW2 + f * kH + o], s);
+      for (int f = 0; f < kH; ++f) s = fmaf(H1B[sidx * kH + f], sw[d.oW2 + f * kH + o], s);
       H2[sidx * kH + o] = tanhf(s);
     }
     __syncthreads();
@@ -217,7 +326,7 @@ mlp_grad_kernel(const float* __restrict__ params, int L, float U, const uint32_t
       const int e = threadIdx.x + q * kMThreads;  // W2 entry (i, o)
       const int i = e / kH, o = e - i * kH;
       float acc = 0.f;
-      for (int sidx = 0; sidx < kTile; ++sidx) acc = fmaf(H1[sidx * kH + i], G2[sidx * kH + o], acc);
+      for (int sidx = 0; sidx < kTile; ++sidx) acc = fmaf(H1B[sidx * kH + i], G2[sidx * kH + o], acc);
       gW2[q] += acc;
     }
 #pragma unroll
@@ -360,7 +469,7 @@ struct ed_mlp {
 
 namespace {
 size_t grad_smem(const MlpDims& d) {
-  return ((size_t)(d.P + 3) / 4 * 4 + (size_t)kTile * kMaxIn + 4 * (size_t)kTile * kH + 2 * kTile) *
+  return ((size_t)(d.P + 3) / 4 * 4 + (size_t)kTile * kMaxIn + 5 * (size_t)kTile * kH + 2 * kTile) *
          sizeof(float);
 }
 

@@ -330,3 +330,26 @@ def test_fixed_point_matches_native_fp64_from_seeded_start(ed):
         assert np.allclose(out["f64"]["beta"], out["f64n"]["beta"], rtol=1e-11, atol=1e-12)
     finally:
         ed.ed_basis_destroy(b)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f64n"])
+def test_cached_solves_repeat_exactly(ed, dtype):
+    """Solves on one basis reuse its cached workspace and graph; changing U or the start
+    vector between them must not leak state: a repeated solve returns the same bits."""
+    L, bonds, nu, nd = 8, ed_inputs.ring_bonds(8), 3, 3
+    b = ed.ed_build_basis(L, bonds, nu, nd)
+    try:
+        opts = ed.make_opts(max_steps=80, tol=0.0, seed=3, dtype=dtype)
+        first = ed.ed_lanczos_solve(b, 1.0, 4.0, opts)
+        other = ed.ed_lanczos_solve(b, 1.0, 2.0, opts)
+        dim = ed.ed_basis_dims(b)[2]
+        tdt = torch.float32 if dtype == "f32" else torch.float64
+        f1 = torch.tensor(ed_inputs.uniform_pm1(5, dim), device="cuda", dtype=tdt)
+        ed.ed_lanczos_solve(b, 1.0, 4.0, opts, f1=f1)
+        again = ed.ed_lanczos_solve(b, 1.0, 4.0, opts)
+        assert other["E0"] != first["E0"]
+        assert again["E0"] == first["E0"]
+        assert np.array_equal(again["alpha"], first["alpha"])
+        assert np.array_equal(again["beta"], first["beta"])
+    finally:
+        ed.ed_basis_destroy(b)

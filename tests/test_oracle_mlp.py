@@ -15,7 +15,7 @@ def _setup(L=6, B=37, seed=0):
     params = rng.normal(size=P) * 0.4
     up = rng.integers(0, 2 ** L, size=B)
     dn = rng.integers(0, 2 ** L, size=B)
-    x = mlp.features(up, dn, L, 3.0)
+    x = mlp.features(up, dn, L, 3.0, round_inputs=False)
     psi = rng.normal(size=B) * 0.2
     psi[3] = 0.0          # a zero amplitude contributes nothing
     return L, params, x, psi
@@ -62,9 +62,13 @@ def test_forward_special_cases():
     o += mlp.HIDDEN * mlp.HIDDEN + mlp.HIDDEN
     params2[o + 0] = 1.0                              # W3[0][0]
     a, z, _ = mlp.forward(params2, x, L)
-    assert np.allclose(a, [np.tanh(np.tanh(1.0)), np.tanh(np.tanh(1.0))])
+    h1b = float(torch.tensor(np.tanh(1.0), dtype=torch.float32).to(torch.bfloat16))
+    assert np.allclose(a, [np.tanh(h1b), np.tanh(h1b)])
 
 
 def test_features_layout():
     x = mlp.features(np.array([0b0101]), np.array([0b0010]), 4, 4.0)
     assert np.array_equal(x[0], [1, 0, 1, 0, 0, 1, 0, 0, 0.5])
+    # U/8 enters rounded to bfloat16: 3.3/8 = 0.4125 -> 0.412109375
+    x = mlp.features(np.array([0]), np.array([0]), 4, 3.3)
+    assert x[0, -1] == 0.412109375
