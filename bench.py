@@ -31,6 +31,24 @@ import ed_inputs  # noqa: E402
 METRIC = "Lanczos step time & H·v HBM GB/s (% peak); time-to-E0 at 1e-8 vs plain FP64"
 FALLBACK_HBM_GBS = 6800.0
 
+# DRAM bytes per launch of the fused H.v (dram__bytes_read.sum + dram__bytes_write.sum) from
+# one ncu capture (profiles/hv2_kernel_torus4x4_5_5_int64.md), valid only while the kernel's
+# sources are unchanged since that capture.
+KERNEL_SOURCES = ["paper_1511_00863_gb300/csrc/ed_hv2.cu", "paper_1511_00863_gb300/csrc/ed_fixed.cuh",
+                  "paper_1511_00863_gb300/csrc/ed_internal.cuh"]
+MEASURED_TRAFFIC = {
+    ("torus4x4_5_5", "f64"): {"sources_sha256": "ad42fcdd6039a94878abd50cc9c12b9bac4ef1fcdc97fa8c9bffdf57fdd02399", "bytes": 584044800,
+                              "profile": "profiles/hv2_kernel_torus4x4_5_5_int64.md"},
+}
+
+
+def _sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()
+
 
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -391,8 +409,12 @@ def bench_ours(args):
     hv_bytes = 3 * esize * dim + table_bytes  # read f_j, read f_{j-1}, write w; + tables
     hv_launch_ms = hv_ms / K
     achieved = hv_bytes / (hv_launch_ms * 1e-3) / 1e9
+    traffic = None
+    rec = MEASURED_TRAFFIC.get((args.workload, dtype))
+    if rec and args.schedule in (-1, 4) and rec["sources_sha256"] == _sources_sha256():
+        traffic = rec["bytes"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
                 "kernel": "hv_staged_kernel (fused Lanczos H.v)",
                 "bytes_per_launch": hv_bytes, "launch_ms": hv_launch_ms,
                 "peak_source": f"{peak_kind} HBM copy bandwidth"}

@@ -15,7 +15,8 @@ from ctypes import POINTER, byref, c_double, c_int, c_int32, c_int64, c_uint32, 
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libed.so")
+# ED_LIB_PATH selects another build of the same library (e.g. a debug or instrumented one)
+LIB_PATH = os.environ.get("ED_LIB_PATH") or os.path.join(_HERE, "libed.so")
 
 ED_OK, ED_BREAKDOWN = 0, 1
 ED_ERR_ARG, ED_ERR_OOM, ED_ERR_CUDA, ED_ERR_TIMEOUT, ED_ERR_NOT_CONVERGED = -1, -2, -3, -4, -5

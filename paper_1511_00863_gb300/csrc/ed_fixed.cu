@@ -373,12 +373,27 @@ fx_update_kernel(LzScalars* S, int cur, const long long* __restrict__ xc, long l
   I192 q2;
   i192_zero(q2);
   long long mx = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const long long q = xp[i] + round_shift((i128)d * xc[i], k2);
-    xp[i] = q;
+  // n is even (rows are padded to 32 elements): pairs of elements, two pairs in flight
+  const longlong2* c2 = reinterpret_cast<const longlong2*>(xc);
+  longlong2* p2 = reinterpret_cast<longlong2*>(xp);
+  const int64_t n2 = n / 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  auto upd = [&](long long w, long long c) {
+    const long long q = w + round_shift((i128)d * c, k2);
     i192_add(q2, (i128)q * q);
     mx = max(mx, q < 0 ? -q : q);
+    return q;
+  };
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += 2 * stride) {
+    const bool two = i + stride < n2;
+    const longlong2 w0 = p2[i], c0 = c2[i];
+    longlong2 w1 = make_longlong2(0, 0), c1 = make_longlong2(0, 0);
+    if (two) {
+      w1 = p2[i + stride];
+      c1 = c2[i + stride];
+    }
+    p2[i] = make_longlong2(upd(w0.x, c0.x), upd(w0.y, c0.y));
+    if (two) p2[i + stride] = make_longlong2(upd(w1.x, c1.x), upd(w1.y, c1.y));
   }
   fx_block_reduce(q2, mx, pb + 4 * blockIdx.x);
 }

@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "ed_internal.cuh"
@@ -100,11 +101,25 @@ lz_update_kernel(LzScalars* S, int cur, const T* __restrict__ bcur, T* __restric
   if (blockIdx.x == 0 && threadIdx.x == 0) S->alpha[j] = a;
   const T coef = (T)(a * S->scale[cur]);
   DotAcc<T> acc;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+  // n is a multiple of 32 (padded rows): 16-byte vectors of 16 / sizeof(T) elements
+  constexpr int VE = 16 / sizeof(T);
+  typedef typename std::conditional<sizeof(T) == 4, float4, double2>::type Vec;
+  const Vec* c4 = reinterpret_cast<const Vec*>(bcur);
+  Vec* p4 = reinterpret_cast<Vec*>(bprev);
+  const int64_t nv = n / VE;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const T q = bprev[i] - coef * bcur[i];
-    bprev[i] = q;
-    acc.add(q, q);
+    Vec w = p4[i];
+    const Vec c = c4[i];
+    T* wv = reinterpret_cast<T*>(&w);
+    const T* cv = reinterpret_cast<const T*>(&c);
+#pragma unroll
+    for (int e = 0; e < VE; ++e) {
+      const T q = wv[e] - coef * cv[e];
+      wv[e] = q;
+      acc.add(q, q);
+    }
+    p4[i] = w;
   }
   const double v = block_sum(acc.get(), red);
   if (threadIdx.x == 0) pb[blockIdx.x] = v;
