@@ -37,7 +37,7 @@ FALLBACK_HBM_GBS = 6800.0
 KERNEL_SOURCES = ["paper_1511_00863_gb300/csrc/ed_hv2.cu", "paper_1511_00863_gb300/csrc/ed_fixed.cuh",
                   "paper_1511_00863_gb300/csrc/ed_internal.cuh"]
 MEASURED_TRAFFIC = {
-    ("torus4x4_5_5", "f64"): {"sources_sha256": "ad42fcdd6039a94878abd50cc9c12b9bac4ef1fcdc97fa8c9bffdf57fdd02399", "bytes": 584044800,
+    ("torus4x4_5_5", "f64"): {"variant": 4, "sources_sha256": "ad42fcdd6039a94878abd50cc9c12b9bac4ef1fcdc97fa8c9bffdf57fdd02399", "bytes": 584044800,
                               "profile": "profiles/hv2_kernel_torus4x4_5_5_int64.md"},
 }
 
@@ -352,6 +352,7 @@ def bench_ours(args):
     opts = ed.make_opts(max_steps=ed.ED_MAX_STEPS, tol=0.0, seed=w["seed"], dtype=dtype,
                         schedule=args.schedule)
     st = ed.ed_lanczos_init(basis, opts)
+    variant = ed.ed_lanczos_schedule(st)
     ed.ed_lanczos_run(st, t, U, W)
     torch.cuda.synchronize()
     clocks = ClockSampler()
@@ -411,11 +412,11 @@ def bench_ours(args):
     achieved = hv_bytes / (hv_launch_ms * 1e-3) / 1e9
     traffic = None
     rec = MEASURED_TRAFFIC.get((args.workload, dtype))
-    if rec and args.schedule in (-1, 4) and rec["sources_sha256"] == _sources_sha256():
+    if rec and rec["variant"] == variant and rec["sources_sha256"] == _sources_sha256():
         traffic = rec["bytes"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "hv_staged_kernel (fused Lanczos H.v)",
+                "kernel": f"hv2_kernel variant {variant} (fused Lanczos H.v)",
                 "bytes_per_launch": hv_bytes, "launch_ms": hv_launch_ms,
                 "peak_source": f"{peak_kind} HBM copy bandwidth"}
     line = {"metric": METRIC, "value": value, "unit": "lanczos_steps/s", "n_gpus": ws,

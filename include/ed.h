@@ -84,7 +84,10 @@ typedef struct {
  *  seed       SplitMix64 seed of the random start vector when f1 == NULL.
  *  dtype      see ed_dtype; f1 vectors are FP64 for ED_F64 and ED_F64_NATIVE, FP32 for
  *             ED_F32.
- *  schedule   kernel schedule id, -1 = library default. */
+ *  schedule   fused H.v kernel variant (1..12, see ed_lanczos_schedule); -1 = the fastest
+ *             variant for this basis and dtype, found by timing every variant that fits on
+ *             the first run's buffers and remembered by the basis. Batched solves: see
+ *             ed_lanczos_solve_batched. */
 typedef struct {
   int32_t max_steps;
   double tol;
@@ -170,6 +173,9 @@ ed_status ed_lanczos_step(ed_lanczos* st, const ed_params* params, double* alpha
  * on that stream around every fused H.v launch and *hv_ms receives their summed time in
  * milliseconds (this synchronises the stream). */
 ed_status ed_lanczos_run(ed_lanczos* st, const ed_params* params, int32_t nsteps, float* hv_ms);
+
+/* ed_lanczos_schedule - the fused H.v variant the state uses (0: the general kernels). */
+ed_status ed_lanczos_schedule(const ed_lanczos* st, int32_t* schedule);
 
 /* ed_lanczos_energy - E0(j) = lowest eigenvalue of T_j (Sec. 2.2), computed on the device
  * by Sturm-sequence bisection in FP64, and the number of steps j taken. Synchronises. */

@@ -62,6 +62,7 @@ _SIGS = {
     "ed_lanczos_step": (c_int, [c_void_p, POINTER(ed_params), POINTER(c_double), POINTER(c_double)]),
     "ed_lanczos_run": (c_int, [c_void_p, POINTER(ed_params), c_int32, POINTER(ctypes.c_float)]),
     "ed_lanczos_energy": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int32)]),
+    "ed_lanczos_schedule": (c_int, [c_void_p, POINTER(c_int32)]),
     "ed_lanczos_destroy": (None, [c_void_p]),
     "ed_lanczos_solve": (c_int, [c_void_p, POINTER(ed_params), POINTER(ed_opts), c_void_p, c_void_p,
                                  POINTER(c_double), POINTER(c_int32), POINTER(c_double),
@@ -212,6 +213,12 @@ def ed_lanczos_run(st, t: float, U: float, nsteps: int, time_hv: bool = False):
         return ms.value
     _check(_lib.ed_lanczos_run(st, byref(p), nsteps, None))
     return None
+
+
+def ed_lanczos_schedule(st) -> int:
+    v = c_int32()
+    _check(_lib.ed_lanczos_schedule(st, byref(v)))
+    return v.value
 
 
 def ed_lanczos_energy(st) -> tuple[float, int]:

@@ -18,6 +18,7 @@
 //  * Diagonal: U popc(up[u] & dn[d]) x on the integer pipe.
 // FP32 accumulates in FP32 (dot products compensated, FP64 per CTA). The int64 variant is
 // the FP64-accurate path of ed_fixed.cu: exact hop sums, W = round((a S + b n X + c P) 2^k).
+#include <algorithm>
 #include <cstring>
 
 #include "ed_fixed.cuh"
@@ -350,7 +351,12 @@ static size_t hv2_smem(const ed_basis* b, int ld) {
   X(4, long long, 2, 2, false, 256)       \
   X(5, long long, 1, 2, false, 256)       \
   X(6, long long, 1, 2, true, 256)        \
-  X(7, long long, 2, 2, true, 512)
+  X(7, long long, 2, 2, true, 512)        \
+  X(8, float, 2, 4, false, 512)           \
+  X(9, float, 1, 4, false, 512)           \
+  X(10, float, 1, 2, false, 256)          \
+  X(11, long long, 2, 2, false, 512)      \
+  X(12, long long, 1, 2, false, 512)
 
 void hv2_free(Hv2Plan* p) {
   if (!p) return;
@@ -434,6 +440,57 @@ ed_status hv2_build(const ed_basis* b, bool fixed_point, int ld, int schedule, c
 }
 
 int hv2_grid(const Hv2Plan* p) { return p ? p->grid : 0; }
+
+ed_status hv2_autotune(const ed_basis* b, bool fixed_point, int ld, void* x, void* y,
+                       const LzScalars* S, void* partial, cudaStream_t s, int* kind) {
+  *kind = 0;
+  static const int cand_f32[] = {2, 8, 1, 9, 3, 10}, cand_fx[] = {4, 11, 12, 5, 6, 7};
+  const int* cand = fixed_point ? cand_fx : cand_f32;
+  const int nc = 6;
+  const size_t lim = (size_t)optin_smem();
+  constexpr int kReps = 5;
+  cudaEvent_t ev[kReps + 1];
+  for (auto& e : ev) ED_TRY_CUDA(cudaEventCreate(&e));
+  float best = 1e30f;
+  ed_status r = ED_OK;
+  for (int i = 0; i < nc && r == ED_OK; ++i) {
+    size_t sm;
+    int R;
+    bool fx, neg;
+    if (!kind_info(cand[i], b, ld, &sm, &R, &fx, &neg) || fx != fixed_point || sm > lim ||
+        b->up.dim < R)
+      continue;
+    Hv2Plan* p = nullptr;
+    if ((r = hv2_build(b, fixed_point, ld, cand[i], s, &p)) != ED_OK) break;
+    if (!p || p->kind != cand[i]) {
+      hv2_free(p);
+      continue;
+    }
+    // two warm-up launches, then the median of kReps individually timed launches
+    for (int k = 0; k < 2 && r == ED_OK; ++k) r = hv2_launch(p, b, 1.0, 1.0, x, y, S, 0, partial, s);
+    float ms = 0.f;
+    if (r == ED_OK) {
+      cudaEventRecord(ev[0], s);
+      for (int k = 0; k < kReps && r == ED_OK; ++k) {
+        r = hv2_launch(p, b, 1.0, 1.0, x, y, S, 0, partial, s);
+        cudaEventRecord(ev[k + 1], s);
+      }
+      float t[kReps];
+      if (r == ED_OK && cudaEventSynchronize(ev[kReps]) == cudaSuccess) {
+        for (int k = 0; k < kReps; ++k) cudaEventElapsedTime(&t[k], ev[k], ev[k + 1]);
+        std::sort(t, t + kReps);
+        ms = t[kReps / 2];
+      } else if (r == ED_OK) {
+        set_error("H.v autotune: timing failed");
+        r = ED_ERR_CUDA;
+      }
+    }
+    hv2_free(p);
+    if (r == ED_OK && ms < best) best = ms, *kind = cand[i];
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  return r;
+}
 int hv2_kind(const Hv2Plan* p) { return p ? p->kind : 0; }
 
 ed_status hv2_launch(const Hv2Plan* p, const ed_basis* b, double t, double U, const void* x,

@@ -60,6 +60,8 @@ struct ed_basis {
   int32_t* up_order = nullptr;
   // Workspaces of ed_lanczos_solve kept between calls (ed_lanczos.cu); freed with the basis.
   mutable void* solve_cache = nullptr;
+  // Fused H.v variant chosen by timing for this basis, per dtype (0 = not tuned yet).
+  mutable int tuned_kind[3] = {0, 0, 0};
 };
 
 namespace ed {
@@ -149,6 +151,11 @@ ed_status hv2_build(const ed_basis* b, bool fixed_point, int ld, int schedule, c
                     Hv2Plan** out);
 void hv2_free(Hv2Plan* p);
 int hv2_grid(const Hv2Plan* p);
+int hv2_kind(const Hv2Plan* p);
+// Time every fused H.v variant that fits on x (f_j) and y (f_{j-1} / w) with scalars S
+// (zeroed: a neutral step) and return the fastest variant id (0 if none fits).
+ed_status hv2_autotune(const ed_basis* b, bool fixed_point, int ld, void* x, void* y,
+                       const LzScalars* S, void* partial, cudaStream_t s, int* kind);
 ed_status hv2_launch(const Hv2Plan* p, const ed_basis* b, double t, double U, const void* x,
                      void* y, const LzScalars* S, int cur, void* partial, cudaStream_t s);
 

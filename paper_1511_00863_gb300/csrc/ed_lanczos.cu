@@ -406,7 +406,21 @@ static ed_status lz_alloc(const ed_basis* b, const ed_opts* o, cudaStream_t s, e
     return fail(ED_ERR_OOM);
   }
   if (o->dtype != ED_F64_NATIVE) {
-    ed_status pr = hv2_build(b, st->fx, (int)st->ld, o->schedule, s, &st->plan);
+    int sched = o->schedule;
+    if (sched < 0) {
+      // autotune once per basis and dtype: time every variant on this run's zeroed buffers
+      int& tuned = b->tuned_kind[(int)o->dtype];
+      if (tuned == 0) {
+        ED_TRY_CUDA(cudaMemsetAsync(st->S, 0, sizeof(LzScalars), s));
+        for (int i = 0; i < 2; ++i) ED_TRY_CUDA(cudaMemsetAsync(st->B[i], 0, st->n * st->esize, s));
+        int k = 0;
+        ed_status tr = hv2_autotune(b, st->fx, (int)st->ld, st->B[0], st->B[1], st->S, st->pa, s, &k);
+        if (tr != ED_OK) return fail(tr);
+        tuned = k > 0 ? k : -1;
+      }
+      sched = tuned > 0 ? tuned : -1;
+    }
+    ed_status pr = hv2_build(b, st->fx, (int)st->ld, sched, s, &st->plan);
     if (pr != ED_OK) return fail(pr);
   }
   *out = st;
@@ -553,6 +567,13 @@ extern "C" ed_status ed_lanczos_run(ed_lanczos* st, const ed_params* p, int32_t 
     if (e) cudaEventDestroy(e);
   if (r == ED_OK) *hv_ms = total;
   return r;
+}
+
+extern "C" ed_status ed_lanczos_schedule(const ed_lanczos* st, int32_t* schedule) {
+  clear_error();
+  ED_CHECK_ARG(st != nullptr && schedule != nullptr, "ed_lanczos_schedule: NULL argument");
+  *schedule = st->plan ? hv2_kind(st->plan) : 0;
+  return ED_OK;
 }
 
 extern "C" ed_status ed_lanczos_energy(ed_lanczos* st, double* E0, int32_t* steps) {
