@@ -117,8 +117,8 @@ __device__ __forceinline__ long long shift_signed(long long v, int sh) {
 // X_i = (2 u_i - 1) 2^53 exactly (u_i from SplitMix64 as in ed_start_vector), moved to the
 // 2^vb range.
 __global__ void __launch_bounds__(kFxThreads)
-fx_start_kernel(uint64_t seed, int64_t n, int64_t cols, int64_t ld, int vb,
-                long long* __restrict__ X, long long* __restrict__ part) {
+fx_start_kernel(uint64_t seed, int64_t n, int64_t cols, int64_t ld, const int32_t* __restrict__ colpos,
+                int vb, long long* __restrict__ X, long long* __restrict__ part) {
   I192 acc;
   i192_zero(acc);
   long long mx = 0;
@@ -131,7 +131,7 @@ fx_start_kernel(uint64_t seed, int64_t n, int64_t cols, int64_t ld, int vb,
     long long v = (long long)(2ull * (z >> 11)) - (1LL << 53);
     v = shift_signed(v, vb - 53);
     const int64_t r = i / cols, c = i - r * cols;
-    X[r * ld + c] = v;
+    X[r * ld + (colpos ? colpos[c] : c)] = v;
     i192_add(acc, (i128)v * v);
     mx = max(mx, v < 0 ? -v : v);
   }
@@ -171,8 +171,9 @@ __global__ void fx_absmax_final(const unsigned long long* __restrict__ part, int
 // X_i = f_i 2^(vb - E) with |f| < 2^E, by integer manipulation of the IEEE fields (round
 // half up where bits fall off).
 __global__ void __launch_bounds__(kFxThreads)
-fx_copy_in_kernel(const double* __restrict__ f, int64_t n, int64_t cols, int64_t ld, int vb,
-                  int E, long long* __restrict__ X, long long* __restrict__ part) {
+fx_copy_in_kernel(const double* __restrict__ f, int64_t n, int64_t cols, int64_t ld,
+                  const int32_t* __restrict__ colpos, int vb, int E, long long* __restrict__ X,
+                  long long* __restrict__ part) {
   I192 acc;
   i192_zero(acc);
   long long mx = 0;
@@ -189,7 +190,7 @@ fx_copy_in_kernel(const double* __restrict__ f, int64_t n, int64_t cols, int64_t
     long long v = shift_signed(mant, e2 + vb - E);
     if (bits >> 63) v = -v;
     const int64_t r = i / cols, c = i - r * cols;
-    X[r * ld + c] = v;
+    X[r * ld + (colpos ? colpos[c] : c)] = v;
     i192_add(acc, (i128)v * v);
     mx = max(mx, v < 0 ? -v : v);
   }
@@ -426,7 +427,7 @@ fx_finish_kernel(LzScalars* S, int cur, const long long* __restrict__ pb, int nb
 __global__ void __launch_bounds__(kFxThreads)
 fx_psi_accum_kernel(const LzScalars* __restrict__ S, int cur, const double* __restrict__ y, int jstep,
                     const long long* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
-                    long long* __restrict__ P) {
+                    const int32_t* __restrict__ colpos, long long* __restrict__ P) {
   const double c = y[jstep] * S->scale[cur] * 0x1.0p60;
   long long m = 0;
   int k = -1;
@@ -438,7 +439,7 @@ fx_psi_accum_kernel(const LzScalars* __restrict__ S, int cur, const double* __re
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = i / cols, cc = i - r * cols;
-    P[i] += round_shift((i128)m * X[r * ld + cc], k);
+    P[i] += round_shift((i128)m * X[r * ld + (colpos ? colpos[cc] : cc)], k);
   }
 }
 
@@ -553,9 +554,10 @@ static int fx_rows(const ed_basis* b) {
 }
 
 ed_status fx_psi_accum(const ed_basis* b, const LzScalars* S, int cur, const double* y, int j,
-                       const long long* X, int64_t ld, long long* P, cudaStream_t s) {
+                       const long long* X, int64_t ld, const int32_t* colpos, long long* P,
+                       cudaStream_t s) {
   fx_psi_accum_kernel<<<fx_red_grid(b->dim), kFxThreads, 0, s>>>(S, cur, y, j, X, b->up.dim,
-                                                                  b->dn.dim, ld, P);
+                                                                  b->dn.dim, ld, colpos, P);
   ED_TRY_CUDA(cudaGetLastError());
   return ED_OK;
 }
@@ -582,16 +584,17 @@ ed_status fx_prepare(const ed_basis* b) {
 }
 
 ed_status fx_start(const ed_basis* b, const FxRun& fx, uint64_t seed, long long* X, int64_t ld,
-                   LzScalars* S, long long* part, cudaStream_t s) {
+                   const int32_t* colpos, LzScalars* S, long long* part, cudaStream_t s) {
   const int g = fx_red_grid(b->dim);
-  fx_start_kernel<<<g, kFxThreads, 0, s>>>(seed, b->dim, b->dn.dim, ld, fx.vb, X, part);
+  fx_start_kernel<<<g, kFxThreads, 0, s>>>(seed, b->dim, b->dn.dim, ld, colpos, fx.vb, X, part);
   fx_init_kernel<<<1, kFxThreads, 0, s>>>(S, part, g);
   ED_TRY_CUDA(cudaGetLastError());
   return ED_OK;
 }
 
 ed_status fx_copy_in(const ed_basis* b, const FxRun& fx, const double* f1, long long* X,
-                     int64_t ld, LzScalars* S, long long* part, cudaStream_t s) {
+                     int64_t ld, const int32_t* colpos, LzScalars* S, long long* part,
+                     cudaStream_t s) {
   const int g = fx_red_grid(b->dim);
   unsigned long long* pm = reinterpret_cast<unsigned long long*>(part);
   fx_absmax_kernel<<<g, kFxThreads, 0, s>>>(f1, b->dim, pm);
@@ -604,7 +607,8 @@ ed_status fx_copy_in(const ed_basis* b, const FxRun& fx, const double* f1, long 
   ED_CHECK_ARG(ef != 0x7FF, "f1 holds a non-finite value");
   ED_CHECK_ARG(mb != 0, "f1 is the zero vector");
   const int E = ef ? ef - 1022 : -1022;  // |f1| < 2^E
-  fx_copy_in_kernel<<<g, kFxThreads, 0, s>>>(f1, b->dim, b->dn.dim, ld, fx.vb, E, X, part);
+  fx_copy_in_kernel<<<g, kFxThreads, 0, s>>>(f1, b->dim, b->dn.dim, ld, colpos, fx.vb, E, X,
+                                              part);
   fx_init_kernel<<<1, kFxThreads, 0, s>>>(S, part, g);
   ED_TRY_CUDA(cudaGetLastError());
   return ED_OK;

@@ -4,15 +4,18 @@
 //   w = s_cur H B_cur - b_j s_prev B_prev, written over B_prev, plus per-CTA partial sums
 //   of w . f_j; H = H_up (x) I + I (x) H_dn + U D  (Sec. 2.1 Eq. 3, Sec. 4 Eqs. 5-6).
 //
-// Layout: B[u * ld + d], ld = dim_dn rounded up to 32 (pads hold 0 and stay 0).
-// One CTA owns R consecutive up rows; each thread owns V consecutive d per iteration.
+// Layout: B[u * ld + p], ld = dim_dn rounded up to 32 (pads hold 0 and stay 0). The column
+// p of a row is not the down rank d itself: the plan orders the down states by their number
+// of hops (most first, ties by rank), p = colpos[d], so that the 32 V states a warp handles
+// have (nearly) equal hop counts and the down loop runs to the warp's own count instead of
+// the largest one in the basis. The order is internal: vectors enter and leave the library
+// in rank order (colpos is applied by the start, copy-in and ground-state kernels).
+// One CTA owns R consecutive up rows; each thread owns V consecutive columns per iteration.
 //  * The R rows are staged once into shared memory, interleaved so that one vector load
-//    (R elements, 16 bytes for 4 x FP32 or 2 x int64) serves every row for a given d.
-//    (A variant that also stages the negated rows, folding the fermion sign into the
-//    table offset, is kept behind the NEG template flag.)
-//  * Down part: a per-run table gives, for hop k of state d, the byte offset of the
-//    target inside the staged rows (sign in bit 31 for FP32; padding -> a zero slot).
-//    Consecutive threads read consecutive table entries (coalesced vector loads).
+//    (R elements: 8 bytes for 2 x FP32, 16 bytes for 2 x int64) serves every row at once.
+//  * Down part: a per-plan table gives, for hop k of column p, the column of the target
+//    (15 bits, or 31 bits in the wide variant) and the fermion sign (top bit); padding points
+//    at a zero slot. Consecutive threads read consecutive table entries (coalesced).
 //  * Up part: each row's hop list is sorted by sign into shared memory once per CTA; the
 //    threads then stream the neighbour rows with V-wide coalesced loads (L2-resident reuse).
 //  * Diagonal: U popc(up[u] & dn[d]) x on the integer pipe.
@@ -20,6 +23,8 @@
 // the FP64-accurate path of ed_fixed.cu: exact hop sums, W = round((a S + b n X + c P) 2^k).
 #include <algorithm>
 #include <cstring>
+#include <numeric>
+#include <vector>
 
 #include "ed_fixed.cuh"
 #include "ed_internal.cuh"
@@ -67,16 +72,17 @@ __device__ __forceinline__ void stcs_pack(Pack<E, N>* p, const Pack<E, N>& r) {
 
 struct Hv2Args {
   const uint32_t* __restrict__ up_bits;
-  const uint32_t* __restrict__ dn_bits;  // padded to ld (pads 0)
-  const uint32_t* __restrict__ dtab;     // [maxhops_dn][ld] byte offsets
+  const uint32_t* __restrict__ dn_bits;  // by column, padded to ld (pads 0)
+  const void* __restrict__ dtab;         // [maxhops_dn][ld] target column | sign
+  const uint8_t* __restrict__ kc;        // down-loop length per chunk of 32 V columns
   const int32_t* __restrict__ hop_up;    // basis table [maxhops_up][dim_up]
   const int32_t* __restrict__ order;     // up-row visit order (NULL = rank order)
   int64_t dim_up;
-  int ld, maxhops_up, maxhops_dn;
+  int ld, maxhops_up;
   float t, U;  // FP32 variant
 };
 
-template <typename E, int R, int V, bool NEG, int T>
+template <typename E, int R, int V, typename TE, int T>
 __global__ void __launch_bounds__(T)
 hv2_kernel(Hv2Args a, const E* __restrict__ x, E* __restrict__ y, const LzScalars* __restrict__ S,
            int cur, void* __restrict__ partial) {
@@ -87,9 +93,8 @@ hv2_kernel(Hv2Args a, const E* __restrict__ x, E* __restrict__ y, const LzScalar
   const int ld = a.ld;
   const int MH = a.maxhops_up > 0 ? a.maxhops_up : 1;
   Pack<E, R>* xs = reinterpret_cast<Pack<E, R>*>(smem);
-  Pack<E, R>* xsn = xs + (ld + 1);  // negated copy (NEG only)
   int64_t* upoff = reinterpret_cast<int64_t*>(
-      smem + ((size_t)(NEG ? 2 : 1) * (ld + 1) * sizeof(Pack<E, R>) + 15) / 16 * 16);
+      smem + ((size_t)(ld + 1) * sizeof(Pack<E, R>) + 15) / 16 * 16);
   uint32_t* upraw = reinterpret_cast<uint32_t*>(upoff + R * MH);
   const int64_t g0 = (int64_t)blockIdx.x * R;
   int64_t urow[R];
@@ -108,11 +113,6 @@ hv2_kernel(Hv2Args a, const E* __restrict__ x, E* __restrict__ y, const LzScalar
       p.v[r] = (d < ld && u < a.dim_up) ? x[u * ld + d] : E(0);
     }
     xs[d] = p;
-    if (NEG) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) p.v[r] = -p.v[r];
-      xsn[d] = p;
-    }
   }
   // ---- up-hop lists: raw entries, then per row positives first, negatives after
   for (int i = threadIdx.x; i < R * a.maxhops_up; i += T) {
@@ -177,27 +177,30 @@ hv2_kernel(Hv2Args a, const E* __restrict__ x, E* __restrict__ y, const LzScalar
     for (int r = 0; r < R; ++r)
 #pragma unroll
       for (int v = 0; v < V; ++v) acc[r][v] = E(0);
-    // ---- down part: gathers inside the staged rows
-    const uint32_t* tp = a.dtab + d0;
+    // ---- down part: gathers inside the staged rows, to this warp's own hop count
+    const int kc = a.kc[d0 / (32 * V)];
+    const TE* tp = reinterpret_cast<const TE*>(a.dtab) + d0;
 #pragma unroll 2
-    for (int k = 0; k < a.maxhops_dn; ++k) {
-      const Pack<uint32_t, V> e = *reinterpret_cast<const Pack<uint32_t, V>*>(tp + (size_t)k * ld);
+    for (int k = 0; k < kc; ++k) {
+      const Pack<TE, V> e = *reinterpret_cast<const Pack<TE, V>*>(tp + (size_t)k * ld);
 #pragma unroll
       for (int v = 0; v < V; ++v) {
+        const uint32_t ev = e.v[v];
+        uint32_t off, ng;  // byte offset of the target, sign in bit 31
+        if constexpr (sizeof(TE) == 2) {
+          off = (ev & 0x7FFFu) * (uint32_t)sizeof(Pack<E, R>);
+          ng = (ev & 0x8000u) << 16;
+        } else {
+          off = (ev & 0x7FFFFFFFu) * (uint32_t)sizeof(Pack<E, R>);
+          ng = ev & 0x80000000u;
+        }
+        const Pack<E, R> q = *reinterpret_cast<const Pack<E, R>*>(xsb + off);
         if constexpr (sizeof(E) == 4) {
-          const uint32_t ev = e.v[v];
-          const Pack<E, R> q = *reinterpret_cast<const Pack<E, R>*>(xsb + (ev & 0x7FFFFFFFu));
-          const float c = __int_as_float(0x3f800000u | (ev & 0x80000000u));
+          const float c = __int_as_float(0x3f800000u | ng);
 #pragma unroll
           for (int r = 0; r < R; ++r) acc[r][v] = (E)fmaf(c, (float)q.v[r], (float)acc[r][v]);
-        } else if constexpr (NEG) {
-          const Pack<E, R> q = *reinterpret_cast<const Pack<E, R>*>(xsb + e.v[v]);
-#pragma unroll
-          for (int r = 0; r < R; ++r) acc[r][v] += q.v[r];
         } else {
-          const uint32_t ev = e.v[v];
-          const Pack<E, R> q = *reinterpret_cast<const Pack<E, R>*>(xsb + (ev & 0x7FFFFFFFu));
-          const long long m = (long long)((int32_t)ev >> 31);  // 0 or -1
+          const long long m = -(long long)(ng >> 31);  // 0 or -1
 #pragma unroll
           for (int r = 0; r < R; ++r) acc[r][v] += ((long long)q.v[r] ^ m) - m;
         }
@@ -292,41 +295,16 @@ hv2_kernel(Hv2Args a, const E* __restrict__ x, E* __restrict__ y, const LzScalar
   }
 }
 
-// Per-run down table: byte offsets of hop targets inside the staged rows.
-__global__ void hv2_table_kernel(const int32_t* __restrict__ hop_dn, const uint32_t* __restrict__ dn_bits,
-                                 int64_t dim_dn, int ld, int maxhops, uint32_t elem_bytes,
-                                 uint32_t neg_region, int sign_bit, uint32_t* __restrict__ dtab,
-                                 uint32_t* __restrict__ dn_pad) {
-  const int64_t total = (int64_t)maxhops * ld;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total + ld;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    if (i >= total) {
-      const int64_t d = i - total;
-      dn_pad[d] = d < dim_dn ? dn_bits[d] : 0u;
-      continue;
-    }
-    const int64_t k = i / ld, d = i - k * ld;
-    uint32_t off = (uint32_t)ld * elem_bytes;  // zero slot
-    if (d < dim_dn) {
-      const uint32_t e = (uint32_t)hop_dn[k * dim_dn + d];
-      const uint32_t tg = e & kTargetMask;
-      if (tg < (uint32_t)dim_dn) {
-        off = tg * elem_bytes;
-        if (e & kSignBit) off = sign_bit ? (off | kSignBit) : off + neg_region;
-      }
-    }
-    dtab[i] = off;
-  }
-}
-
 // ------------------------------------------------------------------ host side
 struct Hv2Plan {
   int kind = 0;  // 0: not usable; otherwise an index into the launch switch
   size_t smem = 0;
   int grid = 0;
   int ld = 0;
-  uint32_t* dtab = nullptr;
-  uint32_t* dn_pad = nullptr;
+  void* dtab = nullptr;       // [maxhops_dn][ld] entries of 2 or 4 bytes
+  uint8_t* kc = nullptr;      // per chunk of 32 V columns
+  uint32_t* dn_pad = nullptr;  // down bits by column
+  int32_t* colpos = nullptr;  // column of each down rank
 };
 
 static int optin_smem() {
@@ -336,44 +314,39 @@ static int optin_smem() {
   return v;
 }
 
-template <typename E, int R, bool NEG>
-static size_t hv2_smem(const ed_basis* b, int ld) {
-  const int MH = b->up.maxhops > 0 ? b->up.maxhops : 1;
-  return ((size_t)(NEG ? 2 : 1) * (ld + 1) * sizeof(E) * R + 15) / 16 * 16 + (size_t)R * MH * 12;
-}
-
-// Variants (schedule ids): 1-3 FP32 with R = 4, 2, 1 rows per CTA; 4-5 int64 with R = 2, 1
-// (sign by xor); 6-7 int64 with the negated copy staged, R = 1 and 2.
+// Variants (schedule ids): R rows per CTA, V columns per thread, T threads, table entries of
+// 2 bytes (15-bit column, needs ld < 2^15) or 4 bytes (wide).
 #define HV2_KINDS(X)                      \
-  X(1, float, 4, 4, false, 256)           \
-  X(2, float, 2, 4, false, 256)           \
-  X(3, float, 1, 4, false, 256)           \
-  X(4, long long, 2, 2, false, 256)       \
-  X(5, long long, 1, 2, false, 256)       \
-  X(6, long long, 1, 2, true, 256)        \
-  X(7, long long, 2, 2, true, 512)        \
-  X(8, float, 2, 4, false, 512)           \
-  X(9, float, 1, 4, false, 512)           \
-  X(10, float, 1, 2, false, 256)          \
-  X(11, long long, 2, 2, false, 512)      \
-  X(12, long long, 1, 2, false, 512)
+  X(1, float, 4, 4, uint16_t, 256)        \
+  X(2, float, 2, 4, uint16_t, 256)        \
+  X(3, float, 1, 4, uint16_t, 256)        \
+  X(4, long long, 2, 2, uint16_t, 256)    \
+  X(5, long long, 1, 2, uint16_t, 256)    \
+  X(6, long long, 4, 2, uint16_t, 512)    \
+  X(7, float, 4, 4, uint16_t, 512)        \
+  X(8, float, 2, 4, uint16_t, 512)        \
+  X(9, float, 1, 4, uint16_t, 512)        \
+  X(10, float, 1, 2, uint16_t, 256)       \
+  X(11, long long, 2, 2, uint16_t, 512)   \
+  X(12, long long, 1, 2, uint16_t, 512)   \
+  X(13, float, 1, 4, uint32_t, 512)
 
-void hv2_free(Hv2Plan* p) {
-  if (!p) return;
-  if (p->dtab) cudaFree(p->dtab);
-  if (p->dn_pad) cudaFree(p->dn_pad);
-  delete p;
-}
+struct KindInfo {
+  size_t smem;
+  int R, V;
+  bool fx, wide;
+};
 
-// Choose the kernel variant for this basis and element type, build the per-run tables.
-static bool kind_info(int kind, const ed_basis* b, int ld, size_t* sm, int* R, bool* fx, bool* neg) {
+static bool kind_info(int kind, const ed_basis* b, int ld, KindInfo* ki) {
+  const int MH = b->up.maxhops > 0 ? b->up.maxhops : 1;
   switch (kind) {
-#define HV2_INFO(K, E, R_, V, NEG, T)                            \
-    case K:                                                      \
-      *sm = hv2_smem<E, R_, NEG>(b, ld);                         \
-      *R = R_;                                                   \
-      *fx = sizeof(E) == 8;                                      \
-      *neg = NEG;                                                \
+#define HV2_INFO(K, E, R_, V_, TE, T)                                                     \
+    case K:                                                                               \
+      ki->smem = ((size_t)(ld + 1) * sizeof(E) * R_ + 15) / 16 * 16 + (size_t)R_ * MH * 12; \
+      ki->R = R_;                                                                         \
+      ki->V = V_;                                                                         \
+      ki->fx = sizeof(E) == 8;                                                            \
+      ki->wide = sizeof(TE) == 4;                                                         \
       return true;
     HV2_KINDS(HV2_INFO)
 #undef HV2_INFO
@@ -382,54 +355,121 @@ static bool kind_info(int kind, const ed_basis* b, int ld, size_t* sm, int* R, b
   }
 }
 
+// Whether variant `kind` runs this basis in this precision within the shared-memory limit.
+static bool kind_usable(int kind, const ed_basis* b, bool fixed_point, int ld, KindInfo* ki) {
+  if (kind <= 0 || !kind_info(kind, b, ld, ki)) return false;
+  if (ki->fx != fixed_point || ki->smem > (size_t)optin_smem() || b->up.dim < ki->R) return false;
+  return ki->wide || ld <= 0x7FFF;  // the zero slot (column ld) must fit the 15-bit field
+}
+
+void hv2_free(Hv2Plan* p) {
+  if (!p) return;
+  if (p->dtab) cudaFree(p->dtab);
+  if (p->kc) cudaFree(p->kc);
+  if (p->dn_pad) cudaFree(p->dn_pad);
+  if (p->colpos) cudaFree(p->colpos);
+  delete p;
+}
+
+// Column order of the down states (by hop count, most first; ties by rank) and the tables of
+// one variant, built on the host from the basis tables and uploaded.
+static ed_status build_down_tables(const ed_basis* b, int ld, const KindInfo& ki, cudaStream_t s,
+                                   Hv2Plan* p) {
+  const int64_t n = b->dn.dim;
+  const int mh = b->dn.maxhops;
+  std::vector<int32_t> hop((size_t)mh * n);
+  std::vector<uint32_t> bits((size_t)n);
+  if (mh > 0)
+    ED_TRY_CUDA(cudaMemcpyAsync(hop.data(), b->dn.hop, hop.size() * 4, cudaMemcpyDeviceToHost, s));
+  ED_TRY_CUDA(cudaMemcpyAsync(bits.data(), b->dn.bits, bits.size() * 4, cudaMemcpyDeviceToHost, s));
+  ED_TRY_CUDA(cudaStreamSynchronize(s));
+  std::vector<int> cnt((size_t)n, 0);
+  for (int k = 0; k < mh; ++k)
+    for (int64_t d = 0; d < n; ++d)
+      if ((int64_t)((uint32_t)hop[(size_t)k * n + d] & kTargetMask) < n) ++cnt[d];
+  std::vector<int32_t> perm((size_t)n), pos((size_t)n);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(), [&](int32_t x, int32_t y) { return cnt[x] > cnt[y]; });
+  for (int64_t q = 0; q < n; ++q) pos[perm[q]] = (int32_t)q;
+
+  const size_t esz = ki.wide ? 4 : 2;
+  const uint32_t top = ki.wide ? 0x80000000u : 0x8000u;
+  const int rows = mh > 0 ? mh : 1;
+  std::vector<uint8_t> tab((size_t)rows * ld * esz);
+  for (int k = 0; k < rows; ++k)
+    for (int64_t q = 0; q < ld; ++q) {
+      uint32_t e = (uint32_t)ld;  // zero slot
+      if (q < n && k < mh) {
+        const uint32_t h = (uint32_t)hop[(size_t)k * n + perm[q]];
+        const uint32_t tg = h & kTargetMask;
+        if ((int64_t)tg < n) e = (uint32_t)pos[tg] | ((h & kSignBit) ? top : 0u);
+      }
+      const size_t i = (size_t)k * ld + q;
+      if (ki.wide) {
+        std::memcpy(&tab[i * 4], &e, 4);
+      } else {
+        const uint16_t e16 = (uint16_t)e;
+        std::memcpy(&tab[i * 2], &e16, 2);
+      }
+    }
+  const int chunk = 32 * ki.V;
+  const int nchunks = (ld + chunk - 1) / chunk;
+  std::vector<uint8_t> kc((size_t)nchunks, 0);
+  for (int64_t q = 0; q < n; ++q) {
+    uint8_t& m = kc[q / chunk];
+    m = (uint8_t)std::max<int>(m, cnt[perm[q]]);
+  }
+  std::vector<uint32_t> pad((size_t)ld, 0u);
+  for (int64_t q = 0; q < n; ++q) pad[q] = bits[perm[q]];
+
+  if (cudaMalloc(&p->dtab, tab.size()) != cudaSuccess ||
+      cudaMalloc((void**)&p->kc, kc.size()) != cudaSuccess ||
+      cudaMalloc((void**)&p->dn_pad, (size_t)ld * 4) != cudaSuccess ||
+      cudaMalloc((void**)&p->colpos, (size_t)(n > 0 ? n : 1) * 4) != cudaSuccess) {
+    set_error("H.v tables: out of device memory");
+    return ED_ERR_OOM;
+  }
+  ED_TRY_CUDA(cudaMemcpyAsync(p->dtab, tab.data(), tab.size(), cudaMemcpyHostToDevice, s));
+  ED_TRY_CUDA(cudaMemcpyAsync(p->kc, kc.data(), kc.size(), cudaMemcpyHostToDevice, s));
+  ED_TRY_CUDA(cudaMemcpyAsync(p->dn_pad, pad.data(), pad.size() * 4, cudaMemcpyHostToDevice, s));
+  ED_TRY_CUDA(cudaMemcpyAsync(p->colpos, pos.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+  ED_TRY_CUDA(cudaStreamSynchronize(s));  // the host vectors go out of scope
+  return ED_OK;
+}
+
+// Choose the kernel variant for this basis and element type, build the per-plan tables.
 ed_status hv2_build(const ed_basis* b, bool fixed_point, int ld, int schedule, cudaStream_t s,
                     Hv2Plan** out) {
   *out = nullptr;
-  const size_t lim = (size_t)optin_smem();
-  static const int pref_f32[] = {2, 1, 3}, pref_fx[] = {4, 5, 6, 7};
+  // down-loop lengths are stored in 8 bits
+  if (b->dn.maxhops > 255) return ED_OK;  // caller falls back to the general kernels
+  static const int pref_f32[] = {2, 1, 3, 13}, pref_fx[] = {4, 11, 5};
   const int* pref = fixed_point ? pref_fx : pref_f32;
-  const int npref = fixed_point ? 4 : 3;
-  int kind = 0, R = 1;
-  size_t sm = 0;
-  bool neg = false;
+  const int npref = fixed_point ? 3 : 4;
+  int kind = 0;
+  KindInfo ki{};
   for (int i = -1; i < npref && !kind; ++i) {
     const int k = i < 0 ? schedule : pref[i];
-    size_t smk;
-    int Rk;
-    bool fxk, negk;
-    if (k <= 0 || !kind_info(k, b, ld, &smk, &Rk, &fxk, &negk)) continue;
-    if (fxk != fixed_point || smk > lim || b->up.dim < Rk) continue;
-    kind = k, R = Rk, sm = smk, neg = negk;
+    if (kind_usable(k, b, fixed_point, ld, &ki)) kind = k;
   }
   if (!kind) return ED_OK;  // caller falls back to the general kernels
   Hv2Plan* p = new Hv2Plan();
   p->kind = kind;
-  p->smem = sm;
+  p->smem = ki.smem;
   p->ld = ld;
-  p->grid = (int)((b->up.dim + R - 1) / R);
-  const int mh = b->dn.maxhops;
-  if (cudaMalloc((void**)&p->dtab, (size_t)(mh > 0 ? mh : 1) * ld * 4) != cudaSuccess ||
-      cudaMalloc((void**)&p->dn_pad, (size_t)ld * 4) != cudaSuccess) {
+  p->grid = (int)((b->up.dim + ki.R - 1) / ki.R);
+  ed_status r = build_down_tables(b, ld, ki, s, p);
+  if (r != ED_OK) {
     hv2_free(p);
-    set_error("H.v tables: out of device memory");
-    return ED_ERR_OOM;
+    return r;
   }
-  const uint32_t elem_bytes = (uint32_t)((fixed_point ? 8 : 4) * R);
-  const uint32_t neg_region = (uint32_t)((ld + 1) * elem_bytes);
-  const int64_t total = (int64_t)mh * ld + ld;
-  int grid = (int)((total + 255) / 256);
-  if (grid > sm_count() * 8) grid = sm_count() * 8;
-  hv2_table_kernel<<<grid, 256, 0, s>>>(b->dn.hop, b->dn.bits, b->dn.dim, ld, mh, elem_bytes,
-                                        neg_region, neg ? 0 : 1, p->dtab, p->dn_pad);
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) {
-#define HV2_ATTR(K, E, R_, V, NEG, T)                                                    \
-    if (kind == K)                                                                        \
-      e = cudaFuncSetAttribute(hv2_kernel<E, R_, V, NEG, T>,                             \
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    HV2_KINDS(HV2_ATTR)
+  cudaError_t e = cudaSuccess;
+#define HV2_ATTR(K, E, R_, V, TE, T)                                                     \
+  if (kind == K)                                                                          \
+    e = cudaFuncSetAttribute(hv2_kernel<E, R_, V, TE, T>,                                 \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ki.smem);
+  HV2_KINDS(HV2_ATTR)
 #undef HV2_ATTR
-  }
   if (e != cudaSuccess) {
     hv2_free(p);
     set_error("H.v tables: %s", cudaGetErrorString(e));
@@ -439,27 +479,24 @@ ed_status hv2_build(const ed_basis* b, bool fixed_point, int ld, int schedule, c
   return ED_OK;
 }
 
+const int32_t* hv2_colpos(const Hv2Plan* p) { return p ? p->colpos : nullptr; }
+
 int hv2_grid(const Hv2Plan* p) { return p ? p->grid : 0; }
 
 ed_status hv2_autotune(const ed_basis* b, bool fixed_point, int ld, void* x, void* y,
                        const LzScalars* S, void* partial, cudaStream_t s, int* kind) {
   *kind = 0;
-  static const int cand_f32[] = {2, 8, 1, 9, 3, 10}, cand_fx[] = {4, 11, 12, 5, 6, 7};
+  static const int cand_f32[] = {2, 8, 1, 7, 9, 3, 10, 13}, cand_fx[] = {4, 11, 12, 5, 6};
   const int* cand = fixed_point ? cand_fx : cand_f32;
-  const int nc = 6;
-  const size_t lim = (size_t)optin_smem();
+  const int nc = fixed_point ? 5 : 8;
   constexpr int kReps = 5;
   cudaEvent_t ev[kReps + 1];
   for (auto& e : ev) ED_TRY_CUDA(cudaEventCreate(&e));
   float best = 1e30f;
   ed_status r = ED_OK;
   for (int i = 0; i < nc && r == ED_OK; ++i) {
-    size_t sm;
-    int R;
-    bool fx, neg;
-    if (!kind_info(cand[i], b, ld, &sm, &R, &fx, &neg) || fx != fixed_point || sm > lim ||
-        b->up.dim < R)
-      continue;
+    KindInfo ki;
+    if (!kind_usable(cand[i], b, fixed_point, ld, &ki)) continue;
     Hv2Plan* p = nullptr;
     if ((r = hv2_build(b, fixed_point, ld, cand[i], s, &p)) != ED_OK) break;
     if (!p || p->kind != cand[i]) {
@@ -499,17 +536,17 @@ ed_status hv2_launch(const Hv2Plan* p, const ed_basis* b, double t, double U, co
   a.up_bits = b->up.bits;
   a.dn_bits = p->dn_pad;
   a.dtab = p->dtab;
+  a.kc = p->kc;
   a.hop_up = b->up.hop;
   a.order = b->up_order;
   a.dim_up = b->up.dim;
   a.ld = p->ld;
   a.maxhops_up = b->up.maxhops;
-  a.maxhops_dn = b->dn.maxhops;
   a.t = (float)t;
   a.U = (float)U;
-#define HV2_LAUNCH(K, E, R_, V, NEG, T)                                                    \
+#define HV2_LAUNCH(K, E, R_, V, TE, T)                                                     \
   if (p->kind == K)                                                                         \
-    hv2_kernel<E, R_, V, NEG, T><<<p->grid, T, p->smem, s>>>(a, (const E*)x, (E*)y, S, cur, \
+    hv2_kernel<E, R_, V, TE, T><<<p->grid, T, p->smem, s>>>(a, (const E*)x, (E*)y, S, cur, \
                                                              partial);
   HV2_KINDS(HV2_LAUNCH)
 #undef HV2_LAUNCH

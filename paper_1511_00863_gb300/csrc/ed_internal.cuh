@@ -124,13 +124,15 @@ struct FxRun {
   int nmax;    // max doubly occupied sites = min(n_up, n_dn)
 };
 FxRun fx_make(const ed_basis* b);
-// Start vector of SplitMix64 `seed` (exact in fixed point) into X (layout rows x ld), and
-// the run's initial scalars (scale[0], fx_max[0]). part: >= 4 * 4 * sm_count longs.
+// Start vector of SplitMix64 `seed` (exact in fixed point) into X (layout rows x ld, down
+// rank d at column colpos[d], or d if colpos is NULL), and the run's initial scalars
+// (scale[0], fx_max[0]). part: >= 4 * 4 * sm_count longs.
 ed_status fx_start(const ed_basis* b, const FxRun& fx, uint64_t seed, long long* X, int64_t ld,
-                   LzScalars* S, long long* part, cudaStream_t s);
-// Caller FP64 vector f1 (dense) converted to fixed point (exponent from max |f1|).
+                   const int32_t* colpos, LzScalars* S, long long* part, cudaStream_t s);
+// Caller FP64 vector f1 (dense, rank order) converted to fixed point (exponent from max |f1|).
 ed_status fx_copy_in(const ed_basis* b, const FxRun& fx, const double* f1, long long* X,
-                     int64_t ld, LzScalars* S, long long* part, cudaStream_t s);
+                     int64_t ld, const int32_t* colpos, LzScalars* S, long long* part,
+                     cudaStream_t s);
 // One step of Algorithm 1 on the fixed-point buffers (cur holds f_j, the other f_{j-1}).
 ed_status fx_step(const ed_basis* b, const FxRun& fx, double t, double U, long long* const B[2],
                   int cur, int64_t ld, LzScalars* S, long long* pa, long long* pb,
@@ -139,7 +141,8 @@ ed_status fx_prepare(const ed_basis* b);
 // Ground-state vector (ed_lanczos_ground_state): P += round(y_j scale[cur] 2^60 X_cur),
 // and the final normalised, sign-gauged FP64 vector. part: >= 6 * 4 * sm_count longs.
 ed_status fx_psi_accum(const ed_basis* b, const LzScalars* S, int cur, const double* y, int j,
-                       const long long* X, int64_t ld, long long* P, cudaStream_t s);
+                       const long long* X, int64_t ld, const int32_t* colpos, long long* P,
+                       cudaStream_t s);
 ed_status fx_psi_finish(const ed_basis* b, const long long* P, long long* part, double* out,
                         cudaStream_t s);
 
@@ -151,6 +154,8 @@ ed_status hv2_build(const ed_basis* b, bool fixed_point, int ld, int schedule, c
                     Hv2Plan** out);
 void hv2_free(Hv2Plan* p);
 int hv2_grid(const Hv2Plan* p);
+// Column of each down rank in the plan's row layout (device, dim_dn entries).
+const int32_t* hv2_colpos(const Hv2Plan* p);
 int hv2_kind(const Hv2Plan* p);
 // Time every fused H.v variant that fits on x (f_j) and y (f_{j-1} / w) with scalars S
 // (zeroed: a neutral step) and return the fastest variant id (0 if none fits).

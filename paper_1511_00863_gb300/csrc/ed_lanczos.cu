@@ -49,17 +49,18 @@ start_norm_kernel(uint64_t seed, int64_t n, double* __restrict__ partial) {
   if (threadIdx.x == 0) partial[blockIdx.x] = v;
 }
 
-// out[(i / cols) * ld + i % cols] = raw_i / ||raw|| rounded to T.
+// out[(i / cols) * ld + colpos[i % cols]] = raw_i / ||raw|| rounded to T (colpos NULL:
+// the identity).
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
-start_write_kernel(uint64_t seed, int64_t n, int64_t cols, int64_t ld,
+start_write_kernel(uint64_t seed, int64_t n, int64_t cols, int64_t ld, const int32_t* __restrict__ colpos,
                    const double* __restrict__ partial, int nparts, T* __restrict__ out) {
   __shared__ double red[33];
   const double inv = 1.0 / sqrt(block_sum_array(partial, nparts, red));
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = i / cols, c = i - r * cols;
-    out[r * ld + c] = (T)(start_element(seed, (uint64_t)i) * inv);
+    out[r * ld + (colpos ? colpos[c] : c)] = (T)(start_element(seed, (uint64_t)i) * inv);
   }
 }
 
@@ -67,14 +68,14 @@ start_write_kernel(uint64_t seed, int64_t n, int64_t cols, int64_t ld,
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
 copy_in_kernel(const T* __restrict__ src, int64_t n, int64_t cols, int64_t ld,
-               T* __restrict__ dst, double* __restrict__ partial) {
+               const int32_t* __restrict__ colpos, T* __restrict__ dst, double* __restrict__ partial) {
   __shared__ double red[33];
   DotAcc<T> acc;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = i / cols, c = i - r * cols;
     const T v = src[i];
-    dst[r * ld + c] = v;
+    dst[r * ld + (colpos ? colpos[c] : c)] = v;
     acc.add(v, v);
   }
   const double v = block_sum(acc.get(), red);
@@ -281,9 +282,11 @@ extern "C" ed_status ed_start_vector(int64_t dim, uint64_t seed, ed_dtype dtype,
   ED_TRY_CUDA(cudaMallocAsync((void**)&part, g * sizeof(double), s));
   start_norm_kernel<<<g, kRedThreads, 0, s>>>(seed, dim, part);
   if (dtype != ED_F32)
-    start_write_kernel<double><<<g, kRedThreads, 0, s>>>(seed, dim, dim, dim, part, g, (double*)out);
+    start_write_kernel<double><<<g, kRedThreads, 0, s>>>(seed, dim, dim, dim, nullptr, part, g,
+                                                         (double*)out);
   else
-    start_write_kernel<float><<<g, kRedThreads, 0, s>>>(seed, dim, dim, dim, part, g, (float*)out);
+    start_write_kernel<float><<<g, kRedThreads, 0, s>>>(seed, dim, dim, dim, nullptr, part, g,
+                                                        (float*)out);
   cudaError_t e = cudaGetLastError();
   cudaFreeAsync(part, s);
   if (e != cudaSuccess) {
@@ -342,9 +345,11 @@ extern "C" ed_status ed_start_vector_noalloc(int64_t dim, uint64_t seed, ed_dtyp
   cudaStream_t s = (cudaStream_t)stream;
   start_norm_kernel<<<g, kRedThreads, 0, s>>>(seed, dim, part);
   if (dtype != ED_F32)
-    start_write_kernel<double><<<g, kRedThreads, 0, s>>>(seed, dim, dim, dim, part, g, (double*)out);
+    start_write_kernel<double><<<g, kRedThreads, 0, s>>>(seed, dim, dim, dim, nullptr, part, g,
+                                                         (double*)out);
   else
-    start_write_kernel<float><<<g, kRedThreads, 0, s>>>(seed, dim, dim, dim, part, g, (float*)out);
+    start_write_kernel<float><<<g, kRedThreads, 0, s>>>(seed, dim, dim, dim, nullptr, part, g,
+                                                        (float*)out);
   ED_TRY_CUDA(cudaGetLastError());
   return ED_OK;
 }
@@ -451,28 +456,30 @@ static ed_status lz_reset(ed_lanczos* st, const ed_opts* o, const void* f1, int 
   const int g = red_grid(dim);
   ED_CHECK_ARG((int64_t)g <= st->npb, "internal: partial buffer too small");
   st->cur = 0;
+  const int32_t* colpos = hv2_colpos(st->plan);  // NULL: rank order (general kernels)
   if (st->fx) {
     return f1 == nullptr
-        ? fx_start(b, st->fxr, o->seed, (long long*)st->B[0], st->ld, st->S, (long long*)st->pb, s)
-        : fx_copy_in(b, st->fxr, (const double*)f1, (long long*)st->B[0], st->ld, st->S,
+        ? fx_start(b, st->fxr, o->seed, (long long*)st->B[0], st->ld, colpos, st->S,
+                   (long long*)st->pb, s)
+        : fx_copy_in(b, st->fxr, (const double*)f1, (long long*)st->B[0], st->ld, colpos, st->S,
                      (long long*)st->pb, s);
   }
   if (f1 == nullptr) {
     start_norm_kernel<<<g, kRedThreads, 0, s>>>(o->seed, dim, st->pb);
     if (o->dtype == ED_F64_NATIVE)
-      start_write_kernel<double><<<g, kRedThreads, 0, s>>>(o->seed, dim, cols, st->ld, st->pb, g,
-                                                           (double*)st->B[0]);
+      start_write_kernel<double><<<g, kRedThreads, 0, s>>>(o->seed, dim, cols, st->ld, colpos,
+                                                           st->pb, g, (double*)st->B[0]);
     else
-      start_write_kernel<float><<<g, kRedThreads, 0, s>>>(o->seed, dim, cols, st->ld, st->pb, g,
-                                                          (float*)st->B[0]);
+      start_write_kernel<float><<<g, kRedThreads, 0, s>>>(o->seed, dim, cols, st->ld, colpos,
+                                                          st->pb, g, (float*)st->B[0]);
     init_scalars_kernel<<<1, 32, 0, s>>>(st->S, st->pb, g, 0);
   } else {
     if (o->dtype == ED_F64_NATIVE)
       copy_in_kernel<double><<<g, kRedThreads, 0, s>>>((const double*)f1, dim, cols, st->ld,
-                                                       (double*)st->B[0], st->pb);
+                                                       colpos, (double*)st->B[0], st->pb);
     else
       copy_in_kernel<float><<<g, kRedThreads, 0, s>>>((const float*)f1, dim, cols, st->ld,
-                                                      (float*)st->B[0], st->pb);
+                                                      colpos, (float*)st->B[0], st->pb);
     init_scalars_kernel<<<1, kRedThreads, 0, s>>>(st->S, st->pb, g, 1);
   }
   const cudaError_t e = cudaGetLastError();
@@ -641,7 +648,8 @@ extern "C" ed_status ed_lanczos_ground_state(const ed_basis* b, const ed_params*
     return cleanup(ED_ERR_OOM);
   ED_TRY_CUDA(cudaMemsetAsync(P, 0, (size_t)b->dim * sizeof(long long), s));
   for (int j = 1; j <= m; ++j) {
-    if ((r = fx_psi_accum(b, st->S, st->cur, yd, j, (const long long*)st->B[st->cur], st->ld, P, s)) != ED_OK)
+    if ((r = fx_psi_accum(b, st->S, st->cur, yd, j, (const long long*)st->B[st->cur], st->ld,
+                          hv2_colpos(st->plan), P, s)) != ED_OK)
       return cleanup(r);
     if (j < m && (r = lz_launch_step(st, p, s)) != ED_OK) return cleanup(r);
   }
