@@ -13,7 +13,11 @@
 // One CTA owns R consecutive up rows; each thread owns V consecutive columns per iteration.
 //  * The R rows are staged once into shared memory, interleaved so that one vector load
 //    (R elements: 8 bytes for 2 x FP32, 16 bytes for 2 x int64) serves every row at once.
-//  * Down part: a per-plan table gives, for hop k of column p, the column of the target
+//    Column p goes to slot (p & ~(G-1)) | lo[p], lo a permutation inside each aligned group
+//    of G = 128 / (R sizeof(E)) columns (G slots span all 32 banks), chosen on the host so
+//    that the gathers of one request fall in distinct bank groups as far as possible; the
+//    staging and epilogue accesses of a warp stay conflict-free.
+//  * Down part: a per-plan table gives, for hop k of column p, the slot of the target
 //    (15 bits, or 31 bits in the wide variant) and the fermion sign (top bit); padding points
 //    at a zero slot. Consecutive threads read consecutive table entries (coalesced).
 //  * Up part: each row's hop list is sorted by sign into shared memory once per CTA; the
@@ -24,6 +28,7 @@
 #include <algorithm>
 #include <cstring>
 #include <numeric>
+#include <random>
 #include <vector>
 
 #include "ed_fixed.cuh"
@@ -70,11 +75,18 @@ __device__ __forceinline__ void stcs_pack(Pack<E, N>* p, const Pack<E, N>& r) {
   }
 }
 
+// Columns per aligned slot group: G slots of R elements cover the 32 banks once.
+template <typename E, int R>
+__host__ __device__ constexpr int hv2_group() {
+  return 128 / (int)(sizeof(E) * R) < 32 ? 128 / (int)(sizeof(E) * R) : 32;
+}
+
 struct Hv2Args {
   const uint32_t* __restrict__ up_bits;
   const uint32_t* __restrict__ dn_bits;  // by column, padded to ld (pads 0)
   const void* __restrict__ dtab;         // [maxhops_dn][ld] target column | sign
   const uint8_t* __restrict__ kc;        // down-loop length per chunk of 32 V columns
+  const uint8_t* __restrict__ slot_lo;   // [ld] slot of column p within its group of G
   const int32_t* __restrict__ hop_up;    // basis table [maxhops_up][dim_up]
   const int32_t* __restrict__ order;     // up-row visit order (NULL = rank order)
   int64_t dim_up;
@@ -86,6 +98,7 @@ template <typename E, int R, int V, typename TE, int T>
 __global__ void __launch_bounds__(T)
 hv2_kernel(Hv2Args a, const E* __restrict__ x, E* __restrict__ y, const LzScalars* __restrict__ S,
            int cur, void* __restrict__ partial) {
+  constexpr int G = hv2_group<E, R>();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int npos_s[R], nneg_s[R];
   __shared__ double red[33];
@@ -112,7 +125,7 @@ hv2_kernel(Hv2Args a, const E* __restrict__ x, E* __restrict__ y, const LzScalar
       const int64_t u = urow[r];
       p.v[r] = (d < ld && u < a.dim_up) ? x[u * ld + d] : E(0);
     }
-    xs[d] = p;
+    xs[d < ld ? (d & ~(G - 1)) | a.slot_lo[d] : ld] = p;
   }
   // ---- up-hop lists: raw entries, then per row positives first, negatives after
   for (int i = threadIdx.x; i < R * a.maxhops_up; i += T) {
@@ -226,6 +239,7 @@ hv2_kernel(Hv2Args a, const E* __restrict__ x, E* __restrict__ y, const LzScalar
     }
     // ---- diagonal and the Lanczos epilogue
     const Pack<uint32_t, V> db = *reinterpret_cast<const Pack<uint32_t, V>*>(a.dn_bits + d0);
+    const Pack<uint8_t, V> lo = *reinterpret_cast<const Pack<uint8_t, V>*>(a.slot_lo + d0);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int64_t u = urow[r];
@@ -235,7 +249,7 @@ hv2_kernel(Hv2Args a, const E* __restrict__ x, E* __restrict__ y, const LzScalar
       Pack<E, V> W;
 #pragma unroll
       for (int v = 0; v < V; ++v) {
-        const E xc = xs[d0 + v].v[r];
+        const E xc = xs[((d0 + v) & ~(G - 1)) | lo.v[v]].v[r];
         const int n = __popc(ub[r] & db.v[v]);
         if constexpr (sizeof(E) == 4) {
           const float hx = fmaf(-a.t, (float)acc[r][v], a.U * (float)n * (float)xc);
@@ -303,6 +317,7 @@ struct Hv2Plan {
   int ld = 0;
   void* dtab = nullptr;       // [maxhops_dn][ld] entries of 2 or 4 bytes
   uint8_t* kc = nullptr;      // per chunk of 32 V columns
+  uint8_t* slot_lo = nullptr;  // per column: slot within its group of G
   uint32_t* dn_pad = nullptr;  // down bits by column
   int32_t* colpos = nullptr;  // column of each down rank
 };
@@ -333,7 +348,7 @@ static int optin_smem() {
 
 struct KindInfo {
   size_t smem;
-  int R, V;
+  int R, V, G;
   bool fx, wide;
 };
 
@@ -345,6 +360,7 @@ static bool kind_info(int kind, const ed_basis* b, int ld, KindInfo* ki) {
       ki->smem = ((size_t)(ld + 1) * sizeof(E) * R_ + 15) / 16 * 16 + (size_t)R_ * MH * 12; \
       ki->R = R_;                                                                         \
       ki->V = V_;                                                                         \
+      ki->G = hv2_group<E, R_>();                                                         \
       ki->fx = sizeof(E) == 8;                                                            \
       ki->wide = sizeof(TE) == 4;                                                         \
       return true;
@@ -366,9 +382,105 @@ void hv2_free(Hv2Plan* p) {
   if (!p) return;
   if (p->dtab) cudaFree(p->dtab);
   if (p->kc) cudaFree(p->kc);
+  if (p->slot_lo) cudaFree(p->slot_lo);
   if (p->dn_pad) cudaFree(p->dn_pad);
   if (p->colpos) cudaFree(p->colpos);
   delete p;
+}
+
+// Shared-memory slots of the staged columns. A down-gather request of the kernel is one
+// hop k, one of the V columns of each lane, and a phase of G lanes (G R-element slots fill
+// the 32 banks once); it costs as many wavefronts as the largest number of distinct slots
+// that share a bank group (slot mod G). Slots are permuted only inside aligned groups of G
+// columns, which keeps each warp's staging stores and epilogue loads conflict-free. Local
+// search: take a request with a conflict, move one of its targets from the most loaded
+// bank group to a free one by swapping slots with the column of its group that holds that
+// free bank group; keep the swap unless the affected requests get more expensive. Fixed
+// seed: the result depends only on the tables.
+static std::vector<uint8_t> choose_slots(const std::vector<int32_t>& tcol, const std::vector<int>& kcount,
+                                         int ld, int V, int G) {
+  const int chunk = 32 * V, nch = (ld + chunk - 1) / chunk;
+  std::vector<int> eoff{0}, eel;  // requests: distinct target columns (ld = zero slot)
+  for (int c = 0; c < nch; ++c) {
+    const int kc = kcount[c];
+    for (int k = 0; k < kc; ++k)
+      for (int v = 0; v < V; ++v)
+        for (int p = 0; p < 32; p += G) {
+          const size_t st = eel.size();
+          for (int l = p; l < p + G; ++l) {
+            const int q = c * chunk + l * V + v;
+            if (q >= ld) continue;
+            int t = tcol[(size_t)k * ld + q];
+            if (t < 0) t = ld;
+            if (std::find(eel.begin() + st, eel.end(), t) == eel.end()) eel.push_back(t);
+          }
+          if (eel.size() > st) eoff.push_back((int)eel.size());
+        }
+  }
+  const int ne = (int)eoff.size() - 1, nn = ld + 1;
+  std::vector<int> ioff((size_t)nn + 1, 0), iel;  // requests touching each column
+  for (int i = 0; i < ne; ++i)
+    for (int j = eoff[i]; j < eoff[i + 1]; ++j) ioff[eel[j] + 1]++;
+  for (int i = 0; i < nn; ++i) ioff[i + 1] += ioff[i];
+  iel.resize(ioff[nn]);
+  {
+    std::vector<int> fill(ioff.begin(), ioff.end() - 1);
+    for (int i = 0; i < ne; ++i)
+      for (int j = eoff[i]; j < eoff[i + 1]; ++j) iel[fill[eel[j]]++] = i;
+  }
+  std::vector<uint8_t> col((size_t)nn);
+  for (int i = 0; i < nn; ++i) col[i] = (uint8_t)(i % G);
+  auto cost = [&](int i) {
+    uint8_t h[32] = {0};
+    int m = 0;
+    for (int j = eoff[i]; j < eoff[i + 1]; ++j) m = std::max(m, (int)++h[col[eel[j]]]);
+    return m;
+  };
+  std::vector<uint8_t> ec((size_t)ne);
+  for (int i = 0; i < ne; ++i) ec[i] = (uint8_t)cost(i);
+  std::mt19937 rng(12345u);
+  std::vector<long> mark((size_t)ne, -1);
+  std::vector<int> aff;
+  const long iters = ne > 0 ? 16L * ld : 0;
+  for (long it = 0; it < iters; ++it) {
+    const int e = (int)(rng() % (uint32_t)ne);
+    if (ec[e] <= 1) continue;
+    uint8_t h[32] = {0};
+    int mc = 0, mx = 0;
+    for (int j = eoff[e]; j < eoff[e + 1]; ++j) {
+      const int x = ++h[col[eel[j]]];
+      if (x > mx) mx = x, mc = col[eel[j]];
+    }
+    int cand[32], nc = 0, fr[32], nf = 0;
+    for (int j = eoff[e]; j < eoff[e + 1]; ++j)
+      if (col[eel[j]] == mc && eel[j] < ld) cand[nc++] = eel[j];
+    for (int c = 0; c < G; ++c)
+      if (!h[c]) fr[nf++] = c;
+    if (!nc || !nf) continue;
+    const int a = cand[rng() % (uint32_t)nc];
+    const int tc = fr[rng() % (uint32_t)nf];
+    const int base = a & ~(G - 1);
+    int b = -1;
+    for (int q = base; q < base + G; ++q)
+      if (col[q] == tc) b = q;
+    if (b < 0) continue;
+    aff.clear();
+    for (int j = ioff[a]; j < ioff[a + 1]; ++j)
+      if (mark[iel[j]] != it) mark[iel[j]] = it, aff.push_back(iel[j]);
+    for (int j = ioff[b]; j < ioff[b + 1]; ++j)
+      if (mark[iel[j]] != it) mark[iel[j]] = it, aff.push_back(iel[j]);
+    int before = 0, after = 0;
+    for (int i : aff) before += ec[i];
+    std::swap(col[a], col[b]);
+    for (int i : aff) after += cost(i);
+    if (after <= before) {
+      for (int i : aff) ec[i] = (uint8_t)cost(i);
+    } else {
+      std::swap(col[a], col[b]);
+    }
+  }
+  col.resize((size_t)ld);
+  return col;
 }
 
 // Column order of the down states (by hop count, most first; ties by rank) and the tables of
@@ -392,38 +504,45 @@ static ed_status build_down_tables(const ed_basis* b, int ld, const KindInfo& ki
   std::stable_sort(perm.begin(), perm.end(), [&](int32_t x, int32_t y) { return cnt[x] > cnt[y]; });
   for (int64_t q = 0; q < n; ++q) pos[perm[q]] = (int32_t)q;
 
-  const size_t esz = ki.wide ? 4 : 2;
-  const uint32_t top = ki.wide ? 0x80000000u : 0x8000u;
   const int rows = mh > 0 ? mh : 1;
-  std::vector<uint8_t> tab((size_t)rows * ld * esz);
-  for (int k = 0; k < rows; ++k)
-    for (int64_t q = 0; q < ld; ++q) {
-      uint32_t e = (uint32_t)ld;  // zero slot
-      if (q < n && k < mh) {
-        const uint32_t h = (uint32_t)hop[(size_t)k * n + perm[q]];
-        const uint32_t tg = h & kTargetMask;
-        if ((int64_t)tg < n) e = (uint32_t)pos[tg] | ((h & kSignBit) ? top : 0u);
-      }
-      const size_t i = (size_t)k * ld + q;
-      if (ki.wide) {
-        std::memcpy(&tab[i * 4], &e, 4);
-      } else {
-        const uint16_t e16 = (uint16_t)e;
-        std::memcpy(&tab[i * 2], &e16, 2);
-      }
-    }
   const int chunk = 32 * ki.V;
   const int nchunks = (ld + chunk - 1) / chunk;
-  std::vector<uint8_t> kc((size_t)nchunks, 0);
-  for (int64_t q = 0; q < n; ++q) {
-    uint8_t& m = kc[q / chunk];
-    m = (uint8_t)std::max<int>(m, cnt[perm[q]]);
+  std::vector<int> kcount((size_t)nchunks, 0);
+  for (int64_t q = 0; q < n; ++q) kcount[q / chunk] = std::max(kcount[q / chunk], cnt[perm[q]]);
+  std::vector<int32_t> tcol((size_t)rows * ld, -1);  // target column, -1 = none
+  std::vector<uint8_t> tsgn((size_t)rows * ld, 0);
+  for (int k = 0; k < mh; ++k)
+    for (int64_t q = 0; q < n; ++q) {
+      const uint32_t h = (uint32_t)hop[(size_t)k * n + perm[q]];
+      const uint32_t tg = h & kTargetMask;
+      if ((int64_t)tg < n) {
+        tcol[(size_t)k * ld + q] = pos[tg];
+        tsgn[(size_t)k * ld + q] = (h & kSignBit) ? 1 : 0;
+      }
+    }
+  const std::vector<uint8_t> lo = choose_slots(tcol, kcount, ld, ki.V, ki.G);
+  const size_t esz = ki.wide ? 4 : 2;
+  const uint32_t top = ki.wide ? 0x80000000u : 0x8000u;
+  std::vector<uint8_t> tab((size_t)rows * ld * esz);
+  for (size_t i = 0; i < tcol.size(); ++i) {
+    const int32_t t = tcol[i];
+    uint32_t e = (uint32_t)ld;  // zero slot
+    if (t >= 0) e = ((uint32_t)(t & ~(ki.G - 1)) | lo[t]) | (tsgn[i] ? top : 0u);
+    if (ki.wide) {
+      std::memcpy(&tab[i * 4], &e, 4);
+    } else {
+      const uint16_t e16 = (uint16_t)e;
+      std::memcpy(&tab[i * 2], &e16, 2);
+    }
   }
+  std::vector<uint8_t> kc((size_t)nchunks);
+  for (int c = 0; c < nchunks; ++c) kc[c] = (uint8_t)kcount[c];
   std::vector<uint32_t> pad((size_t)ld, 0u);
   for (int64_t q = 0; q < n; ++q) pad[q] = bits[perm[q]];
 
   if (cudaMalloc(&p->dtab, tab.size()) != cudaSuccess ||
       cudaMalloc((void**)&p->kc, kc.size()) != cudaSuccess ||
+      cudaMalloc((void**)&p->slot_lo, (size_t)ld) != cudaSuccess ||
       cudaMalloc((void**)&p->dn_pad, (size_t)ld * 4) != cudaSuccess ||
       cudaMalloc((void**)&p->colpos, (size_t)(n > 0 ? n : 1) * 4) != cudaSuccess) {
     set_error("H.v tables: out of device memory");
@@ -431,6 +550,7 @@ static ed_status build_down_tables(const ed_basis* b, int ld, const KindInfo& ki
   }
   ED_TRY_CUDA(cudaMemcpyAsync(p->dtab, tab.data(), tab.size(), cudaMemcpyHostToDevice, s));
   ED_TRY_CUDA(cudaMemcpyAsync(p->kc, kc.data(), kc.size(), cudaMemcpyHostToDevice, s));
+  ED_TRY_CUDA(cudaMemcpyAsync(p->slot_lo, lo.data(), lo.size(), cudaMemcpyHostToDevice, s));
   ED_TRY_CUDA(cudaMemcpyAsync(p->dn_pad, pad.data(), pad.size() * 4, cudaMemcpyHostToDevice, s));
   ED_TRY_CUDA(cudaMemcpyAsync(p->colpos, pos.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
   ED_TRY_CUDA(cudaStreamSynchronize(s));  // the host vectors go out of scope
@@ -537,6 +657,7 @@ ed_status hv2_launch(const Hv2Plan* p, const ed_basis* b, double t, double U, co
   a.dn_bits = p->dn_pad;
   a.dtab = p->dtab;
   a.kc = p->kc;
+  a.slot_lo = p->slot_lo;
   a.hop_up = b->up.hop;
   a.order = b->up_order;
   a.dim_up = b->up.dim;
