@@ -84,10 +84,12 @@ typedef struct {
  *  seed       SplitMix64 seed of the random start vector when f1 == NULL.
  *  dtype      see ed_dtype; f1 vectors are FP64 for ED_F64 and ED_F64_NATIVE, FP32 for
  *             ED_F32.
- *  schedule   fused H.v kernel variant (1..12, see ed_lanczos_schedule); -1 = the fastest
- *             variant for this basis and dtype, found by timing every variant that fits on
- *             the first run's buffers and remembered by the basis. Batched solves: see
- *             ed_lanczos_solve_batched. */
+ *  schedule   fused H.v kernel variant (1..7 for ED_F32, 8..13 for ED_F64; a variant of
+ *             the other precision or one that does not fit falls back to the default one,
+ *             see ed_lanczos_schedule); -1 = the fastest variant for this basis and dtype,
+ *             found by timing every variant that fits on the first run's buffers and
+ *             remembered by the basis. ED_F64_NATIVE always uses the general kernels.
+ *             Batched solves: see ed_lanczos_solve_batched. */
 typedef struct {
   int32_t max_steps;
   double tol;

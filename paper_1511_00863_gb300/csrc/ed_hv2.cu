@@ -6,9 +6,9 @@
 //
 // Layout: B[u * ld + p], ld = dim_dn rounded up to 32 (pads hold 0 and stay 0). The column
 // p of a row is not the down rank d itself: the plan orders the down states by their number
-// of hops (most first, ties by rank), p = colpos[d], so that the 32 V states a warp handles
-// have (nearly) equal hop counts and the down loop runs to the warp's own count instead of
-// the largest one in the basis. The order is internal: vectors enter and leave the library
+// of hops (most first; then by the number of hops with sign +1, most first; then by rank),
+// p = colpos[d], so that the 32 V states a warp handles have (nearly) equal hop counts and
+// the down loops run to the warp's own counts instead of the largest ones in the basis. The order is internal: vectors enter and leave the library
 // in rank order (colpos is applied by the start, copy-in and ground-state kernels).
 // One CTA owns R consecutive up rows; each thread owns V consecutive columns per iteration.
 //  * The R rows are staged once into shared memory, interleaved so that one vector load
@@ -18,8 +18,11 @@
 //    that the gathers of one request fall in distinct bank groups as far as possible; the
 //    staging and epilogue accesses of a warp stay conflict-free.
 //  * Down part: a per-plan table gives, for hop k of column p, the slot of the target
-//    (15 bits, or 31 bits in the wide variant) and the fermion sign (top bit); padding points
-//    at a zero slot. Consecutive threads read consecutive table entries (coalesced).
+//    (16 bits); padding points at a zero slot. Within a chunk of 32 V columns (one warp) the
+//    hops with fermion sign +1 come first and those with -1 after, each group padded to the
+//    chunk's largest count, so the sign costs nothing per element; the columns are ordered
+//    by (hop count, positive-hop count) to keep that padding small. Consecutive threads
+//    read consecutive table entries (coalesced).
 //  * Up part: each row's hop list is sorted by sign into shared memory once per CTA; the
 //    threads then stream the neighbour rows with V-wide coalesced loads (L2-resident reuse).
 //  * Diagonal: U popc(up[u] & dn[d]) x on the integer pipe.
@@ -84,8 +87,8 @@ __host__ __device__ constexpr int hv2_group() {
 struct Hv2Args {
   const uint32_t* __restrict__ up_bits;
   const uint32_t* __restrict__ dn_bits;  // by column, padded to ld (pads 0)
-  const void* __restrict__ dtab;         // [maxhops_dn][ld] target column | sign
-  const uint8_t* __restrict__ kc;        // down-loop length per chunk of 32 V columns
+  const uint16_t* __restrict__ dtab;     // [rows][ld] slot of the hop target
+  const uchar2* __restrict__ kpn;        // per chunk of 32 V columns: positive, negative rows
   const uint8_t* __restrict__ slot_lo;   // [ld] slot of column p within its group of G
   const int32_t* __restrict__ hop_up;    // basis table [maxhops_up][dim_up]
   const int32_t* __restrict__ order;     // up-row visit order (NULL = rank order)
@@ -94,8 +97,8 @@ struct Hv2Args {
   float t, U;  // FP32 variant
 };
 
-template <typename E, int R, int V, typename TE, int T>
-__global__ void __launch_bounds__(T)
+template <typename E, int R, int V, int T, int MB>
+__global__ void __launch_bounds__(T, MB)
 hv2_kernel(Hv2Args a, const E* __restrict__ x, E* __restrict__ y, const LzScalars* __restrict__ S,
            int cur, void* __restrict__ partial) {
   constexpr int G = hv2_group<E, R>();
@@ -179,7 +182,6 @@ hv2_kernel(Hv2Args a, const E* __restrict__ x, E* __restrict__ y, const LzScalar
     cc = S->fx_c;
     ck = S->fx_k;
   }
-  const unsigned char* xsb = smem;
   DotAcc<float> dotf;
   I192 doti;
   i192_zero(doti);
@@ -190,32 +192,46 @@ hv2_kernel(Hv2Args a, const E* __restrict__ x, E* __restrict__ y, const LzScalar
     for (int r = 0; r < R; ++r)
 #pragma unroll
       for (int v = 0; v < V; ++v) acc[r][v] = E(0);
-    // ---- down part: gathers inside the staged rows, to this warp's own hop count
-    const int kc = a.kc[d0 / (32 * V)];
-    const TE* tp = reinterpret_cast<const TE*>(a.dtab) + d0;
+    // ---- down part: gathers inside the staged rows. The chunk's table rows hold its
+    // positive hops first (kpn.x rows), then its negative ones (kpn.y rows); padding points
+    // at the zero slot.
+    const uchar2 kpn = a.kpn[d0 / (32 * V)];
+    const uint16_t* tp = a.dtab + d0;
+    const int kend = kpn.x + kpn.y;
+    if constexpr (sizeof(E) == 4) {
+      // FP32: one loop, the sign as a warp-uniform +-1 factor of the FMA
 #pragma unroll 2
-    for (int k = 0; k < kc; ++k) {
-      const Pack<TE, V> e = *reinterpret_cast<const Pack<TE, V>*>(tp + (size_t)k * ld);
+      for (int k = 0; k < kend; ++k) {
+        const Pack<uint16_t, V> e = *reinterpret_cast<const Pack<uint16_t, V>*>(tp + (size_t)k * ld);
+        const float c = k < kpn.x ? 1.f : -1.f;
 #pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const uint32_t ev = e.v[v];
-        uint32_t off, ng;  // byte offset of the target, sign in bit 31
-        if constexpr (sizeof(TE) == 2) {
-          off = (ev & 0x7FFFu) * (uint32_t)sizeof(Pack<E, R>);
-          ng = (ev & 0x8000u) << 16;
-        } else {
-          off = (ev & 0x7FFFFFFFu) * (uint32_t)sizeof(Pack<E, R>);
-          ng = ev & 0x80000000u;
+        for (int v = 0; v < V; ++v) {
+          const Pack<E, R> q = xs[e.v[v]];
+#pragma unroll
+          for (int r = 0; r < R; ++r) acc[r][v] = fmaf(c, q.v[r], acc[r][v]);
         }
-        const Pack<E, R> q = *reinterpret_cast<const Pack<E, R>*>(xsb + off);
-        if constexpr (sizeof(E) == 4) {
-          const float c = __int_as_float(0x3f800000u | ng);
+      }
+    } else {
+      // int64: plain adds, then plain subtractions
+      int k = 0;
+#pragma unroll 2
+      for (; k < kpn.x; ++k) {
+        const Pack<uint16_t, V> e = *reinterpret_cast<const Pack<uint16_t, V>*>(tp + (size_t)k * ld);
 #pragma unroll
-          for (int r = 0; r < R; ++r) acc[r][v] = (E)fmaf(c, (float)q.v[r], (float)acc[r][v]);
-        } else {
-          const long long m = -(long long)(ng >> 31);  // 0 or -1
+        for (int v = 0; v < V; ++v) {
+          const Pack<E, R> q = xs[e.v[v]];
 #pragma unroll
-          for (int r = 0; r < R; ++r) acc[r][v] += ((long long)q.v[r] ^ m) - m;
+          for (int r = 0; r < R; ++r) acc[r][v] += q.v[r];
+        }
+      }
+#pragma unroll 2
+      for (; k < kend; ++k) {
+        const Pack<uint16_t, V> e = *reinterpret_cast<const Pack<uint16_t, V>*>(tp + (size_t)k * ld);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const Pack<E, R> q = xs[e.v[v]];
+#pragma unroll
+          for (int r = 0; r < R; ++r) acc[r][v] -= q.v[r];
         }
       }
     }
@@ -315,8 +331,8 @@ struct Hv2Plan {
   size_t smem = 0;
   int grid = 0;
   int ld = 0;
-  void* dtab = nullptr;       // [maxhops_dn][ld] entries of 2 or 4 bytes
-  uint8_t* kc = nullptr;      // per chunk of 32 V columns
+  void* dtab = nullptr;       // [rows][ld] 16-bit slots
+  uchar2* kpn = nullptr;      // per chunk of 32 V columns: positive, negative table rows
   uint8_t* slot_lo = nullptr;  // per column: slot within its group of G
   uint32_t* dn_pad = nullptr;  // down bits by column
   int32_t* colpos = nullptr;  // column of each down rank
@@ -329,40 +345,41 @@ static int optin_smem() {
   return v;
 }
 
-// Variants (schedule ids): R rows per CTA, V columns per thread, T threads, table entries of
-// 2 bytes (15-bit column, needs ld < 2^15) or 4 bytes (wide).
-#define HV2_KINDS(X)                      \
-  X(1, float, 4, 4, uint16_t, 256)        \
-  X(2, float, 2, 4, uint16_t, 256)        \
-  X(3, float, 1, 4, uint16_t, 256)        \
-  X(4, long long, 2, 2, uint16_t, 256)    \
-  X(5, long long, 1, 2, uint16_t, 256)    \
-  X(6, long long, 4, 2, uint16_t, 512)    \
-  X(7, float, 4, 4, uint16_t, 512)        \
-  X(8, float, 2, 4, uint16_t, 512)        \
-  X(9, float, 1, 4, uint16_t, 512)        \
-  X(10, float, 1, 2, uint16_t, 256)       \
-  X(11, long long, 2, 2, uint16_t, 512)   \
-  X(12, long long, 1, 2, uint16_t, 512)   \
-  X(13, float, 1, 4, uint32_t, 512)
+// Variants (schedule ids): R rows per CTA, V columns per thread, T threads, MB CTAs per SM
+// the register allocation must allow (the occupancy the smem of small rows permits; the
+// tighter bounds spill a few words).
+#define HV2_KINDS(X)               \
+  X(1, float, 2, 4, 256, 5)        \
+  X(2, float, 1, 4, 512, 3)        \
+  X(3, float, 2, 4, 256, 6)        \
+  X(4, float, 1, 4, 256, 6)        \
+  X(5, float, 2, 4, 512, 2)        \
+  X(6, float, 4, 4, 256, 3)        \
+  X(7, float, 1, 4, 512, 4)        \
+  X(8, long long, 1, 2, 384, 4)    \
+  X(9, long long, 1, 2, 256, 6)    \
+  X(10, long long, 1, 2, 768, 2)   \
+  X(11, long long, 2, 2, 512, 2)   \
+  X(12, long long, 1, 2, 512, 2)   \
+  X(13, long long, 2, 2, 256, 3)   \
+  X(14, float, 2, 4, 256, 4)
 
 struct KindInfo {
   size_t smem;
   int R, V, G;
-  bool fx, wide;
+  bool fx;
 };
 
 static bool kind_info(int kind, const ed_basis* b, int ld, KindInfo* ki) {
   const int MH = b->up.maxhops > 0 ? b->up.maxhops : 1;
   switch (kind) {
-#define HV2_INFO(K, E, R_, V_, TE, T)                                                     \
+#define HV2_INFO(K, E, R_, V_, T, MB)                                                     \
     case K:                                                                               \
       ki->smem = ((size_t)(ld + 1) * sizeof(E) * R_ + 15) / 16 * 16 + (size_t)R_ * MH * 12; \
       ki->R = R_;                                                                         \
       ki->V = V_;                                                                         \
       ki->G = hv2_group<E, R_>();                                                         \
       ki->fx = sizeof(E) == 8;                                                            \
-      ki->wide = sizeof(TE) == 4;                                                         \
       return true;
     HV2_KINDS(HV2_INFO)
 #undef HV2_INFO
@@ -375,13 +392,13 @@ static bool kind_info(int kind, const ed_basis* b, int ld, KindInfo* ki) {
 static bool kind_usable(int kind, const ed_basis* b, bool fixed_point, int ld, KindInfo* ki) {
   if (kind <= 0 || !kind_info(kind, b, ld, ki)) return false;
   if (ki->fx != fixed_point || ki->smem > (size_t)optin_smem() || b->up.dim < ki->R) return false;
-  return ki->wide || ld <= 0x7FFF;  // the zero slot (column ld) must fit the 15-bit field
+  return ld <= 0xFFFF;  // the zero slot (slot ld) must fit the 16-bit table entries
 }
 
 void hv2_free(Hv2Plan* p) {
   if (!p) return;
   if (p->dtab) cudaFree(p->dtab);
-  if (p->kc) cudaFree(p->kc);
+  if (p->kpn) cudaFree(p->kpn);
   if (p->slot_lo) cudaFree(p->slot_lo);
   if (p->dn_pad) cudaFree(p->dn_pad);
   if (p->colpos) cudaFree(p->colpos);
@@ -495,61 +512,71 @@ static ed_status build_down_tables(const ed_basis* b, int ld, const KindInfo& ki
     ED_TRY_CUDA(cudaMemcpyAsync(hop.data(), b->dn.hop, hop.size() * 4, cudaMemcpyDeviceToHost, s));
   ED_TRY_CUDA(cudaMemcpyAsync(bits.data(), b->dn.bits, bits.size() * 4, cudaMemcpyDeviceToHost, s));
   ED_TRY_CUDA(cudaStreamSynchronize(s));
-  std::vector<int> cnt((size_t)n, 0);
+  std::vector<int> np((size_t)n, 0), nn((size_t)n, 0);  // hops with sign +1 / -1
   for (int k = 0; k < mh; ++k)
-    for (int64_t d = 0; d < n; ++d)
-      if ((int64_t)((uint32_t)hop[(size_t)k * n + d] & kTargetMask) < n) ++cnt[d];
+    for (int64_t d = 0; d < n; ++d) {
+      const uint32_t h = (uint32_t)hop[(size_t)k * n + d];
+      if ((int64_t)(h & kTargetMask) < n) ++((h & kSignBit) ? nn : np)[d];
+    }
   std::vector<int32_t> perm((size_t)n), pos((size_t)n);
   std::iota(perm.begin(), perm.end(), 0);
-  std::stable_sort(perm.begin(), perm.end(), [&](int32_t x, int32_t y) { return cnt[x] > cnt[y]; });
+  std::stable_sort(perm.begin(), perm.end(), [&](int32_t x, int32_t y) {
+    const int cx = np[x] + nn[x], cy = np[y] + nn[y];
+    return cx != cy ? cx > cy : np[x] > np[y];
+  });
   for (int64_t q = 0; q < n; ++q) pos[perm[q]] = (int32_t)q;
 
-  const int rows = mh > 0 ? mh : 1;
+  // per chunk: rows [0, kp) positive hops, [kp, kp + kn) negative hops
   const int chunk = 32 * ki.V;
   const int nchunks = (ld + chunk - 1) / chunk;
-  std::vector<int> kcount((size_t)nchunks, 0);
-  for (int64_t q = 0; q < n; ++q) kcount[q / chunk] = std::max(kcount[q / chunk], cnt[perm[q]]);
-  std::vector<int32_t> tcol((size_t)rows * ld, -1);  // target column, -1 = none
-  std::vector<uint8_t> tsgn((size_t)rows * ld, 0);
-  for (int k = 0; k < mh; ++k)
-    for (int64_t q = 0; q < n; ++q) {
+  std::vector<int> kp((size_t)nchunks, 0), kn((size_t)nchunks, 0), kcount((size_t)nchunks, 0);
+  for (int64_t q = 0; q < n; ++q) {
+    kp[q / chunk] = std::max(kp[q / chunk], np[perm[q]]);
+    kn[q / chunk] = std::max(kn[q / chunk], nn[perm[q]]);
+  }
+  int rows = 1;
+  for (int c = 0; c < nchunks; ++c) {
+    if (kp[c] > 255 || kn[c] > 255) {
+      set_error("H.v tables: more than 255 down hops of one sign");
+      return ED_ERR_ARG;
+    }
+    kcount[c] = kp[c] + kn[c];
+    rows = std::max(rows, kcount[c]);
+  }
+  std::vector<int32_t> tcol((size_t)rows * ld, -1);  // target column, -1 = zero slot
+  for (int64_t q = 0; q < n; ++q) {
+    const int c = (int)(q / chunk);
+    int ip = 0, in = kp[c];
+    for (int k = 0; k < mh; ++k) {
       const uint32_t h = (uint32_t)hop[(size_t)k * n + perm[q]];
       const uint32_t tg = h & kTargetMask;
-      if ((int64_t)tg < n) {
-        tcol[(size_t)k * ld + q] = pos[tg];
-        tsgn[(size_t)k * ld + q] = (h & kSignBit) ? 1 : 0;
-      }
-    }
-  const std::vector<uint8_t> lo = choose_slots(tcol, kcount, ld, ki.V, ki.G);
-  const size_t esz = ki.wide ? 4 : 2;
-  const uint32_t top = ki.wide ? 0x80000000u : 0x8000u;
-  std::vector<uint8_t> tab((size_t)rows * ld * esz);
-  for (size_t i = 0; i < tcol.size(); ++i) {
-    const int32_t t = tcol[i];
-    uint32_t e = (uint32_t)ld;  // zero slot
-    if (t >= 0) e = ((uint32_t)(t & ~(ki.G - 1)) | lo[t]) | (tsgn[i] ? top : 0u);
-    if (ki.wide) {
-      std::memcpy(&tab[i * 4], &e, 4);
-    } else {
-      const uint16_t e16 = (uint16_t)e;
-      std::memcpy(&tab[i * 2], &e16, 2);
+      if ((int64_t)tg >= n) continue;
+      const int row = (h & kSignBit) ? in++ : ip++;
+      tcol[(size_t)row * ld + q] = pos[tg];
     }
   }
-  std::vector<uint8_t> kc((size_t)nchunks);
-  for (int c = 0; c < nchunks; ++c) kc[c] = (uint8_t)kcount[c];
+  const std::vector<uint8_t> lo = choose_slots(tcol, kcount, ld, ki.V, ki.G);
+  std::vector<uint16_t> tab((size_t)rows * ld);
+  for (size_t i = 0; i < tcol.size(); ++i) {
+    const int32_t t = tcol[i];
+    tab[i] = (uint16_t)(t >= 0 ? (t & ~(ki.G - 1)) | lo[t] : ld);
+  }
+  std::vector<uchar2> kpnv((size_t)nchunks);
+  for (int c = 0; c < nchunks; ++c) kpnv[c] = make_uchar2((unsigned char)kp[c], (unsigned char)kn[c]);
   std::vector<uint32_t> pad((size_t)ld, 0u);
   for (int64_t q = 0; q < n; ++q) pad[q] = bits[perm[q]];
 
-  if (cudaMalloc(&p->dtab, tab.size()) != cudaSuccess ||
-      cudaMalloc((void**)&p->kc, kc.size()) != cudaSuccess ||
+  if (cudaMalloc(&p->dtab, tab.size() * 2) != cudaSuccess ||
+      cudaMalloc((void**)&p->kpn, kpnv.size() * sizeof(uchar2)) != cudaSuccess ||
       cudaMalloc((void**)&p->slot_lo, (size_t)ld) != cudaSuccess ||
       cudaMalloc((void**)&p->dn_pad, (size_t)ld * 4) != cudaSuccess ||
       cudaMalloc((void**)&p->colpos, (size_t)(n > 0 ? n : 1) * 4) != cudaSuccess) {
     set_error("H.v tables: out of device memory");
     return ED_ERR_OOM;
   }
-  ED_TRY_CUDA(cudaMemcpyAsync(p->dtab, tab.data(), tab.size(), cudaMemcpyHostToDevice, s));
-  ED_TRY_CUDA(cudaMemcpyAsync(p->kc, kc.data(), kc.size(), cudaMemcpyHostToDevice, s));
+  ED_TRY_CUDA(cudaMemcpyAsync(p->dtab, tab.data(), tab.size() * 2, cudaMemcpyHostToDevice, s));
+  ED_TRY_CUDA(cudaMemcpyAsync(p->kpn, kpnv.data(), kpnv.size() * sizeof(uchar2),
+                              cudaMemcpyHostToDevice, s));
   ED_TRY_CUDA(cudaMemcpyAsync(p->slot_lo, lo.data(), lo.size(), cudaMemcpyHostToDevice, s));
   ED_TRY_CUDA(cudaMemcpyAsync(p->dn_pad, pad.data(), pad.size() * 4, cudaMemcpyHostToDevice, s));
   ED_TRY_CUDA(cudaMemcpyAsync(p->colpos, pos.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
@@ -563,9 +590,9 @@ ed_status hv2_build(const ed_basis* b, bool fixed_point, int ld, int schedule, c
   *out = nullptr;
   // down-loop lengths are stored in 8 bits
   if (b->dn.maxhops > 255) return ED_OK;  // caller falls back to the general kernels
-  static const int pref_f32[] = {2, 1, 3, 13}, pref_fx[] = {4, 11, 5};
+  static const int pref_f32[] = {1, 4, 2, 6}, pref_fx[] = {8, 9, 12, 11};
   const int* pref = fixed_point ? pref_fx : pref_f32;
-  const int npref = fixed_point ? 3 : 4;
+  const int npref = 4;
   int kind = 0;
   KindInfo ki{};
   for (int i = -1; i < npref && !kind; ++i) {
@@ -584,9 +611,9 @@ ed_status hv2_build(const ed_basis* b, bool fixed_point, int ld, int schedule, c
     return r;
   }
   cudaError_t e = cudaSuccess;
-#define HV2_ATTR(K, E, R_, V, TE, T)                                                     \
+#define HV2_ATTR(K, E, R_, V, T, MB)                                                     \
   if (kind == K)                                                                          \
-    e = cudaFuncSetAttribute(hv2_kernel<E, R_, V, TE, T>,                                 \
+    e = cudaFuncSetAttribute(hv2_kernel<E, R_, V, T, MB>,                                 \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ki.smem);
   HV2_KINDS(HV2_ATTR)
 #undef HV2_ATTR
@@ -606,9 +633,9 @@ int hv2_grid(const Hv2Plan* p) { return p ? p->grid : 0; }
 ed_status hv2_autotune(const ed_basis* b, bool fixed_point, int ld, void* x, void* y,
                        const LzScalars* S, void* partial, cudaStream_t s, int* kind) {
   *kind = 0;
-  static const int cand_f32[] = {2, 8, 1, 7, 9, 3, 10, 13}, cand_fx[] = {4, 11, 12, 5, 6};
+  static const int cand_f32[] = {1, 2, 3, 4, 5, 6, 7, 14}, cand_fx[] = {8, 9, 10, 11, 12, 13};
   const int* cand = fixed_point ? cand_fx : cand_f32;
-  const int nc = fixed_point ? 5 : 8;
+  const int nc = fixed_point ? 6 : 8;
   constexpr int kReps = 5;
   cudaEvent_t ev[kReps + 1];
   for (auto& e : ev) ED_TRY_CUDA(cudaEventCreate(&e));
@@ -655,8 +682,8 @@ ed_status hv2_launch(const Hv2Plan* p, const ed_basis* b, double t, double U, co
   Hv2Args a;
   a.up_bits = b->up.bits;
   a.dn_bits = p->dn_pad;
-  a.dtab = p->dtab;
-  a.kc = p->kc;
+  a.dtab = (const uint16_t*)p->dtab;
+  a.kpn = p->kpn;
   a.slot_lo = p->slot_lo;
   a.hop_up = b->up.hop;
   a.order = b->up_order;
@@ -665,9 +692,9 @@ ed_status hv2_launch(const Hv2Plan* p, const ed_basis* b, double t, double U, co
   a.maxhops_up = b->up.maxhops;
   a.t = (float)t;
   a.U = (float)U;
-#define HV2_LAUNCH(K, E, R_, V, TE, T)                                                     \
+#define HV2_LAUNCH(K, E, R_, V, T, MB)                                                     \
   if (p->kind == K)                                                                         \
-    hv2_kernel<E, R_, V, TE, T><<<p->grid, T, p->smem, s>>>(a, (const E*)x, (E*)y, S, cur, \
+    hv2_kernel<E, R_, V, T, MB><<<p->grid, T, p->smem, s>>>(a, (const E*)x, (E*)y, S, cur, \
                                                              partial);
   HV2_KINDS(HV2_LAUNCH)
 #undef HV2_LAUNCH
