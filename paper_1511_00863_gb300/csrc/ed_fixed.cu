@@ -371,8 +371,7 @@ fx_update_kernel(LzScalars* S, int cur, const long long* __restrict__ xc, long l
     k2 = ilogb(D) - 61;
     d = llrint(ldexp(D, -k2));
   }
-  I192 q2;
-  i192_zero(q2);
+  A192 q2;
   long long mx = 0;
   // n is even (rows are padded to 32 elements): pairs of elements, two pairs in flight
   const longlong2* c2 = reinterpret_cast<const longlong2*>(xc);
@@ -380,9 +379,10 @@ fx_update_kernel(LzScalars* S, int cur, const long long* __restrict__ xc, long l
   const int64_t n2 = n / 2;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   auto upd = [&](long long w, long long c) {
-    const long long q = w + round_shift((i128)d * c, k2);
-    i192_add(q2, (i128)q * q);
-    mx = max(mx, q < 0 ? -q : q);
+    const long long q = w + round_shift128(smul128(d, c), k2);
+    const unsigned long long aq = q < 0 ? 0ull - (unsigned long long)q : (unsigned long long)q;
+    a192_add_sq(q2, aq);
+    mx = max(mx, (long long)aq);
     return q;
   };
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += 2 * stride) {
@@ -396,7 +396,7 @@ fx_update_kernel(LzScalars* S, int cur, const long long* __restrict__ xc, long l
     p2[i] = make_longlong2(upd(w0.x, c0.x), upd(w0.y, c0.y));
     if (two) p2[i + stride] = make_longlong2(upd(w1.x, c1.x), upd(w1.y, c1.y));
   }
-  fx_block_reduce(q2, mx, pb + 4 * blockIdx.x);
+  fx_block_reduce(a192_get(q2), mx, pb + 4 * blockIdx.x);
 }
 
 __global__ void __launch_bounds__(kRedThreads)

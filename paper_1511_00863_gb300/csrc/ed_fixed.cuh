@@ -93,6 +93,79 @@ __device__ __forceinline__ long long round_shift(i128 p, int k) {
   return (long long)((p + half) >> s);
 }
 
+// The same arithmetic with the 128-bit words spelled out: 64 x 64 -> 128 products from the
+// low and high halves of the multiply, sums as carry chains, and the rounding shift split on
+// the (warp-uniform) shift amount. Results equal those of the i128 forms above bit for bit.
+struct W128 {
+  unsigned long long lo;
+  long long hi;
+};
+
+__device__ __forceinline__ W128 smul128(long long a, long long b) {
+  W128 r;
+  r.lo = (unsigned long long)a * (unsigned long long)b;
+  r.hi = __mul64hi(a, b);
+  return r;
+}
+
+__device__ __forceinline__ W128 add128(const W128& a, const W128& b) {
+  W128 r;
+  asm("add.cc.u64 %0, %2, %4;\n\taddc.u64 %1, %3, %5;"
+      : "=l"(r.lo), "=l"(r.hi)
+      : "l"(a.lo), "l"(a.hi), "l"(b.lo), "l"(b.hi));
+  return r;
+}
+
+// round_shift for a W128 value.
+__device__ __forceinline__ long long round_shift128(const W128& p, int k) {
+  if (k >= 0) return k >= 64 ? 0 : (long long)(p.lo << k);
+  const int s = -k;
+  if (s >= 127) return 0;
+  if (s >= 64) {  // the half (2^(s-1)) reaches the high word only through bit 63 of the low one
+    long long hi = p.hi;
+    if (s == 64) {
+      const unsigned long long l2 = p.lo + (1ull << 63);
+      hi += (l2 < p.lo) ? 1 : 0;
+    } else {
+      hi += 1LL << (s - 65);
+    }
+    return hi >> (s - 64);
+  }
+  const unsigned long long l2 = p.lo + (1ull << (s - 1));
+  const long long h2 = p.hi + ((l2 < p.lo) ? 1 : 0);
+  return (long long)((l2 >> s) | ((unsigned long long)h2 << (64 - s)));
+}
+
+// 192-bit two's complement accumulator as three words (w2:w1:w0).
+struct A192 {
+  unsigned long long w0 = 0, w1 = 0, w2 = 0;
+};
+
+// a += x^2 with x = |v| < 2^64.
+__device__ __forceinline__ void a192_add_sq(A192& a, unsigned long long x) {
+  const unsigned long long lo = x * x, hi = __umul64hi(x, x);
+  asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, %4;\n\taddc.u64 %2, %2, 0;"
+      : "+l"(a.w0), "+l"(a.w1), "+l"(a.w2)
+      : "l"(lo), "l"(hi));
+}
+
+// a += x y (signed).
+__device__ __forceinline__ void a192_add_prod(A192& a, long long x, long long y) {
+  const unsigned long long lo = (unsigned long long)x * (unsigned long long)y;
+  const long long hi = __mul64hi(x, y);
+  const unsigned long long ext = (unsigned long long)(hi >> 63);
+  asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, %4;\n\taddc.u64 %2, %2, %5;"
+      : "+l"(a.w0), "+l"(a.w1), "+l"(a.w2)
+      : "l"(lo), "l"((unsigned long long)hi), "l"(ext));
+}
+
+__device__ __forceinline__ I192 a192_get(const A192& a) {
+  I192 r;
+  r.lo = ((u128)a.w1 << 64) | (u128)a.w0;
+  r.hi = (long long)a.w2;
+  return r;
+}
+
 // Coefficient c = m * 2^e with m an int64 mantissa, |m| < 2^62 for the largest of a set.
 struct FxCoef {
   long long m;

@@ -183,8 +183,7 @@ hv2_kernel(Hv2Args a, const E* __restrict__ x, E* __restrict__ y, const LzScalar
     ck = S->fx_k;
   }
   DotAcc<float> dotf;
-  I192 doti;
-  i192_zero(doti);
+  A192 dota;
 
   for (int d0 = threadIdx.x * V; d0 < ld; d0 += T * V) {
     E acc[R][V];
@@ -274,11 +273,11 @@ hv2_kernel(Hv2Args a, const E* __restrict__ x, E* __restrict__ y, const LzScalar
           dotf.add(w, sc * (float)xc);
         } else {
           const long long xi = (long long)xc;
-          const i128 p = (i128)ca * (long long)acc[r][v] + (i128)cb * (xi * n) +
-                         (i128)cc * (long long)P.v[v];
-          const long long w = round_shift(p, ck);
+          const W128 p = add128(add128(smul128(ca, (long long)acc[r][v]), smul128(cb, xi * n)),
+                                smul128(cc, (long long)P.v[v]));
+          const long long w = round_shift128(p, ck);
           W.v[v] = (E)w;
-          i192_add(doti, (i128)w * xi);
+          a192_add_prod(dota, w, xi);
         }
       }
       stcs_pack(reinterpret_cast<Pack<E, V>*>(yp), W);
@@ -290,6 +289,7 @@ hv2_kernel(Hv2Args a, const E* __restrict__ x, E* __restrict__ y, const LzScalar
   } else {
     // same record layout as the fixed-point reductions: (lo, lo >> 64, hi, max)
     __shared__ unsigned long long sm[32][3];
+    I192 doti = a192_get(dota);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const I192 w = i192_shfl_down(doti, o);
