@@ -353,3 +353,72 @@ def test_cached_solves_repeat_exactly(ed, dtype):
         assert np.array_equal(again["beta"], first["beta"])
     finally:
         ed.ed_basis_destroy(b)
+
+
+# Every fused H.v variant (schedule id) on a lattice whose down rows span several warp chunks
+# with a ragged tail (dim_dn = 462, rows padded to 480), long-range bonds for mixed fermion
+# signs and uneven hop counts: a_j, b_{j+1} of the first steps follow the oracle.
+VARIANT_LATTICE = (11, np.array([[i, (i + 1) % 11] for i in range(11)] +
+                                [[0, 5], [2, 9], [3, 7], [1, 8], [4, 10], [6, 0]]), 3, 5, 1.0, 3.5)
+F32_VARIANTS = [1, 2, 3, 4, 5, 6, 7, 14]
+F64_VARIANTS = [8, 9, 10, 11, 12, 13]
+
+
+@pytest.fixture(scope="module")
+def variant_reference():
+    L, bonds, nu, nd, t, U = VARIANT_LATTICE
+    H = hamiltonian.hamiltonian_csr(L, bonds, nu, nd, t, U)
+    f1 = olz.normalized_start(ed_inputs.start_vector_raw(21, H.shape[0]))
+    return f1, olz.lanczos(lambda v: H @ v, f1, max_steps=16, reorth=False, fixed_steps=True)
+
+
+@pytest.mark.parametrize("variant", F32_VARIANTS + F64_VARIANTS)
+def test_every_variant_follows_oracle(ed, variant, variant_reference):
+    L, bonds, nu, nd, t, U = VARIANT_LATTICE
+    f1, ref = variant_reference
+    dtype = "f32" if variant in F32_VARIANTS else "f64"
+    b = ed.ed_build_basis(L, bonds, nu, nd)
+    try:
+        opts = ed.make_opts(max_steps=16, tol=0.0, seed=1, dtype=dtype, schedule=variant)
+        st = ed.ed_lanczos_init(b, opts)
+        try:
+            assert ed.ed_lanczos_schedule(st) == variant
+        finally:
+            ed.ed_lanczos_destroy(st)
+        fdev = torch.tensor(f1, dtype=torch.float32 if dtype == "f32" else torch.float64,
+                            device="cuda")
+        res = ed.ed_lanczos_solve(b, t, U, opts, f1=fdev, raise_not_converged=False)
+    finally:
+        ed.ed_basis_destroy(b)
+    assert res["steps"] == 16
+    tol = 2e-5 if dtype == "f32" else 1e-11
+    assert np.allclose(res["alpha"], ref.alpha, rtol=tol, atol=tol), (res["alpha"], ref.alpha)
+    assert np.allclose(res["beta"], ref.beta, rtol=tol, atol=tol), (res["beta"], ref.beta)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_down_dimension_above_2_15(ed, dtype):
+    """L=18 ring with N_dn=9: 48,620 down states, so the FP32 fused H.v addresses shared-memory
+    slots above 2^15 (16-bit table entries) and the int64 rows exceed shared memory (general
+    kernels). First steps follow the oracle from the same start vector."""
+    L, bonds, nu, nd, t, U = 18, ed_inputs.ring_bonds(18), 1, 9, 1.0, 2.0
+    H = hamiltonian.hamiltonian_csr(L, bonds, nu, nd, t, U)
+    f1 = olz.normalized_start(ed_inputs.start_vector_raw(5, H.shape[0]))
+    ref = olz.lanczos(lambda v: H @ v, f1, max_steps=6, reorth=False, fixed_steps=True)
+    b = ed.ed_build_basis(L, bonds, nu, nd)
+    try:
+        opts = ed.make_opts(max_steps=6, tol=0.0, seed=1, dtype=dtype)
+        st = ed.ed_lanczos_init(b, opts)
+        try:
+            variant = ed.ed_lanczos_schedule(st)
+        finally:
+            ed.ed_lanczos_destroy(st)
+        assert (variant > 0) == (dtype == "f32")
+        fdev = torch.tensor(f1, dtype=torch.float32 if dtype == "f32" else torch.float64,
+                            device="cuda")
+        res = ed.ed_lanczos_solve(b, t, U, opts, f1=fdev, raise_not_converged=False)
+    finally:
+        ed.ed_basis_destroy(b)
+    tol = 2e-5 if dtype == "f32" else 1e-11
+    assert np.allclose(res["alpha"], ref.alpha, rtol=tol, atol=tol), (res["alpha"], ref.alpha)
+    assert np.allclose(res["beta"], ref.beta, rtol=tol, atol=tol), (res["beta"], ref.beta)
