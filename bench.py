@@ -32,13 +32,20 @@ METRIC = "Lanczos step time & H·v HBM GB/s (% peak); time-to-E0 at 1e-8 vs plai
 FALLBACK_HBM_GBS = 6800.0
 
 # DRAM bytes per launch of the fused H.v (dram__bytes_read.sum + dram__bytes_write.sum) from
-# one ncu capture (profiles/hv2_kernel_torus4x4_5_5_int64.md), valid only while the kernel's
-# sources are unchanged since that capture.
+# one ncu capture per (workload, dtype, variant) (summaries under profiles/), valid only while
+# the kernel's sources are unchanged since that capture.
 KERNEL_SOURCES = ["paper_1511_00863_gb300/csrc/ed_hv2.cu", "paper_1511_00863_gb300/csrc/ed_fixed.cuh",
                   "paper_1511_00863_gb300/csrc/ed_internal.cuh"]
+TRAFFIC_SOURCES_SHA256 = "8ad42c5bc60e24ca7ffd30deaacf3784147d8bbaffc02423fd6beba96d7ccfcf"
 MEASURED_TRAFFIC = {
-    ("torus4x4_5_5", "f64"): {"variant": 4, "sources_sha256": "ad42fcdd6039a94878abd50cc9c12b9bac4ef1fcdc97fa8c9bffdf57fdd02399", "bytes": 584044800,
-                              "profile": "profiles/hv2_kernel_torus4x4_5_5_int64.md"},
+    ("torus4x4_5_5", "f64", 8): {"bytes": 476123136 + 137003264,
+                                 "profile": "profiles/hv2_kernel_torus4x4_5_5_int64.md"},
+    ("torus4x4_5_5", "f64", 9): {"bytes": 458324224 + 135570944,
+                                 "profile": "profiles/hv2_kernel_torus4x4_5_5_int64.md"},
+    ("torus4x4_5_5", "f32", 1): {"bytes": 178430208 + 51420672,
+                                 "profile": "profiles/hv2_kernel_torus4x4_5_5_f32.md"},
+    ("ring16_8_8", "f32", 2): {"bytes": 2448580608 + 634764032,
+                               "profile": "profiles/hv2_kernel_ring16_8_8_f32.md"},
 }
 
 
@@ -411,8 +418,8 @@ def bench_ours(args):
     hv_launch_ms = hv_ms / K
     achieved = hv_bytes / (hv_launch_ms * 1e-3) / 1e9
     traffic = None
-    rec = MEASURED_TRAFFIC.get((args.workload, dtype))
-    if rec and rec["variant"] == variant and rec["sources_sha256"] == _sources_sha256():
+    rec = MEASURED_TRAFFIC.get((args.workload, dtype, variant))
+    if rec and _sources_sha256() == TRAFFIC_SOURCES_SHA256:
         traffic = rec["bytes"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
