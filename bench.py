@@ -34,9 +34,9 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per launch of the fused H.v (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture per (workload, dtype, variant) (summaries under profiles/), valid only while
 # the kernel's sources are unchanged since that capture.
-KERNEL_SOURCES = ["paper_1511_00863_gb300/csrc/ed_hv2.cu", "paper_1511_00863_gb300/csrc/ed_fixed.cuh",
+KERNEL_SOURCES = ["paper_1511_00863_gb300/csrc/ed_hv2_kernel.cuh", "paper_1511_00863_gb300/csrc/ed_fixed.cuh",
                   "paper_1511_00863_gb300/csrc/ed_internal.cuh"]
-TRAFFIC_SOURCES_SHA256 = "8ad42c5bc60e24ca7ffd30deaacf3784147d8bbaffc02423fd6beba96d7ccfcf"
+TRAFFIC_SOURCES_SHA256 = "72ce6a2cff95cb6cc40445dd64251b8a4f6c7b120035d1442b6940a1cc47aa5e"
 MEASURED_TRAFFIC = {
     ("torus4x4_5_5", "f64", 8): {"bytes": 476123136 + 137003264,
                                  "profile": "profiles/hv2_kernel_torus4x4_5_5_int64.md"},
@@ -393,13 +393,21 @@ def bench_ours(args):
         torch.float64 if dtype == "f64" else torch.float32).pin_memory()
     f1_dev = torch.empty(dim, dtype=f1_host.dtype, device="cuda")
     eopts = ed.make_opts(max_steps=K, tol=0.0, seed=w["seed"], dtype=dtype, schedule=args.schedule)
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    f1_dev.copy_(f1_host, non_blocking=True)
-    res = ed.ed_lanczos_solve(basis, t, U, eopts, f1=f1_dev)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+
+    def e2e_call():
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f1_dev.copy_(f1_host, non_blocking=True)
+        r = ed.ed_lanczos_solve(basis, t, U, eopts, f1=f1_dev)
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0
+
+    # The first call on a basis also allocates the cached solve state, builds the fused H.v
+    # plan and captures the step graph: timed and reported on its own; the second call is
+    # the steady-state end-to-end number.
+    _, first_s = e2e_call()
+    res, e2e_s = e2e_call()
     barrier()
     if ws > 1:
         import torch.distributed as dist
@@ -434,7 +442,10 @@ def bench_ours(args):
             "roofline": roofline,
             "e2e": {"value": ws * K / e2e_s, "unit": "lanczos_steps/s",
                     "h2d_bytes_per_step": dim * esize / K, "d2h_bytes_per_step": d2h / K,
-                    "E0": res["E0"], "api": "ed_lanczos_solve (f1 from pinned host memory)"},
+                    "E0": res["E0"], "api": "ed_lanczos_solve (f1 from pinned host memory)",
+                    "first_call_s": first_s,
+                    "note": "second call on the basis; the first also allocates the cached "
+                            "state, builds the H.v plan and captures the graph (first_call_s)"},
             "gpu_launches": 3 * K,
             "clocks": clk}
     if ws == 1 and not args.no_extras:

@@ -319,6 +319,7 @@ extern "C" void ed_basis_destroy(ed_basis* B) {
   cudaGetDevice(&prev);
   if (prev != B->device) cudaSetDevice(B->device);
   lz_cache_free(B);
+  hv2_tables_free(B);
   free_species(B->up);
   free_species(B->dn);
   if (B->binom) cudaFree(B->binom);

@@ -62,6 +62,9 @@ struct ed_basis {
   mutable void* solve_cache = nullptr;
   // Fused H.v variant chosen by timing for this basis, per dtype (0 = not tuned yet).
   mutable int tuned_kind[3] = {0, 0, 0};
+  // Host-built down tables of the fused H.v per (V, G) geometry (ed_hv2.cu); freed with the
+  // basis.
+  mutable void* hv2_tables = nullptr;
 };
 
 namespace ed {
@@ -73,6 +76,8 @@ int sm_count();
 
 // Free the solve workspaces cached on a basis (called by ed_basis_destroy).
 void lz_cache_free(const ed_basis* b);
+// Free the fused H.v down tables cached on a basis (called by ed_basis_destroy).
+void hv2_tables_free(const ed_basis* b);
 
 // Device-resident scalars of one Lanczos run (Algorithm 1). Index j is 1-based as in the
 // paper: alpha[j] = a_j, beta[j] = b_j (beta[1] = 0), E0[j] = lambda_min(T_j).
