@@ -294,14 +294,18 @@ def batched_study(ed):
         def _seq():
             return [ed.ed_lanczos_solve(b, t, U, ed.make_opts(max_steps=600, tol=1e-12, seed=4),
                                         raise_not_converged=False)["E0"] for b, t, U in zip(bases, ts, Us)]
-        ref, t_s = _timed(_seq)
+        # first solve on each basis (state allocation, H.v plan, graph capture), then again
+        ref, t_cold = _timed(_seq)
+        ref2, t_s = _timed(_seq)
         ref = np.array(ref)
         err = np.abs(res["E0"] - ref) / np.maximum(1.0, np.abs(ref))
         return {"instances": len(insts), "sum_dim": int(sum(ed.ed_basis_dims(b)[2] for b in bases)),
                 "batched_f32_s": t_b, "schedule": res["schedule"],
                 "batched_max_steps": int(res["steps"].max()), "sequential_f64_s": t_s,
+                "sequential_f64_first_solves_s": t_cold,
                 "speedup": t_s / t_b, "max_rel_err_vs_f64": float(err.max()),
-                "median_rel_err_vs_f64": float(np.median(err))}
+                "median_rel_err_vs_f64": float(np.median(err)),
+                "repeat_identical": bool(np.array_equal(ref, np.array(ref2)))}
     finally:
         for b in bases:
             ed.ed_basis_destroy(b)

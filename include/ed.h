@@ -86,9 +86,10 @@ typedef struct {
  *             ED_F32.
  *  schedule   fused H.v kernel variant (1..7 for ED_F32, 8..13 for ED_F64; a variant of
  *             the other precision or one that does not fit falls back to the default one,
- *             see ed_lanczos_schedule); -1 = the fastest variant for this basis and dtype,
- *             found by timing every variant that fits on the first run's buffers and
- *             remembered by the basis. ED_F64_NATIVE always uses the general kernels.
+ *             see ed_lanczos_schedule); -1 = for bases of at least 2^22 states, the fastest
+ *             variant for this basis and dtype, found by timing every variant that fits on
+ *             the first run's buffers and remembered by the basis; smaller bases take the
+ *             default variant. ED_F64_NATIVE always uses the general kernels.
  *             Batched solves: see ed_lanczos_solve_batched. */
 typedef struct {
   int32_t max_steps;

@@ -259,7 +259,7 @@ batched_lanczos_kernel(BArgs a) {
         __syncthreads();
         int st = stop_s;
         if (st != 0 || j >= a.max_steps || (j % a.check) == 0) {
-          const double E = sturm_lowest(al, be, j);
+          const double E = sturm_lowest(al, be, j, S->last_E0_step > 0 ? S->last_E0 : NAN);
           if (threadIdx.x == 0) {
             e0[j] = E;
             if (st == 0 && a.tol > 0.0 && S->last_E0_step > 0 &&

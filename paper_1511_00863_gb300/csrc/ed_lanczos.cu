@@ -149,7 +149,7 @@ lz_energy_kernel(const LzScalars* S, double* out) {
     if (threadIdx.x == 0) *out = NAN;
     return;
   }
-  const double E = sturm_lowest(S->alpha, S->beta, j);
+  const double E = sturm_lowest(S->alpha, S->beta, j, NAN);
   if (threadIdx.x == 0) *out = E;
 }
 
@@ -374,6 +374,10 @@ extern "C" void ed_lanczos_destroy(ed_lanczos* st) {
 
 // check_every: compute E0(j) in the finish kernel every this many steps; step_mode: the
 // caller drives the loop, so only breakdown and max_steps stop the run (no tol test).
+// Bases below this many states use the default fused H.v variant order: timing every
+// variant would cost more than their solves.
+constexpr int64_t kAutotuneMinDim = (int64_t)1 << 22;
+
 static ed_status lz_alloc(const ed_basis* b, const ed_opts* o, cudaStream_t s, ed_lanczos** out) {
   *out = nullptr;
   ED_CHECK_ARG(b != nullptr, "basis is NULL");
@@ -415,6 +419,7 @@ static ed_status lz_alloc(const ed_basis* b, const ed_opts* o, cudaStream_t s, e
     if (sched < 0) {
       // autotune once per basis and dtype: time every variant on this run's zeroed buffers
       int& tuned = b->tuned_kind[(int)o->dtype];
+      if (tuned == 0 && b->dim < kAutotuneMinDim) tuned = -1;  // default variant order
       if (tuned == 0) {
         ED_TRY_CUDA(cudaMemsetAsync(st->S, 0, sizeof(LzScalars), s));
         for (int i = 0; i < 2; ++i) ED_TRY_CUDA(cudaMemsetAsync(st->B[i], 0, st->n * st->esize, s));

@@ -422,3 +422,29 @@ def test_down_dimension_above_2_15(ed, dtype):
     tol = 2e-5 if dtype == "f32" else 1e-11
     assert np.allclose(res["alpha"], ref.alpha, rtol=tol, atol=tol), (res["alpha"], ref.alpha)
     assert np.allclose(res["beta"], ref.beta, rtol=tol, atol=tol), (res["beta"], ref.beta)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("lattice", ["torus2x4", "ring10"])
+def test_per_step_lowest_ritz_value_matches_lapack(ed, dtype, lattice):
+    """E0(j) reported for every step (device Sturm multisection, warm-started from E0(j-1))
+    equals lambda_min of T_j assembled from the returned a_j, b_j, by LAPACK, to a few ulps
+    of ||T_j||."""
+    import scipy.linalg
+    if lattice == "torus2x4":
+        L, bonds, nu, nd, U = 8, ed_inputs.torus_bonds(2, 4), 3, 4, 6.0
+    else:
+        L, bonds, nu, nd, U = 10, ed_inputs.ring_bonds(10), 5, 4, 2.5
+    b = ed.ed_build_basis(L, bonds, nu, nd)
+    try:
+        res = ed.ed_lanczos_solve(b, 1.0, U, ed.make_opts(max_steps=120, tol=1e-14, seed=3,
+                                                          dtype=dtype), raise_not_converged=False)
+    finally:
+        ed.ed_basis_destroy(b)
+    a, bt, hist = res["alpha"], res["beta"], res["E0_hist"]
+    n = res["steps"]
+    assert n >= 10
+    for j in range(1, n + 1):
+        w = scipy.linalg.eigvalsh_tridiagonal(a[:j], bt[:j - 1], select="i", select_range=(0, 0))
+        scale = np.max(np.abs(a[:j])) + (np.max(np.abs(bt[:j - 1])) if j > 1 else 0.0)
+        assert abs(hist[j - 1] - w[0]) <= 8 * EPS64 * max(scale, 1.0), (j, hist[j - 1], w[0])
