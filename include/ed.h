@@ -203,7 +203,8 @@ ed_status ed_lanczos_solve(const ed_basis* basis, const ed_params* params, const
  * CUDA graph. opts apply to every instance (dtype must be ED_F32: FP32 vectors and H.v,
  * FP64 a_j, b_j, dot-product accumulation and tridiagonal solve; start vector of opts->seed
  * for every instance). The convergence test of opts is evaluated every 4 steps.
- * opts->schedule picks how instances are packed onto groups of CTAs (0..4); -1 lets the
+ * opts->schedule picks how instances are packed onto groups of CTAs (0..5; 5 sizes groups
+ * in proportion to each instance's work); -1 lets the
  * library time every schedule on this batch with a short run and keep the fastest (cached
  * per process for the same batch shape). Outputs (HOST arrays of n, steps/status optional):
  * E0[i], steps[i], status[i] (0 running, 1 breakdown, 2 converged, 3 max_steps) and

@@ -11,7 +11,8 @@
 //   phase 2: a_j, q = w - a_j f_j, partial sums of q . q
 //   phase 3: b_{j+1}, scale of f_{j+1}, every `check` steps E0(j) = lambda_min(T_j) by
 //            Sturm bisection (leader CTA), convergence / breakdown / max_steps.
-// Gathers read global memory directly (instances are small; their vectors stay in L2).
+// The H.v phase stages blocks of up rows in shared memory (down-hop gathers there) and reads
+// up-neighbour rows coalesced; vectors of the batch stay in L2.
 #include <algorithm>
 #include <cmath>
 #include <map>
@@ -25,6 +26,10 @@
 namespace ed {
 
 constexpr int kBThreads = 256;
+// Shared buffer of the batched kernel: a block of up rows staged for the H.v phase, or the
+// Sturm workspace of the leader CTA (used at different times).
+constexpr int kBRowFloats = 4096;
+constexpr int kBSmemBytes = kBRowFloats * 4 > kSturmWork * 8 ? kBRowFloats * 4 : kSturmWork * 8;
 
 struct BInst {
   const uint32_t* upb;
@@ -141,10 +146,12 @@ __device__ __forceinline__ double group_sum(const double* part, int first, int g
   return v;
 }
 
-__global__ void __launch_bounds__(kBThreads)
+__global__ void __launch_bounds__(kBThreads, 4)
 batched_lanczos_kernel(BArgs a) {
   __shared__ double red[33];
   __shared__ int stop_s;
+  __shared__ __align__(16) unsigned char bsm[kBSmemBytes];
+  float* xsm = reinterpret_cast<float*>(bsm);
   const int gi = a.group_of_cta[blockIdx.x];
   const BGroup G = a.groups[gi];
   const int c = blockIdx.x - G.first_cta, g = G.ncta;
@@ -199,29 +206,71 @@ batched_lanczos_kernel(BArgs a) {
       const float bsp = (float)(__ldcg(&be[j]) * __ldcg(&S->scale[1 - cur]));
       const float tt = (float)I.t, UU = (float)I.U;
       DotAcc<float> dot;
-      for (int64_t e = t0; e < dim; e += gt) {
-        const int u = (int)(e / I.dim_dn), d = (int)(e - (int64_t)u * I.dim_dn);
-        const float* xr = xc + (int64_t)u * I.dim_dn;
-        float acc = 0.f;
-        for (int k = 0; k < I.mhd; ++k) {
-          const uint32_t en = (uint32_t)I.hd[(int64_t)k * I.dim_dn + d];
-          const uint32_t tg = en & kTargetMask;
-          if (tg >= (uint32_t)I.dim_dn) break;
-          const float v = ld_shared_f(xr + tg, multi);
-          acc += (en & kSignBit) ? -v : v;
+      if (I.dim_dn <= kBRowFloats) {
+        // blocks of BR consecutive up rows staged in shared memory (coalesced loads; from L2
+        // when other CTAs of the group wrote them): down-hop gathers read shared memory,
+        // up-hop gathers read whole neighbour rows coalesced
+        const int BR = max(1, min(kBRowFloats, 2048) / I.dim_dn);
+        const int nblk = (I.dim_up + BR - 1) / BR;
+        for (int blk = c; blk < nblk; blk += g) {
+          const int u0 = blk * BR;
+          const int nr = min(BR, I.dim_up - u0);
+          const int nel = nr * I.dim_dn;
+          const float* xb = xc + (int64_t)u0 * I.dim_dn;
+          for (int i = threadIdx.x; i < nel; i += blockDim.x) xsm[i] = ld_shared_f(xb + i, multi);
+          __syncthreads();
+          for (int i = threadIdx.x; i < nel; i += blockDim.x) {
+            const int r = i / I.dim_dn, d = i - r * I.dim_dn, u = u0 + r;
+            const float* xr = xsm + r * I.dim_dn;
+            float acc = 0.f;
+            for (int k = 0; k < I.mhd; ++k) {
+              const uint32_t en = (uint32_t)I.hd[(int64_t)k * I.dim_dn + d];
+              const uint32_t tg = en & kTargetMask;
+              if (tg >= (uint32_t)I.dim_dn) break;
+              const float v = xr[tg];
+              acc += (en & kSignBit) ? -v : v;
+            }
+            for (int k = 0; k < I.mhu; ++k) {
+              const uint32_t en = (uint32_t)I.hu[(int64_t)k * I.dim_up + u];
+              const uint32_t tg = en & kTargetMask;
+              if (tg >= (uint32_t)I.dim_up) break;
+              const float v = ld_shared_f(xc + (int64_t)tg * I.dim_dn + d, multi);
+              acc += (en & kSignBit) ? -v : v;
+            }
+            const float xv = xsm[i];
+            const int64_t e = (int64_t)u0 * I.dim_dn + i;
+            const float hx = fmaf(-tt, acc, UU * (float)__popc(I.upb[u] & I.dnb[d]) * xv);
+            const float w = fmaf(sc, hx, -bsp * ld_shared_f(xp + e, multi));
+            xp[e] = w;
+            dot.add(w, sc * xv);
+          }
+          __syncthreads();
         }
-        for (int k = 0; k < I.mhu; ++k) {
-          const uint32_t en = (uint32_t)I.hu[(int64_t)k * I.dim_up + u];
-          const uint32_t tg = en & kTargetMask;
-          if (tg >= (uint32_t)I.dim_up) break;
-          const float v = ld_shared_f(xc + (int64_t)tg * I.dim_dn + d, multi);
-          acc += (en & kSignBit) ? -v : v;
+      } else {
+        for (int64_t e = t0; e < dim; e += gt) {
+          const int u = (int)(e / I.dim_dn), d = (int)(e - (int64_t)u * I.dim_dn);
+          const float* xr = xc + (int64_t)u * I.dim_dn;
+          float acc = 0.f;
+          for (int k = 0; k < I.mhd; ++k) {
+            const uint32_t en = (uint32_t)I.hd[(int64_t)k * I.dim_dn + d];
+            const uint32_t tg = en & kTargetMask;
+            if (tg >= (uint32_t)I.dim_dn) break;
+            const float v = ld_shared_f(xr + tg, multi);
+            acc += (en & kSignBit) ? -v : v;
+          }
+          for (int k = 0; k < I.mhu; ++k) {
+            const uint32_t en = (uint32_t)I.hu[(int64_t)k * I.dim_up + u];
+            const uint32_t tg = en & kTargetMask;
+            if (tg >= (uint32_t)I.dim_up) break;
+            const float v = ld_shared_f(xc + (int64_t)tg * I.dim_dn + d, multi);
+            acc += (en & kSignBit) ? -v : v;
+          }
+          const float xv = ld_shared_f(xr + d, multi);
+          const float hx = fmaf(-tt, acc, UU * (float)__popc(I.upb[u] & I.dnb[d]) * xv);
+          const float w = fmaf(sc, hx, -bsp * ld_shared_f(xp + e, multi));
+          xp[e] = w;
+          dot.add(w, sc * xv);
         }
-        const float xv = xr[d];
-        const float hx = fmaf(-tt, acc, UU * (float)__popc(I.upb[u] & I.dnb[d]) * xv);
-        const float w = fmaf(sc, hx, -bsp * xp[e]);
-        xp[e] = w;
-        dot.add(w, sc * xv);
       }
       {
         const double v = block_sum(dot.get(), red);
@@ -233,8 +282,9 @@ batched_lanczos_kernel(BArgs a) {
       if (leader && threadIdx.x == 0) al[j] = alpha;
       const float coef = (float)(alpha * __ldcg(&S->scale[cur]));
       DotAcc<float> q2;
+      // (phase 1 wrote w by row blocks: other CTAs' values are read from L2)
       for (int64_t e = t0; e < dim; e += gt) {
-        const float q = xp[e] - coef * xc[e];
+        const float q = ld_shared_f(xp + e, multi) - coef * ld_shared_f(xc + e, multi);
         xp[e] = q;
         q2.add(q, q);
       }
@@ -259,7 +309,8 @@ batched_lanczos_kernel(BArgs a) {
         __syncthreads();
         int st = stop_s;
         if (st != 0 || j >= a.max_steps || (j % a.check) == 0) {
-          const double E = sturm_lowest(al, be, j, S->last_E0_step > 0 ? S->last_E0 : NAN);
+          const double E = sturm_lowest(al, be, j, S->last_E0_step > 0 ? S->last_E0 : NAN,
+                                        reinterpret_cast<double*>(bsm));
           if (threadIdx.x == 0) {
             e0[j] = E;
             if (st == 0 && a.tol > 0.0 && S->last_E0_step > 0 &&
@@ -286,6 +337,9 @@ batched_lanczos_kernel(BArgs a) {
 // A schedule maps instances to CTA groups: instances with dim >= big get `gbig` CTAs,
 // with dim >= mid get `gmid` CTAs, the rest are queued on single-CTA groups; queues are
 // balanced by estimated work (dim x hops x 1), longest first.
+// Schedule 5 instead sizes groups in proportion to work: with T = total work / CTAs, an
+// instance of at least 4096 states and work w >= 1.5 T gets about w / T CTAs, the rest are
+// queued.
 struct Sched {
   int big, gbig, mid, gmid;
 };
@@ -295,6 +349,7 @@ static const Sched kScheds[] = {
     {100000, 16, 10000, 4},    // 2
     {400000, 32, 40000, 4},    // 3
     {50000, 8, 5000, 2},       // 4
+    {0, 0, 0, 0},              // 5: proportional
 };
 constexpr int kNumScheds = (int)(sizeof(kScheds) / sizeof(kScheds[0]));
 
@@ -314,9 +369,37 @@ static Plan make_plan(const std::vector<long long>& work, const std::vector<int>
   Plan p;
   int ctas = 0;
   std::vector<int> big_ids, small_ids;
+  const bool prop = sc.gbig == 0;
+  std::vector<int> gprop(n, 1);
+  if (prop) {
+    // T = work per CTA if the batch were spread evenly over all but one CTA; instances of
+    // at least 4096 states and 1.5 T get round(w / T) CTAs; the largest groups give CTAs
+    // back until the groups fit
+    long long W = 0;
+    for (long long w : work) W += w;
+    const int cap = std::max(1, max_ctas - 1);
+    const double T = (double)W / (double)cap;
+    long long total = 0;
+    for (int i = 0; i < n; ++i) {
+      if (dims[i] >= 4096 && (double)work[i] >= 1.5 * T)
+        gprop[i] = (int)std::min((double)cap, std::floor((double)work[i] / T + 0.5));
+      if (gprop[i] > 1) total += gprop[i];
+    }
+    while (total > cap) {
+      int big = 0;
+      for (int i = 1; i < n; ++i)
+        if (gprop[i] > gprop[big]) big = i;
+      if (gprop[big] <= 1) break;
+      --gprop[big];
+      --total;
+      if (gprop[big] == 1) --total;  // queued from now on
+    }
+  }
   for (int i : idx) {
-    const int gsz = dims[i] >= sc.big ? sc.gbig : (dims[i] >= sc.mid ? sc.gmid : 1);
-    if (gsz > 1 && ctas + gsz <= max_ctas / 2) {
+    int gsz = dims[i] >= sc.big ? sc.gbig : (dims[i] >= sc.mid ? sc.gmid : 1);
+    if (prop) gsz = gprop[i];
+    const int cap = prop ? max_ctas - 1 : max_ctas / 2;
+    if (gsz > 1 && ctas + gsz <= cap) {
       BGroup G{ctas, gsz, (int)p.order.size(), (int)p.order.size() + 1};
       p.order.push_back(i);
       p.groups.push_back(G);

@@ -149,7 +149,8 @@ lz_energy_kernel(const LzScalars* S, double* out) {
     if (threadIdx.x == 0) *out = NAN;
     return;
   }
-  const double E = sturm_lowest(S->alpha, S->beta, j, NAN);
+  __shared__ double sturm_work[kSturmWork];
+  const double E = sturm_lowest(S->alpha, S->beta, j, NAN, sturm_work);
   if (threadIdx.x == 0) *out = E;
 }
 

@@ -45,18 +45,23 @@ __device__ __forceinline__ int sturm_count(const double* aa, const double* bb, i
   return cnt;
 }
 
+// Shared-memory workspace of sturm_lowest: a_i and b_i^2 for i <= ED_MAX_STEPS + 1.
+constexpr int kSturmWork = 2 * (ED_MAX_STEPS + 2);
+
 // lambda_min(T_m) by multisection, called by the whole block (>= 128 threads); returns the
 // upper end of the final bracket (valid in every thread). a, b: 1-based a_1..a_m, b_2..b_m.
-// The diagonal and the squared off-diagonal are staged in shared memory. Each round
+// The diagonal and the squared off-diagonal are staged in `work` (kSturmWork doubles of
+// shared memory). Each round
 // evaluates the Sturm count at 128 interior points of the bracket (four warps, one per SM
 // sub-partition) and keeps the sub-interval holding the first eigenvalue, until the bracket
 // stops shrinking in FP64. With a hint (a previous lambda_min of a leading block of T_m, an
 // upper bound by Cauchy interlacing; NaN = none), a first round probes geometrically spaced
 // points below it, so a bracket of the size of the last change is found in one round.
 __device__ __forceinline__ double sturm_lowest(const double* a, const double* b, int m,
-                                               double hint) {
+                                               double hint, double* work) {
   constexpr int P = 128;
-  __shared__ double aa[ED_MAX_STEPS + 2], bb[ED_MAX_STEPS + 2];
+  double* aa = work;
+  double* bb = work + (ED_MAX_STEPS + 2);
   __shared__ double lo_s, hi_s;
   __shared__ int first_s, last0_s, top_s;
   for (int i = 1 + threadIdx.x; i <= m; i += blockDim.x) {
@@ -150,9 +155,11 @@ __device__ __forceinline__ int finish_record_beta(LzScalars* S, int j, double be
 
 // Whole block: E0(j) = lambda_min(T_j) when due, convergence test, final status.
 __device__ __forceinline__ void finish_tail(LzScalars* S, int j, int st) {
+  __shared__ double sturm_work[kSturmWork];
   const bool check = st != 0 || j >= S->max_steps || (j % S->check_every) == 0;
   if (check) {
-    const double E = sturm_lowest(S->alpha, S->beta, j, S->last_E0_step > 0 ? S->last_E0 : NAN);
+    const double E = sturm_lowest(S->alpha, S->beta, j, S->last_E0_step > 0 ? S->last_E0 : NAN,
+                                  sturm_work);
     if (threadIdx.x == 0) {
       S->E0[j] = E;
       if (st == 0 && S->tol > 0.0 && S->last_E0_step > 0 &&
