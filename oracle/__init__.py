@@ -14,7 +14,8 @@ Module map:
   tridiag      lowest eigenvalue of the Lanczos tridiagonal T (Sec. 2.2, Eq. for T)
   lanczos      Algorithm 1 in FP64, optional full reorthogonalisation (Sec. 2.2)
   dense        dense diagonalisation for small dimensions
+  observables  double occupancy of a state vector (the on-site term; dE0/dU)
   mlp          the learned start-vector network, its loss and gradient (no counterpart in
                the paper; test oracle of the library's MLP kernels)
 """
-from . import basis, hamiltonian, tridiag, lanczos, dense, mlp  # noqa: F401
+from . import basis, hamiltonian, tridiag, lanczos, dense, mlp, observables  # noqa: F401
