@@ -117,6 +117,10 @@ ed_status ed_build_basis(const ed_lattice* lattice, int32_t n_up, int32_t n_dn, 
  * (Eq. 2). Any output pointer may be NULL. */
 ed_status ed_basis_dims(const ed_basis* basis, int64_t* dim_up, int64_t* dim_dn, int64_t* dim);
 
+/* ed_basis_filling - the lattice size and particle numbers the basis was built for (Sec. 2.1:
+ * L sites, N_up and N_dn fixed). Any output pointer may be NULL. */
+ed_status ed_basis_filling(const ed_basis* basis, int32_t* n_sites, int32_t* n_up, int32_t* n_dn);
+
 /* ed_basis_tables - read-only DEVICE views of the basis tables (valid until destroy):
  *  up_bits[dim_up], dn_bits[dim_dn]: uint32 bit strings in rank order.
  *  hop_up[maxhops_up * dim_up], hop_dn[maxhops_dn * dim_dn]: hop k of state r at
@@ -225,6 +229,17 @@ ed_status ed_lanczos_solve_batched(int32_t n, const ed_basis* const* bases,
 ed_status ed_lanczos_ground_state(const ed_basis* basis, const ed_params* params,
                                   const ed_opts* opts, const void* f1, void* stream, double* psi,
                                   double* E0, int32_t* steps);
+
+/* ed_double_occupancy - double occupancy of a state: D_i = <psi| n_i,up n_i,dn |psi> / <psi|psi>
+ * for every site i and D = sum_i D_i. n_i,up n_i,dn is the on-site operator of the
+ * interaction term U sum_i n_i,up n_i,dn the paper adds to Eq. 1 (Sec. 1), so for a
+ * normalised non-degenerate ground state D = dE0/dU (Hellmann-Feynman). psi: DEVICE array of
+ * dim FP64 in the basis order (index rank_up * dim_dn + rank_dn, Sec. 4 Eqs. 5-6), e.g. the
+ * output of ed_lanczos_ground_state; any nonzero norm. D_total: HOST double; D_site: HOST
+ * array of n_sites doubles or NULL. Accumulated in FP64 in a fixed order (deterministic).
+ * ED_ERR_ARG for a NULL or unaligned psi or a zero vector. Synchronises `stream`. */
+ed_status ed_double_occupancy(const ed_basis* basis, const double* psi, void* stream,
+                              double* D_total, double* D_site);
 
 /* ---------------------------------------------------------------- learned start vector
  * A small network predicts the ground-state amplitude of a basis state from its occupation

@@ -52,6 +52,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 _SIGS = {
     "ed_build_basis": (c_int, [POINTER(ed_lattice), c_int32, c_int32, c_void_p, POINTER(c_void_p)]),
     "ed_basis_dims": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64), POINTER(c_int64)]),
+    "ed_basis_filling": (c_int, [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)]),
     "ed_basis_tables": (c_int, [c_void_p, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p),
                                 POINTER(c_void_p), POINTER(c_int32), POINTER(c_int32)]),
     "ed_basis_destroy": (None, [c_void_p]),
@@ -73,6 +74,7 @@ _SIGS = {
     "ed_selftest_barrier_timeout": (c_int, [c_int32, c_int32, c_void_p]),
     "ed_lanczos_ground_state": (c_int, [c_void_p, POINTER(ed_params), POINTER(ed_opts), c_void_p,
                                         c_void_p, c_void_p, POINTER(c_double), POINTER(c_int32)]),
+    "ed_double_occupancy": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(c_double), POINTER(c_double)]),
     "ed_mlp_create": (c_int, [c_int32, c_uint64, c_void_p, POINTER(c_void_p)]),
     "ed_mlp_params": (c_int, [c_void_p, POINTER(c_void_p), POINTER(c_int64)]),
     "ed_mlp_loss_grad": (c_int, [c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_int64,
@@ -148,6 +150,13 @@ def ed_basis_dims(basis) -> tuple[int, int, int]:
     du, dd, d = c_int64(), c_int64(), c_int64()
     _check(_lib.ed_basis_dims(basis, byref(du), byref(dd), byref(d)))
     return du.value, dd.value, d.value
+
+
+def ed_basis_filling(basis):
+    """(n_sites, n_up, n_dn)."""
+    L, nu, nd = c_int32(), c_int32(), c_int32()
+    _check(_lib.ed_basis_filling(basis, byref(L), byref(nu), byref(nd)))
+    return L.value, nu.value, nd.value
 
 
 def ed_basis_tables(basis) -> dict:
@@ -282,6 +291,17 @@ def ed_lanczos_ground_state(basis, t: float, U: float, opts: ed_opts, psi, f1=No
     if s < 0 and not (s == ED_ERR_NOT_CONVERGED and not raise_not_converged):
         _check(s)
     return dict(status=s, E0=E0.value, steps=steps.value)
+
+
+def ed_double_occupancy(basis, psi, stream=None):
+    """(D, D_site): double occupancy of the FP64 state psi (device, basis order)."""
+    import numpy as np
+    dim = ed_basis_dims(basis)[2]
+    n_sites = ed_basis_filling(basis)[0]
+    D = c_double()
+    site = (c_double * max(n_sites, 1))()
+    _check(_lib.ed_double_occupancy(basis, _ptr(psi, ED_F64, dim), _stream(stream), byref(D), site))
+    return D.value, np.array(site[:n_sites])
 
 
 def ed_mlp_create(n_sites: int, seed: int, stream=None) -> c_void_p:

@@ -298,6 +298,16 @@ extern "C" ed_status ed_basis_dims(const ed_basis* B, int64_t* dim_up, int64_t* 
   return ED_OK;
 }
 
+extern "C" ed_status ed_basis_filling(const ed_basis* B, int32_t* n_sites, int32_t* n_up,
+                                      int32_t* n_dn) {
+  clear_error();
+  ED_CHECK_ARG(B != nullptr, "ed_basis_filling: basis is NULL");
+  if (n_sites) *n_sites = B->n_sites;
+  if (n_up) *n_up = B->n_up;
+  if (n_dn) *n_dn = B->n_dn;
+  return ED_OK;
+}
+
 extern "C" ed_status ed_basis_tables(const ed_basis* B, const uint32_t** up_bits,
                                      const uint32_t** dn_bits, const int32_t** hop_up,
                                      const int32_t** hop_dn, int32_t* maxhops_up,
