@@ -75,7 +75,7 @@ def start_vector_raw(seed: int, dim: int) -> np.ndarray:
 
 # --------------------------------------------------------------------------- workloads
 def workload(name: str) -> dict:
-    """The five synthetic workloads: lattice, fillings, t, U, dtype, seed."""
+    """The synthetic workloads: lattice, fillings, t, U, dtype, seed."""
     if name == "ring12_3_3":      # L=12 ring, 3/3, dim 220^2, FP64, U in {0, 4}
         return dict(n_sites=12, bonds=ring_bonds(12), n_up=3, n_dn=3, t=1.0, U=4.0,
                     dtype="f64", seed=1)
@@ -88,6 +88,9 @@ def workload(name: str) -> dict:
     if name == "ring14_7_7":      # L=14 ring, 7/7, dim 3432^2 (learned start)
         return dict(n_sites=14, bonds=ring_bonds(14), n_up=7, n_dn=7, t=1.0, U=4.0,
                     dtype="f32", seed=5)
+    if name == "ring18_9_9":      # L=18 ring, half filling, dim 48620^2 = 2.36e9, FP32
+        return dict(n_sites=18, bonds=ring_bonds(18), n_up=9, n_dn=9, t=1.0, U=4.0,
+                    dtype="f32", seed=6)
     raise KeyError(name)
 
 

@@ -448,3 +448,26 @@ def test_per_step_lowest_ritz_value_matches_lapack(ed, dtype, lattice):
         w = scipy.linalg.eigvalsh_tridiagonal(a[:j], bt[:j - 1], select="i", select_range=(0, 0))
         scale = np.max(np.abs(a[:j])) + (np.max(np.abs(bt[:j - 1])) if j > 1 else 0.0)
         assert abs(hist[j - 1] - w[0]) <= 8 * EPS64 * max(scale, 1.0), (j, hist[j - 1], w[0])
+
+
+@pytest.mark.slow
+def test_ring18_half_filling_U0_closed_form(ed):
+    """The 18-site 9/9 basis (2,363,904,400 states; 9.5 GB per FP32 vector; int64 indices
+    throughout) on one GPU: at U = 0 the closed-shell E0 is 2 x (-2t sin(pi N/L)/sin(pi/L))
+    for N = 9 per species."""
+    w = ed_inputs.workload("ring18_9_9")
+    L, N = w["n_sites"], w["n_up"]
+    ref = 2 * (-2.0 * math.sin(math.pi * N / L) / math.sin(math.pi / L))
+    b = ed.ed_build_basis(L, w["bonds"], N, N)
+    try:
+        assert ed.ed_basis_dims(b)[2] == math.comb(18, 9) ** 2
+        opts = ed.make_opts(max_steps=400, tol=1e-6, seed=w["seed"], dtype="f32")
+        st = ed.ed_lanczos_init(b, opts)
+        try:
+            assert ed.ed_lanczos_schedule(st) > 0   # the fused FP32 path (R = 1 rows per CTA)
+        finally:
+            ed.ed_lanczos_destroy(st)
+        res = ed.ed_lanczos_solve(b, 1.0, 0.0, opts, raise_not_converged=False)
+    finally:
+        ed.ed_basis_destroy(b)
+    assert abs(res["E0"] - ref) <= 2e-5 * abs(ref), (res["E0"], ref, res["steps"])
