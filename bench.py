@@ -435,7 +435,9 @@ def bench_ours(args):
         traffic = rec["bytes"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": f"hv2_kernel variant {variant} (fused Lanczos H.v)",
+                "kernel": (f"hv2_kernel variant {variant} (fused Lanczos H.v)" if variant > 0 else
+                           "general H.v kernels (fx_hv_global_kernel / hv_global_kernel: rows "
+                           "too few or too long for the fused kernel)"),
                 "bytes_per_launch": hv_bytes, "launch_ms": hv_launch_ms,
                 "peak_source": f"{peak_kind} HBM copy bandwidth"}
     line = {"metric": METRIC, "value": value, "unit": "lanczos_steps/s", "n_gpus": ws,

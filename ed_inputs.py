@@ -88,6 +88,9 @@ def workload(name: str) -> dict:
     if name == "ring14_7_7":      # L=14 ring, 7/7, dim 3432^2 (learned start)
         return dict(n_sites=14, bonds=ring_bonds(14), n_up=7, n_dn=7, t=1.0, U=4.0,
                     dtype="f32", seed=5)
+    if name == "ring26_13_0":     # L=26 ring, 13 particles of one spin, dim 10,400,600
+        return dict(n_sites=26, bonds=ring_bonds(26), n_up=13, n_dn=0, t=1.0, U=4.0,
+                    dtype="f64", seed=7)
     if name == "ring18_9_9":      # L=18 ring, half filling, dim 48620^2 = 2.36e9, FP32
         return dict(n_sites=18, bonds=ring_bonds(18), n_up=9, n_dn=9, t=1.0, U=4.0,
                     dtype="f32", seed=6)

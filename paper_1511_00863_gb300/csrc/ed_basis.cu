@@ -269,6 +269,10 @@ extern "C" ed_status ed_build_basis(const ed_lattice* L, int32_t n_up, int32_t n
   if ((st = build_species(B->dn, L->n_sites, n_dn, d_bonds, L->n_bonds, B->binom, d_count, s)) != ED_OK)
     return fail(st);
   B->dim = B->up.dim * B->dn.dim;
+  if (B->dn.dim == 1 && B->up.dim > 1) {  // single occupied species: one long row
+    std::swap(B->up, B->dn);
+    B->swapped = true;
+  }
   if (B->up.dim <= kMaxOrderedRows && B->up.maxhops > 0) {
     std::vector<int32_t> order;
     if ((st = rcm_order(B->up, s, order)) != ED_OK) return fail(st);
@@ -292,8 +296,8 @@ extern "C" ed_status ed_basis_dims(const ed_basis* B, int64_t* dim_up, int64_t* 
                                    int64_t* dim) {
   clear_error();
   ED_CHECK_ARG(B != nullptr, "ed_basis_dims: basis is NULL");
-  if (dim_up) *dim_up = B->up.dim;
-  if (dim_dn) *dim_dn = B->dn.dim;
+  if (dim_up) *dim_up = B->user_up().dim;
+  if (dim_dn) *dim_dn = B->user_dn().dim;
   if (dim) *dim = B->dim;
   return ED_OK;
 }
@@ -314,12 +318,12 @@ extern "C" ed_status ed_basis_tables(const ed_basis* B, const uint32_t** up_bits
                                      int32_t* maxhops_dn) {
   clear_error();
   ED_CHECK_ARG(B != nullptr, "ed_basis_tables: basis is NULL");
-  if (up_bits) *up_bits = B->up.bits;
-  if (dn_bits) *dn_bits = B->dn.bits;
-  if (hop_up) *hop_up = B->up.hop;
-  if (hop_dn) *hop_dn = B->dn.hop;
-  if (maxhops_up) *maxhops_up = B->up.maxhops;
-  if (maxhops_dn) *maxhops_dn = B->dn.maxhops;
+  if (up_bits) *up_bits = B->user_up().bits;
+  if (dn_bits) *dn_bits = B->user_dn().bits;
+  if (hop_up) *hop_up = B->user_up().hop;
+  if (hop_dn) *hop_dn = B->user_dn().hop;
+  if (maxhops_up) *maxhops_up = B->user_up().maxhops;
+  if (maxhops_dn) *maxhops_dn = B->user_dn().maxhops;
   return ED_OK;
 }
 

@@ -547,6 +547,7 @@ static int smem_optin() {
 }
 
 static int fx_rows(const ed_basis* b) {
+  if (b->up.dim < kMinRowsStaged) return 0;  // few rows: the element-parallel kernel
   const size_t lim = (size_t)smem_optin();
   if (fx_smem<2>(b) <= lim && b->up.dim >= 2) return 2;
   if (fx_smem<1>(b) <= lim) return 1;

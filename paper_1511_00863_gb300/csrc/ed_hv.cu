@@ -199,9 +199,9 @@ template <typename T, bool kLz>
 static ed_status launch_any(const ed_basis* b, const HvArgs& a, const T* x, T* y,
                             cudaStream_t s, const LzHvArgs& lz, int* grid_out) {
   const size_t lim = (size_t)max_smem_optin();
-  if (staged_smem<T, 2>(b) <= lim && b->up.dim >= 2)
-    return launch_staged<T, 2, kLz>(a, b, x, y, s, lz, grid_out);
-  if (staged_smem<T, 1>(b) <= lim) return launch_staged<T, 1, kLz>(a, b, x, y, s, lz, grid_out);
+  const bool rows = b->up.dim >= kMinRowsStaged;
+  if (rows && staged_smem<T, 2>(b) <= lim) return launch_staged<T, 2, kLz>(a, b, x, y, s, lz, grid_out);
+  if (rows && staged_smem<T, 1>(b) <= lim) return launch_staged<T, 1, kLz>(a, b, x, y, s, lz, grid_out);
   const int grid = global_grid(b);
   hv_global_kernel<T, kLz><<<grid, kHvThreads, 0, s>>>(a, x, y, lz);
   ED_TRY_CUDA(cudaGetLastError());

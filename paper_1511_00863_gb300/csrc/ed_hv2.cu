@@ -336,6 +336,7 @@ ed_status hv2_build(const ed_basis* b, bool fixed_point, int ld, int schedule, c
   KindInfo ki{};
   for (int i = -1; i < npref && !kind; ++i) {
     const int k = i < 0 ? schedule : pref[i];
+    if (i >= 0 && b->up.dim < kMinRowsStaged) break;  // few rows: the general kernels
     if (kind_usable(k, b, fixed_point, ld, &ki)) kind = k;
   }
   if (!kind) return ED_OK;  // caller falls back to the general kernels
@@ -374,6 +375,7 @@ int hv2_grid(const Hv2Plan* p) { return p ? p->grid : 0; }
 ed_status hv2_autotune(const ed_basis* b, bool fixed_point, int ld, void* x, void* y,
                        const LzScalars* S, void* partial, cudaStream_t s, int* kind) {
   *kind = 0;
+  if (b->up.dim < kMinRowsStaged) return ED_OK;  // few rows: the general kernels
   static const int cand_f32[] = {1, 2, 3, 4, 5, 6, 7, 14}, cand_fx[] = {8, 9, 10, 11, 12, 13};
   const int* cand = fixed_point ? cand_fx : cand_f32;
   const int nc = fixed_point ? 6 : 8;

@@ -65,11 +65,23 @@ struct ed_basis {
   // Host-built down tables of the fused H.v per (V, G) geometry (ed_hv2.cu); freed with the
   // basis.
   mutable void* hv2_tables = nullptr;
+  // True when the caller's down species has a single state (N_dn = 0 or N_dn = n_sites) and
+  // the up species more: the kernels then see the occupied species as the row (`dn`)
+  // species, so a state vector is one row of C(L, N_up) elements instead of C(L, N_up) rows
+  // padded to 32. The global index rank_up * dim_dn + rank_dn is unchanged (one factor is
+  // 1); `up`/`dn` below are the kernels' view, user_up()/user_dn() the caller's.
+  bool swapped = false;
+  const ed::SpeciesTables& user_up() const { return swapped ? dn : up; }
+  const ed::SpeciesTables& user_dn() const { return swapped ? up : dn; }
 };
 
 namespace ed {
 
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Row-staged H.v kernels run one CTA per few up rows; with fewer rows than this the
+// element-parallel global kernels are chosen instead (automatic selection only).
+constexpr int64_t kMinRowsStaged = 64;
 
 // Number of SMs of the current device (cached per device).
 int sm_count();

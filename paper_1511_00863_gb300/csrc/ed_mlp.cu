@@ -478,8 +478,9 @@ ed_status mlp_grad(ed_mlp* M, const ed_basis* b, double U, const int64_t* idx, c
   cudaStream_t s = M->stream;
   const size_t sm = grad_smem(M->d);
   ED_TRY_CUDA(cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  mlp_grad_kernel<<<M->ncta, kMThreads, sm, s>>>(M->params, M->L, (float)U, b->up.bits, b->dn.bits,
-                                                  b->dn.dim, idx, tgt, n, wscale, M->partial, M->lpart);
+  mlp_grad_kernel<<<M->ncta, kMThreads, sm, s>>>(M->params, M->L, (float)U, b->user_up().bits,
+                                                  b->user_dn().bits, b->user_dn().dim, idx, tgt, n,
+                                                  wscale, M->partial, M->lpart);
   if (adam) ++M->step;
   mlp_reduce_kernel<<<(M->d.P + kMThreads - 1) / kMThreads, kMThreads, 0, s>>>(
       M->partial, M->ncta, M->d.P, M->lpart, M->grad, M->loss, M->params, M->m,
@@ -600,12 +601,14 @@ extern "C" ed_status ed_mlp_infer(ed_mlp* M, const ed_basis* b, double U, ed_dty
   const int grid = sm_count() * 8;
   if (dtype == ED_F32) {
     ED_TRY_CUDA(cudaFuncSetAttribute(mlp_infer_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    mlp_infer_kernel<float><<<grid, kMThreads, sm, M->stream>>>(M->params, M->L, (float)U, b->up.bits,
-                                                                b->dn.bits, b->dn.dim, b->dim, (float*)out);
+    mlp_infer_kernel<float><<<grid, kMThreads, sm, M->stream>>>(M->params, M->L, (float)U,
+                                                                b->user_up().bits, b->user_dn().bits,
+                                                                b->user_dn().dim, b->dim, (float*)out);
   } else {
     ED_TRY_CUDA(cudaFuncSetAttribute(mlp_infer_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    mlp_infer_kernel<double><<<grid, kMThreads, sm, M->stream>>>(M->params, M->L, (float)U, b->up.bits,
-                                                                 b->dn.bits, b->dn.dim, b->dim, (double*)out);
+    mlp_infer_kernel<double><<<grid, kMThreads, sm, M->stream>>>(M->params, M->L, (float)U,
+                                                                 b->user_up().bits, b->user_dn().bits,
+                                                                 b->user_dn().dim, b->dim, (double*)out);
   }
   ED_TRY_CUDA(cudaGetLastError());
   return ED_OK;

@@ -90,8 +90,10 @@ def test_mlp_gradient_vs_oracle(ed):
         ed.ed_basis_destroy(b)
 
 
-def test_mlp_inference_vs_oracle(ed):
-    L, nu, nd, U = 8, 3, 4, 2.5
+@pytest.mark.parametrize("fill", [(3, 4), (3, 0)])
+def test_mlp_inference_vs_oracle(ed, fill):
+    L, U = 8, 2.5
+    nu, nd = fill
     b = ed.ed_build_basis(L, ed_inputs.ring_bonds(L), nu, nd)
     net = ed.ed_mlp_create(L, 11)
     try:

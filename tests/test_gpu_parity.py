@@ -50,6 +50,8 @@ TABLE_CASES = [
     ("single_site", 1, np.zeros((0, 2), np.int32), 1, 0),
     ("doubled_pair", 2, ed_inputs.ring_bonds(2), 1, 1),
     ("random_bonds", 9, np.array([[0, 5], [3, 8], [1, 2], [7, 0], [6, 4], [2, 8], [5, 1]]), 4, 3),
+    ("single_species_up", 10, ed_inputs.ring_bonds(10), 4, 0),
+    ("single_species_dn", 10, ed_inputs.ring_bonds(10), 0, 4),
 ]
 
 
@@ -89,6 +91,7 @@ HV_CASES = [
     (12, ed_inputs.ring_bonds(12), 3, 3, 1.0, 4.0),
     (9, np.array([[0, 5], [3, 8], [1, 2], [7, 0], [6, 4], [2, 8], [5, 1]]), 4, 3, 1.3, -1.5),
     (8, ed_inputs.ring_bonds(8), 0, 3, 1.0, 2.0),
+    (10, ed_inputs.ring_bonds(10), 4, 0, 1.0, 2.0),
     (4, ed_inputs.ring_bonds(4), 4, 4, 1.0, 2.0),
 ]
 
@@ -407,13 +410,16 @@ def test_down_dimension_above_2_15(ed, dtype):
     ref = olz.lanczos(lambda v: H @ v, f1, max_steps=6, reorth=False, fixed_steps=True)
     b = ed.ed_build_basis(L, bonds, nu, nd)
     try:
-        opts = ed.make_opts(max_steps=6, tol=0.0, seed=1, dtype=dtype)
+        # 18 up rows: automatic selection would take the element-parallel kernels, so the
+        # FP32 fused variant (R = 1) is requested explicitly
+        opts = ed.make_opts(max_steps=6, tol=0.0, seed=1, dtype=dtype,
+                            schedule=2 if dtype == "f32" else -1)
         st = ed.ed_lanczos_init(b, opts)
         try:
             variant = ed.ed_lanczos_schedule(st)
         finally:
             ed.ed_lanczos_destroy(st)
-        assert (variant > 0) == (dtype == "f32")
+        assert variant == (2 if dtype == "f32" else 0)
         fdev = torch.tensor(f1, dtype=torch.float32 if dtype == "f32" else torch.float64,
                             device="cuda")
         res = ed.ed_lanczos_solve(b, t, U, opts, f1=fdev, raise_not_converged=False)
@@ -471,3 +477,46 @@ def test_ring18_half_filling_U0_closed_form(ed):
     finally:
         ed.ed_basis_destroy(b)
     assert abs(res["E0"] - ref) <= 2e-5 * abs(ref), (res["E0"], ref, res["steps"])
+
+
+
+# ----------------------------------------------------------------- single spin species
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("fill", [(8, 0), (0, 8)])
+def test_single_species_alpha_beta_follow_oracle(ed, dtype, fill):
+    """All particles of one spin (the paper's one-species workloads): the occupied species
+    forms one long row internally whichever slot it is given in; a_j, b_{j+1} follow the
+    oracle from the same start vector."""
+    nu, nd = fill
+    L, bonds, t, U = 16, ed_inputs.ring_bonds(16), 1.0, 3.0
+    H = hamiltonian.hamiltonian_csr(L, bonds, nu, nd, t, U)
+    f1 = olz.normalized_start(ed_inputs.start_vector_raw(31, H.shape[0]))
+    ref = olz.lanczos(lambda v: H @ v, f1, max_steps=16, reorth=False, fixed_steps=True)
+    b = ed.ed_build_basis(L, bonds, nu, nd)
+    try:
+        du, dd, dim = ed.ed_basis_dims(b)
+        assert (du, dd) == (math.comb(16, nu), math.comb(16, nd)) and dim == math.comb(16, 8)
+        fdev = torch.tensor(f1, dtype=torch.float32 if dtype == "f32" else torch.float64,
+                            device="cuda")
+        res = ed.ed_lanczos_solve(b, t, U, ed.make_opts(max_steps=16, tol=0.0, dtype=dtype),
+                                  f1=fdev, raise_not_converged=False)
+    finally:
+        ed.ed_basis_destroy(b)
+    tol = 2e-5 if dtype == "f32" else 1e-11
+    assert np.allclose(res["alpha"], ref.alpha, rtol=tol, atol=tol)
+    assert np.allclose(res["beta"], ref.beta, rtol=tol, atol=tol)
+
+
+@pytest.mark.parametrize("fill", [(13, 0), (0, 13)])
+def test_single_species_ring26_closed_form(ed, fill):
+    """26-site ring with 13 particles of one spin (dim 10,400,600, one row of the layout):
+    free fermions, closed shell, E0 = -2t sin(pi N/L) / sin(pi/L)."""
+    w = ed_inputs.workload("ring26_13_0")
+    L, N = w["n_sites"], 13
+    ref = -2.0 * math.sin(math.pi * N / L) / math.sin(math.pi / L)
+    b = ed.ed_build_basis(L, w["bonds"], *fill)
+    try:
+        res = ed.ed_lanczos_solve(b, 1.0, w["U"], ed.make_opts(max_steps=600, tol=1e-13, seed=w["seed"]))
+    finally:
+        ed.ed_basis_destroy(b)
+    assert abs(res["E0"] - ref) <= 1e-11 * abs(ref), (res["E0"], ref, res["steps"])
