@@ -14,10 +14,12 @@
 // reduced in a fixed order.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
 #include "ed_internal.cuh"
+#include "ed_tcgen05.cuh"
 
 namespace ed {
 
@@ -54,156 +56,181 @@ __device__ __forceinline__ void load_weights(const float* __restrict__ params, i
 }
 
 // ------------------------------------------------------------------ inference
-// BF16 tensor-core products (mma.sync m16n8k16, FP32 accumulation): a warp evaluates 16
-// basis states at a time. Thread (g = lane/4, q = lane%4) holds rows g and g+8 of every
-// fragment; the first layer's accumulator fragments are, after tanh and rounding, exactly
-// the A fragments of the second layer (its K index is the first layer's N index), so the
-// activations never leave registers.
+// 5th-generation tensor cores: a CTA of 4 warps evaluates tiles of 128 basis states, one
+// state per thread (TMEM lane). The features of the tile (bits as 0/1, bf16(U/8), zero
+// padding to K1 = 16 ceil(nin/16)) and later bf16(h1) are written to shared memory in the
+// K-major core-matrix layout; one thread issues tcgen05.mma (BF16 x BF16 -> FP32 in TMEM:
+// D1 = X W1 in columns 0..63, D2 = bf16(h1) W2 in columns 64..127) and commits to an
+// mbarrier; every thread then reads its row of the accumulator with tcgen05.ld and applies
+// bias and tanh on the CUDA cores; the 64 -> 2 output layer stays on the CUDA cores.
+// Waits on the mbarrier are bounded (1 s of the global timer); on expiry the kernel sets
+// *err, frees its TMEM and returns.
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, uint2 b) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
-}
+constexpr int kTcRows = 128;      // states per tile = threads per CTA = TMEM lanes used
+constexpr uint32_t kTcCols = 128;  // TMEM columns: D1 [0, 64), D2 [64, 128)
+constexpr int kTcSmemMin = 61440;  // at most 3 CTAs (384 TMEM columns) per SM
 
-constexpr int kMaxKT1 = (kMaxIn + 15) / 16;  // k-tiles of the first layer
+struct TcLayout {
+  int K1;
+  uint32_t a1, a2, b1, b2, par, mbar, tslot, total;
+};
 
-// B fragments of a K x 64 weight block (row-major W[k][n], rows >= K are zero) into shared
-// memory: frag[(kt * 8 + nt) * 32 + lane] = (W[k0..k0+1][n], W[k0+8..k0+9][n]) packed,
-// k0 = kt*16 + 2q, n = nt*8 + g.
-__device__ void build_frags(const float* W, int K, int KT, uint2* frag) {
-  for (int i = threadIdx.x; i < KT * 8 * 32; i += blockDim.x) {
-    const int lane = i & 31, nt = (i >> 5) & 7, kt = i >> 8;
-    const int g = lane >> 2, q = lane & 3;
-    const int n = nt * 8 + g, k0 = kt * 16 + 2 * q;
-    auto w = [&](int k) { return k < K ? W[k * kH + n] : 0.f; };
-    frag[i] = make_uint2(pack_bf16(w(k0), w(k0 + 1)), pack_bf16(w(k0 + 8), w(k0 + 9)));
-  }
+__host__ __device__ inline TcLayout tc_layout(int nin) {
+  auto up = [](uint32_t v, uint32_t a) { return (v + a - 1) / a * a; };
+  TcLayout t;
+  t.K1 = (nin + 15) / 16 * 16;
+  t.a1 = 0;
+  t.a2 = up(t.a1 + (uint32_t)kTcRows * t.K1 * 2, 1024);
+  t.b1 = up(t.a2 + (uint32_t)kTcRows * kH * 2, 1024);
+  t.b2 = up(t.b1 + (uint32_t)kH * t.K1 * 2, 1024);
+  t.par = up(t.b2 + (uint32_t)kH * kH * 2, 1024);
+  t.mbar = up(t.par + (uint32_t)(4 * kH + 2) * 4, 16);
+  t.tslot = t.mbar + 8;
+  t.total = up(t.tslot + 8, 1024);
+  return t;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kMThreads)
-mlp_infer_kernel(const float* __restrict__ params, int L, float U, const uint32_t* __restrict__ upb,
-                 const uint32_t* __restrict__ dnb, int64_t dim_dn, int64_t dim, T* __restrict__ out) {
-  __shared__ uint2 f1[kMaxKT1 * 8 * 32];
-  __shared__ uint2 f2[4 * 8 * 32];
-  __shared__ float sb1[kH], sb2[kH], sW3[2 * kH], sb3[2];
-  extern __shared__ float sw[];
+__global__ void __launch_bounds__(kTcRows)
+mlp_infer_tc_kernel(const float* __restrict__ params, int L, float U, const uint32_t* __restrict__ upb,
+                    const uint32_t* __restrict__ dnb, int64_t dim_dn, int64_t dim, T* __restrict__ out,
+                    int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
   const MlpDims d = mlp_dims(L);
-  const int KT1 = (d.nin + 15) / 16;
-  load_weights(params, d.P, sw);  // rounded weights
-  build_frags(sw + d.oW1, d.nin, KT1, f1);
-  build_frags(sw + d.oW2, kH, 4, f2);
-  for (int i = threadIdx.x; i < kH; i += blockDim.x) {
-    sb1[i] = sw[d.ob1 + i];
-    sb2[i] = sw[d.ob2 + i];
-    sW3[2 * i] = sw[d.oW3 + 2 * i];
-    sW3[2 * i + 1] = sw[d.oW3 + 2 * i + 1];
+  const TcLayout ly = tc_layout(d.nin);
+  const int K1 = ly.K1;
+  unsigned char* A1 = tsm + ly.a1;
+  unsigned char* A2 = tsm + ly.a2;
+  unsigned char* B1 = tsm + ly.b1;
+  unsigned char* B2 = tsm + ly.b2;
+  float* sb1 = reinterpret_cast<float*>(tsm + ly.par);
+  float* sb2 = sb1 + kH;
+  float* sW3 = sb2 + kH;
+  float* sb3 = sW3 + 2 * kH;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tsm + ly.tslot);
+  const uint32_t mbar = smem_addr(tsm + ly.mbar);
+  const int tid = threadIdx.x, warp = tid >> 5;
+
+  // rounded weights: W1, W2 as K-major B operands (row n = output unit), the rest in FP32
+  for (int i = tid; i < kH * K1; i += blockDim.x) {
+    const int n = i / K1, k = i - n * K1;
+    const float w = k < d.nin ? params[d.oW1 + k * kH + n] : 0.f;
+    *reinterpret_cast<__nv_bfloat16*>(B1 + cm_offset(n, k, K1)) = __float2bfloat16_rn(w);
   }
-  if (threadIdx.x < 2) sb3[threadIdx.x] = sw[d.ob3 + threadIdx.x];
+  for (int i = tid; i < kH * kH; i += blockDim.x) {
+    const int n = i / kH, k = i - n * kH;
+    *reinterpret_cast<__nv_bfloat16*>(B2 + cm_offset(n, k, kH)) =
+        __float2bfloat16_rn(params[d.oW2 + k * kH + n]);
+  }
+  for (int i = tid; i < kH; i += blockDim.x) {
+    sb1[i] = bf16r(params[d.ob1 + i]);
+    sb2[i] = bf16r(params[d.ob2 + i]);
+    sW3[2 * i] = bf16r(params[d.oW3 + 2 * i]);
+    sW3[2 * i + 1] = bf16r(params[d.oW3 + 2 * i + 1]);
+  }
+  if (tid < 2) sb3[tid] = bf16r(params[d.ob3 + tid]);
+  if (tid == 0) mbar_init(mbar, 1);
+  if (warp == 0) tc_alloc(smem_addr(tslot), kTcCols);
+  fence_smem_to_async();
+  tc_fence_before_sync();
   __syncthreads();
-  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  tc_fence_after_sync();
+  const uint32_t tmem = *tslot;
+  const uint32_t lanes = (uint32_t)(warp * 32) << 16;  // this warp's TMEM lane quarter
   const float u8 = bf16r(U * 0.125f);
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  for (int64_t base = wid * 16; base < dim; base += warps * 16) {
-    const int64_t e0 = base + g, e1 = base + g + 8;
-    uint32_t ub0 = 0, db0 = 0, ub1 = 0, db1 = 0;
-    if (e0 < dim) {
-      const int64_t u = e0 / dim_dn;
-      ub0 = upb[u];
-      db0 = dnb[e0 - u * dim_dn];
+  const uint32_t idesc = tc_idesc_bf16_f32(kTcRows, kH);
+  const uint32_t a1s = smem_addr(A1), a2s = smem_addr(A2), b1s = smem_addr(B1), b2s = smem_addr(B2);
+  const uint32_t sbo1 = (uint32_t)(K1 >> 3) << 7, sbo2 = (uint32_t)(kH >> 3) << 7;
+  constexpr unsigned long long kWaitNs = 1000000000ull;
+  uint32_t phase = 0;
+  bool ok = true;
+  const int64_t ntiles = (dim + kTcRows - 1) / kTcRows;
+  for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const int64_t e = tile * kTcRows + tid;
+    const bool valid = e < dim;
+    uint32_t ub = 0, db = 0;
+    if (valid) {
+      const int64_t u = e / dim_dn;
+      ub = upb[u];
+      db = dnb[e - u * dim_dn];
     }
-    if (e1 < dim) {
-      const int64_t u = e1 / dim_dn;
-      ub1 = upb[u];
-      db1 = dnb[e1 - u * dim_dn];
-    }
-    auto feat = [&](uint32_t ub, uint32_t db, int f) -> float {
+    auto feat = [&](int f) -> float {
       if (f < L) return (float)((ub >> f) & 1u);
       if (f < 2 * L) return (float)((db >> (f - L)) & 1u);
       return f == 2 * L ? u8 : 0.f;
     };
-    // ---- layer 1: acc[nt] = b1 + x W1 over KT1 k-tiles
-    float acc[8][4];
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      const float c0 = sb1[nt * 8 + 2 * q], c1 = sb1[nt * 8 + 2 * q + 1];
-      acc[nt][0] = c0;
-      acc[nt][1] = c1;
-      acc[nt][2] = c0;
-      acc[nt][3] = c1;
+    for (int j = 0; j < K1; j += 8) {
+      const uint4 w = make_uint4(pack_bf16(feat(j), feat(j + 1)), pack_bf16(feat(j + 2), feat(j + 3)),
+                                 pack_bf16(feat(j + 4), feat(j + 5)), pack_bf16(feat(j + 6), feat(j + 7)));
+      *reinterpret_cast<uint4*>(A1 + cm_offset(tid, j, K1)) = w;
     }
-    for (int kt = 0; kt < KT1; ++kt) {
-      const int c = kt * 16 + 2 * q;
-      uint32_t A[4];
-      A[0] = pack_bf16(feat(ub0, db0, c), feat(ub0, db0, c + 1));
-      A[1] = pack_bf16(feat(ub1, db1, c), feat(ub1, db1, c + 1));
-      A[2] = pack_bf16(feat(ub0, db0, c + 8), feat(ub0, db0, c + 9));
-      A[3] = pack_bf16(feat(ub1, db1, c + 8), feat(ub1, db1, c + 9));
-#pragma unroll
-      for (int nt = 0; nt < 8; ++nt) mma_bf16(acc[nt], A, f1[(kt * 8 + nt) * 32 + lane]);
+    // ---- layer 1 on the tensor cores
+    fence_smem_to_async();
+    tc_fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after_sync();
+      for (int s = 0; s < K1 / 16; ++s)
+        tc_mma_f16(tmem, tc_smem_desc(a1s + s * 256, 128, sbo1), tc_smem_desc(b1s + s * 256, 128, sbo1),
+                   idesc, s > 0);
+      tc_commit(mbar);
     }
-    // ---- layer 2: A fragments from tanh(layer 1), acc2 = b2 + h1 W2
-    uint32_t A2[4][4];
+    ok = __syncthreads_and(mbar_wait_bounded(mbar, phase, kWaitNs)) != 0;
+    phase ^= 1u;
+    if (!ok) break;
+    tc_fence_after_sync();
+    float h[kH];
+    tc_ld32(tmem + lanes, h);
+    tc_ld32(tmem + lanes + 32, h + 32);
 #pragma unroll
-    for (int kt = 0; kt < 4; ++kt) {
-      A2[kt][0] = pack_bf16(tanhf(acc[2 * kt][0]), tanhf(acc[2 * kt][1]));
-      A2[kt][1] = pack_bf16(tanhf(acc[2 * kt][2]), tanhf(acc[2 * kt][3]));
-      A2[kt][2] = pack_bf16(tanhf(acc[2 * kt + 1][0]), tanhf(acc[2 * kt + 1][1]));
-      A2[kt][3] = pack_bf16(tanhf(acc[2 * kt + 1][2]), tanhf(acc[2 * kt + 1][3]));
+    for (int j = 0; j < kH; j += 8) {
+      uint32_t w[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        w[q] = pack_bf16(tanhf(h[j + 2 * q] + sb1[j + 2 * q]), tanhf(h[j + 2 * q + 1] + sb1[j + 2 * q + 1]));
+      *reinterpret_cast<uint4*>(A2 + cm_offset(tid, j, kH)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      const float c0 = sb2[nt * 8 + 2 * q], c1 = sb2[nt * 8 + 2 * q + 1];
-      acc[nt][0] = c0;
-      acc[nt][1] = c1;
-      acc[nt][2] = c0;
-      acc[nt][3] = c1;
+    // ---- layer 2 on the tensor cores
+    fence_smem_to_async();
+    tc_fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after_sync();
+      for (int s = 0; s < kH / 16; ++s)
+        tc_mma_f16(tmem + kH, tc_smem_desc(a2s + s * 256, 128, sbo2), tc_smem_desc(b2s + s * 256, 128, sbo2),
+                   idesc, s > 0);
+      tc_commit(mbar);
     }
+    ok = __syncthreads_and(mbar_wait_bounded(mbar, phase, kWaitNs)) != 0;
+    phase ^= 1u;
+    if (!ok) break;
+    tc_fence_after_sync();
+    tc_ld32(tmem + lanes + kH, h);
+    tc_ld32(tmem + lanes + kH + 32, h + 32);
+    // ---- output layer on the CUDA cores
+    float a = sb3[0], z = sb3[1];
 #pragma unroll
-    for (int kt = 0; kt < 4; ++kt)
-#pragma unroll
-      for (int nt = 0; nt < 8; ++nt) mma_bf16(acc[nt], A2[kt], f2[(kt * 8 + nt) * 32 + lane]);
-    // ---- layer 3: partial dot products over this thread's 16 hidden units, then the 4 lanes
-    float a0 = 0.f, z0 = 0.f, a1 = 0.f, z1 = 0.f;
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      const int c = nt * 8 + 2 * q;
-      const float h00 = tanhf(acc[nt][0]), h01 = tanhf(acc[nt][1]);
-      const float h10 = tanhf(acc[nt][2]), h11 = tanhf(acc[nt][3]);
-      a0 = fmaf(h00, sW3[2 * c], fmaf(h01, sW3[2 * c + 2], a0));
-      z0 = fmaf(h00, sW3[2 * c + 1], fmaf(h01, sW3[2 * c + 3], z0));
-      a1 = fmaf(h10, sW3[2 * c], fmaf(h11, sW3[2 * c + 2], a1));
-      z1 = fmaf(h10, sW3[2 * c + 1], fmaf(h11, sW3[2 * c + 3], z1));
+    for (int n = 0; n < kH; ++n) {
+      const float t = tanhf(h[n] + sb2[n]);
+      a = fmaf(t, sW3[2 * n], a);
+      z = fmaf(t, sW3[2 * n + 1], z);
     }
-#pragma unroll
-    for (int o = 1; o <= 2; o <<= 1) {
-      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-      z0 += __shfl_xor_sync(0xffffffffu, z0, o);
-      a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-      z1 += __shfl_xor_sync(0xffffffffu, z1, o);
+    if (valid) {
+      const float v = expf(a);
+      out[e] = (T)(z >= 0.f ? v : -v);
     }
-    if (q == 0) {
-      a0 += sb3[0];
-      z0 += sb3[1];
-      a1 += sb3[0];
-      z1 += sb3[1];
-      if (e0 < dim) {
-        const float v = expf(a0);
-        out[e0] = (T)(z0 >= 0.f ? v : -v);
-      }
-      if (e1 < dim) {
-        const float v = expf(a1);
-        out[e1] = (T)(z1 >= 0.f ? v : -v);
-      }
-    }
+    tc_fence_before_sync();  // this tile's TMEM reads before the next tile's MMAs
+  }
+  if (!ok && tid == 0) atomicExch(err, 1);
+  tc_fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after_sync();
+    tc_dealloc(tmem, kTcCols);
   }
 }
 
@@ -465,6 +492,7 @@ struct ed_mlp {
   int64_t cap = 0;  // batch capacity of idx / tgt
   int ncta = 0;
   int step = 0;
+  int* err = nullptr;  // timeout flag of the inference kernel
 };
 
 namespace {
@@ -503,6 +531,7 @@ extern "C" void ed_mlp_destroy(ed_mlp* M) {
   if (M->loss) cudaFree(M->loss);
   if (M->idx) cudaFree(M->idx);
   if (M->tgt) cudaFree(M->tgt);
+  if (M->err) cudaFree(M->err);
   if (prev != M->device) cudaSetDevice(prev);
   delete M;
 }
@@ -525,7 +554,8 @@ extern "C" ed_status ed_mlp_create(int32_t n_sites, uint64_t seed, void* stream,
             cudaMalloc((void**)&M->grad, P * 4) == cudaSuccess &&
             cudaMalloc((void**)&M->partial, (size_t)M->ncta * P * 4) == cudaSuccess &&
             cudaMalloc((void**)&M->lpart, (size_t)M->ncta * 8) == cudaSuccess &&
-            cudaMalloc((void**)&M->loss, 8) == cudaSuccess;
+            cudaMalloc((void**)&M->loss, 8) == cudaSuccess &&
+            cudaMalloc((void**)&M->err, sizeof(int)) == cudaSuccess;
   if (!ok) {
     ed_mlp_destroy(M);
     set_error("ed_mlp_create: out of device memory");
@@ -597,19 +627,29 @@ extern "C" ed_status ed_mlp_infer(ed_mlp* M, const ed_basis* b, double U, ed_dty
   clear_error();
   ED_CHECK_ARG(M && b && out && aligned16(out), "ed_mlp_infer: bad arguments");
   ED_CHECK_ARG(b->n_sites == M->L, "ed_mlp_infer: basis has %d sites, network %d", b->n_sites, M->L);
-  const size_t sm = (size_t)M->d.P * sizeof(float);
-  const int grid = sm_count() * 8;
+  const TcLayout ly = tc_layout(M->d.nin);
+  const int sm = (int)std::max<uint32_t>(ly.total, (uint32_t)kTcSmemMin);
+  const int64_t ntiles = (b->dim + kTcRows - 1) / kTcRows;
+  const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sm_count() * 3);
+  ED_TRY_CUDA(cudaMemsetAsync(M->err, 0, sizeof(int), M->stream));
   if (dtype == ED_F32) {
-    ED_TRY_CUDA(cudaFuncSetAttribute(mlp_infer_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    mlp_infer_kernel<float><<<grid, kMThreads, sm, M->stream>>>(M->params, M->L, (float)U,
-                                                                b->user_up().bits, b->user_dn().bits,
-                                                                b->user_dn().dim, b->dim, (float*)out);
+    ED_TRY_CUDA(cudaFuncSetAttribute(mlp_infer_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    mlp_infer_tc_kernel<float><<<grid, kTcRows, sm, M->stream>>>(
+        M->params, M->L, (float)U, b->user_up().bits, b->user_dn().bits, b->user_dn().dim, b->dim,
+        (float*)out, M->err);
   } else {
-    ED_TRY_CUDA(cudaFuncSetAttribute(mlp_infer_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    mlp_infer_kernel<double><<<grid, kMThreads, sm, M->stream>>>(M->params, M->L, (float)U,
-                                                                 b->user_up().bits, b->user_dn().bits,
-                                                                 b->user_dn().dim, b->dim, (double*)out);
+    ED_TRY_CUDA(cudaFuncSetAttribute(mlp_infer_tc_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    mlp_infer_tc_kernel<double><<<grid, kTcRows, sm, M->stream>>>(
+        M->params, M->L, (float)U, b->user_up().bits, b->user_dn().bits, b->user_dn().dim, b->dim,
+        (double*)out, M->err);
   }
   ED_TRY_CUDA(cudaGetLastError());
+  int h = 0;
+  ED_TRY_CUDA(cudaMemcpyAsync(&h, M->err, sizeof(int), cudaMemcpyDeviceToHost, M->stream));
+  ED_TRY_CUDA(cudaStreamSynchronize(M->stream));
+  if (h) {
+    set_error("ed_mlp_infer: a tensor-core completion wait ran out");
+    return ED_ERR_TIMEOUT;
+  }
   return ED_OK;
 }
