@@ -15,7 +15,9 @@ Module map:
   lanczos      Algorithm 1 in FP64, optional full reorthogonalisation (Sec. 2.2)
   dense        dense diagonalisation for small dimensions
   observables  double occupancy of a state vector (the on-site term; dE0/dU)
+  complex_hopping  H with a complex amplitude per bond (Sec. 2.1: the checkerboard lattice's
+               complex hoppings) and its real view
   mlp          the learned start-vector network, its loss and gradient (no counterpart in
                the paper; test oracle of the library's MLP kernels)
 """
-from . import basis, hamiltonian, tridiag, lanczos, dense, mlp, observables  # noqa: F401
+from . import basis, hamiltonian, tridiag, lanczos, dense, mlp, observables, complex_hopping  # noqa: F401
