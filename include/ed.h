@@ -57,12 +57,28 @@ typedef enum {
  *                 runs no FP64 instruction per vector element.
  *  ED_F32         FP32 vectors and FP32 H.v arithmetic; a_j, b_j, dot-product accumulation
  *                 and the tridiagonal eigensolve in FP64.
- *  ED_F64_NATIVE  FP64 vectors and FP64 arithmetic throughout (the plain method). */
-typedef enum { ED_F64 = 0, ED_F32 = 1, ED_F64_NATIVE = 2 } ed_dtype;
+ *  ED_F64_NATIVE  FP64 vectors and FP64 arithmetic throughout (the plain method).
+ *  ED_C32         complex vectors (interleaved re, im) of FP32 pairs, complex FP32 H.v
+ *                 arithmetic; a_j, b_j (real for Hermitian H), dot products and the
+ *                 tridiagonal eigensolve in FP64. For lattices with complex amplitudes.
+ *  ED_C64         complex vectors of FP64 pairs, FP64 arithmetic throughout.
+ * Complex vectors are arrays of dim (re, im) pairs = 2 dim scalars, element i of the basis
+ * at scalars 2i, 2i + 1. A real dtype requires a lattice without t_bond; a complex dtype
+ * takes either (no t_bond: every amplitude 1). */
+typedef enum {
+  ED_F64 = 0,
+  ED_F32 = 1,
+  ED_F64_NATIVE = 2,
+  ED_C32 = 3,
+  ED_C64 = 4
+} ed_dtype;
 
 /* Lattice (Sec. 2.1): n_sites in [1, 32]; bonds is a HOST array [n_bonds][2] of site
- * pairs (i != j, both in range), read during ed_build_basis only. t_bond must be NULL
- * (uniform hopping t); per-bond amplitudes are reserved for a later version. */
+ * pairs (i != j, both in range), read during ed_build_basis only. t_bond is NULL (every
+ * bond hops with amplitude t, Eq. 1) or a HOST array of n_bonds complex relative
+ * amplitudes as (re, im) pairs (2 n_bonds doubles): bond b = (i, j) then contributes
+ * -t (tau_b c+_i c_j + conj(tau_b) c+_j c_i) for each spin (the checkerboard lattice's
+ * complex hoppings, Sec. 2.1 Fig. 1), and only the complex dtypes apply. */
 typedef struct {
   int32_t n_sites;
   int32_t n_bonds;
@@ -83,7 +99,9 @@ typedef struct {
  *  reorth     0 = none (Algorithm 1 as printed). Other values are reserved.
  *  seed       SplitMix64 seed of the random start vector when f1 == NULL.
  *  dtype      see ed_dtype; f1 vectors are FP64 for ED_F64 and ED_F64_NATIVE, FP32 for
- *             ED_F32.
+ *             ED_F32, complex pairs for ED_C32 / ED_C64. The seeded complex start vector
+ *             takes element i = (r_2i, r_2i+1) from the real sequence of ed_start_vector
+ *             over 2 dim entries, scaled to unit norm.
  *  schedule   fused H.v kernel variant (1..7 for ED_F32, 8..13 for ED_F64; a variant of
  *             the other precision or one that does not fit falls back to the default one,
  *             see ed_lanczos_schedule); -1 = for bases of at least 2^22 states, the fastest
@@ -136,7 +154,8 @@ void ed_basis_destroy(ed_basis* basis);
 /* ed_hv - y = H x (the product of Algorithm 1's first update; Sec. 4 Eqs. 5-6 split it into
  * the up part, which mixes sub-vectors, and the down part, which acts inside each). x and y
  * are DEVICE arrays of dim elements (FP64 for ED_F64 and ED_F64_NATIVE, which both compute
- * in FP64 here; FP32 for ED_F32), distinct and 16-byte aligned. Asynchronous. */
+ * in FP64 here; FP32 for ED_F32; complex pairs for ED_C32 / ED_C64), distinct and 16-byte
+ * aligned. Asynchronous. */
 ed_status ed_hv(const ed_basis* basis, const ed_params* params, ed_dtype dtype, const void* x,
                 void* y, void* stream);
 

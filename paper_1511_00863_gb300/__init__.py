@@ -20,7 +20,7 @@ LIB_PATH = os.environ.get("ED_LIB_PATH") or os.path.join(_HERE, "libed.so")
 
 ED_OK, ED_BREAKDOWN = 0, 1
 ED_ERR_ARG, ED_ERR_OOM, ED_ERR_CUDA, ED_ERR_TIMEOUT, ED_ERR_NOT_CONVERGED = -1, -2, -3, -4, -5
-ED_F64, ED_F32, ED_F64_NATIVE = 0, 1, 2
+ED_F64, ED_F32, ED_F64_NATIVE, ED_C32, ED_C64 = 0, 1, 2, 3, 4
 ED_MAX_STEPS = 1000
 
 
@@ -114,7 +114,8 @@ def _ptr(t, dtype_code=None, numel=None):
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
         raise ValueError("expected a contiguous CUDA tensor")
     if dtype_code is not None:
-        want = torch.float32 if dtype_code == ED_F32 else torch.float64
+        want = {ED_F32: torch.float32, ED_C32: torch.complex64,
+                ED_C64: torch.complex128}.get(dtype_code, torch.float64)
         if t.dtype != want:
             raise ValueError(f"expected {want}, got {t.dtype}")
     if numel is not None and t.numel() != numel:
@@ -129,18 +130,35 @@ def dtype_code(dtype) -> int:
         return ED_F64
     if dtype in (ED_F32, "f32", "float32", "fp32"):
         return ED_F32
+    if dtype in (ED_C32, "c32", "complex64"):
+        return ED_C32
+    if dtype in (ED_C64, "c64", "complex128"):
+        return ED_C64
     import torch
     if dtype == torch.float64:
         return ED_F64
     if dtype == torch.float32:
         return ED_F32
+    if dtype == torch.complex64:
+        return ED_C32
+    if dtype == torch.complex128:
+        return ED_C64
     raise ValueError(f"unknown dtype {dtype!r}")
 
 
 # ------------------------------------------------------------------------ basis
-def ed_build_basis(n_sites: int, bonds, n_up: int, n_dn: int, stream=None) -> c_void_p:
+def ed_build_basis(n_sites: int, bonds, n_up: int, n_dn: int, stream=None, t_bond=None) -> c_void_p:
+    """t_bond: None, or one complex relative amplitude per bond (then only the complex
+    dtypes apply)."""
     b = np.ascontiguousarray(np.asarray(bonds, dtype=np.int32).reshape(-1, 2))
-    lat = ed_lattice(n_sites, b.shape[0], b.ctypes.data_as(POINTER(c_int32)), None)
+    tb = None
+    if t_bond is not None:
+        tc = np.asarray(t_bond, dtype=np.complex128).reshape(-1)
+        if tc.shape[0] != b.shape[0]:
+            raise ValueError("t_bond needs one amplitude per bond")
+        tb = np.ascontiguousarray(np.stack([tc.real, tc.imag], axis=1).reshape(-1))
+    lat = ed_lattice(n_sites, b.shape[0], b.ctypes.data_as(POINTER(c_int32)),
+                     tb.ctypes.data_as(POINTER(c_double)) if tb is not None else None)
     out = c_void_p()
     _check(_lib.ed_build_basis(byref(lat), n_up, n_dn, _stream(stream), byref(out)))
     return out

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <cmath>
 #include <vector>
 
 #include "ed_internal.cuh"
@@ -77,7 +78,7 @@ __global__ void unrank_kernel(uint32_t* __restrict__ bits, int64_t dim, int n_si
 __global__ void hop_kernel(const uint32_t* __restrict__ bits, int64_t dim,
                            const int2* __restrict__ bonds, int n_bonds,
                            const uint32_t* __restrict__ C, int32_t* __restrict__ hop,
-                           int maxhops, int* __restrict__ maxcount) {
+                           int32_t* __restrict__ hopa, int maxhops, int* __restrict__ maxcount) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < dim;
        r += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t s = bits[r];
@@ -91,12 +92,16 @@ __global__ void hop_kernel(const uint32_t* __restrict__ bits, int64_t dim,
           const uint32_t neg = (uint32_t)__popc(s & between) & 1u;
           const uint32_t tgt = rank_state(s ^ ((1u << i) | (1u << j)), C);
           hop[(int64_t)cnt * dim + r] = (int32_t)(tgt | (neg << 31));
+          if (hopa) hopa[(int64_t)cnt * dim + r] = 2 * b + (int)((s >> j) & 1u);
         }
         ++cnt;
       }
     }
     if (hop) {
-      for (int k = cnt; k < maxhops; ++k) hop[(int64_t)k * dim + r] = (int32_t)dim;
+      for (int k = cnt; k < maxhops; ++k) {
+        hop[(int64_t)k * dim + r] = (int32_t)dim;
+        if (hopa) hopa[(int64_t)k * dim + r] = 0;
+      }
     } else {
       atomicMax(maxcount, cnt);
     }
@@ -113,7 +118,7 @@ static uint64_t binom_host(int n, int k) {
 }
 
 static ed_status build_species(SpeciesTables& sp, int n_sites, int n, const int2* d_bonds,
-                               int n_bonds, const uint32_t* d_binom, int* d_count,
+                               int n_bonds, const uint32_t* d_binom, int* d_count, bool amps,
                                cudaStream_t s) {
   sp.dim = (int64_t)binom_host(n_sites, n);
   ED_TRY_CUDA(cudaMallocAsync((void**)&sp.bits, sp.dim * sizeof(uint32_t), s));
@@ -124,7 +129,7 @@ static ed_status build_species(SpeciesTables& sp, int n_sites, int n, const int2
   ED_TRY_CUDA(cudaGetLastError());
   ED_TRY_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), s));
   hop_kernel<<<blocks, threads, 0, s>>>(sp.bits, sp.dim, d_bonds, n_bonds, d_binom, nullptr,
-                                        0, d_count);
+                                        nullptr, 0, d_count);
   ED_TRY_CUDA(cudaGetLastError());
   int h = 0;
   ED_TRY_CUDA(cudaMemcpyAsync(&h, d_count, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -132,8 +137,9 @@ static ed_status build_species(SpeciesTables& sp, int n_sites, int n, const int2
   sp.maxhops = h;
   if (h > 0) {
     ED_TRY_CUDA(cudaMallocAsync((void**)&sp.hop, (size_t)h * sp.dim * sizeof(int32_t), s));
+    if (amps) ED_TRY_CUDA(cudaMallocAsync((void**)&sp.hopa, (size_t)h * sp.dim * sizeof(int32_t), s));
     hop_kernel<<<blocks, threads, 0, s>>>(sp.bits, sp.dim, d_bonds, n_bonds, d_binom, sp.hop,
-                                          h, nullptr);
+                                          sp.hopa, h, nullptr);
     ED_TRY_CUDA(cudaGetLastError());
   }
   return ED_OK;
@@ -207,8 +213,10 @@ static ed_status rcm_order(const SpeciesTables& sp, cudaStream_t s, std::vector<
 static void free_species(SpeciesTables& sp) {
   if (sp.bits) cudaFree(sp.bits);
   if (sp.hop) cudaFree(sp.hop);
+  if (sp.hopa) cudaFree(sp.hopa);
   sp.bits = nullptr;
   sp.hop = nullptr;
+  sp.hopa = nullptr;
 }
 
 }  // namespace ed
@@ -225,7 +233,6 @@ extern "C" ed_status ed_build_basis(const ed_lattice* L, int32_t n_up, int32_t n
                "ed_build_basis: n_sites = %d outside [1, 32]", L->n_sites);
   ED_CHECK_ARG(L->n_bonds >= 0, "ed_build_basis: n_bonds < 0");
   ED_CHECK_ARG(L->n_bonds == 0 || L->bonds != nullptr, "ed_build_basis: bonds is NULL");
-  ED_CHECK_ARG(L->t_bond == nullptr, "ed_build_basis: per-bond amplitudes are not supported");
   ED_CHECK_ARG(n_up >= 0 && n_up <= L->n_sites && n_dn >= 0 && n_dn <= L->n_sites,
                "ed_build_basis: particle numbers (%d, %d) outside [0, n_sites]", n_up, n_dn);
   std::vector<int2> hb(L->n_bonds > 0 ? L->n_bonds : 1);
@@ -235,6 +242,9 @@ extern "C" ed_status ed_build_basis(const ed_lattice* L, int32_t n_up, int32_t n
                  "ed_build_basis: bond %d = (%d, %d) invalid", b, i, j);
     hb[b] = make_int2(i, j);
   }
+  if (L->t_bond)
+    for (int b = 0; b < 2 * L->n_bonds; ++b)
+      ED_CHECK_ARG(std::isfinite(L->t_bond[b]), "ed_build_basis: t_bond[%d] is not finite", b);
   cudaStream_t s = (cudaStream_t)stream;
   ed_basis* B = new ed_basis();
   cudaGetDevice(&B->device);
@@ -264,9 +274,19 @@ extern "C" ed_status ed_build_basis(const ed_lattice* L, int32_t n_up, int32_t n
     set_error("ed_build_basis: host to device copy failed");
     return fail(ED_ERR_CUDA);
   }
-  if ((st = build_species(B->up, L->n_sites, n_up, d_bonds, L->n_bonds, B->binom, d_count, s)) != ED_OK)
+  const bool amps = L->t_bond != nullptr;
+  if (amps) {
+    B->n_bonds = L->n_bonds;
+    if (cudaMalloc((void**)&B->tau, (size_t)(L->n_bonds > 0 ? L->n_bonds : 1) * sizeof(double2)) != cudaSuccess ||
+        (L->n_bonds > 0 && cudaMemcpyAsync(B->tau, L->t_bond, (size_t)L->n_bonds * sizeof(double2),
+                                           cudaMemcpyHostToDevice, s) != cudaSuccess)) {
+      set_error("ed_build_basis: amplitude upload failed");
+      return fail(ED_ERR_OOM);
+    }
+  }
+  if ((st = build_species(B->up, L->n_sites, n_up, d_bonds, L->n_bonds, B->binom, d_count, amps, s)) != ED_OK)
     return fail(st);
-  if ((st = build_species(B->dn, L->n_sites, n_dn, d_bonds, L->n_bonds, B->binom, d_count, s)) != ED_OK)
+  if ((st = build_species(B->dn, L->n_sites, n_dn, d_bonds, L->n_bonds, B->binom, d_count, amps, s)) != ED_OK)
     return fail(st);
   B->dim = B->up.dim * B->dn.dim;
   if (B->dn.dim == 1 && B->up.dim > 1) {  // single occupied species: one long row
@@ -338,6 +358,7 @@ extern "C" void ed_basis_destroy(ed_basis* B) {
   free_species(B->dn);
   if (B->binom) cudaFree(B->binom);
   if (B->up_order) cudaFree(B->up_order);
+  if (B->tau) cudaFree(B->tau);
   if (prev != B->device) cudaSetDevice(prev);
   delete B;
 }

@@ -632,6 +632,7 @@ extern "C" ed_status ed_lanczos_solve_batched(int32_t n, const ed_basis* const* 
   for (int i = 0; i < n; ++i) {
     const ed_basis* b = bases[i];
     ED_CHECK_ARG(b != nullptr, "ed_lanczos_solve_batched: basis %d is NULL", i);
+    ED_CHECK_ARG(!b->has_tau(), "ed_lanczos_solve_batched: basis %d has complex amplitudes", i);
     ED_CHECK_ARG(b->dim < (1LL << 31), "ed_lanczos_solve_batched: instance %d too large", i);
     R.dims[i] = (int)b->dim;
     R.work[i] = (long long)b->dim * (b->up.maxhops + b->dn.maxhops + 4);

@@ -259,14 +259,22 @@ extern "C" ed_status ed_hv(const ed_basis* b, const ed_params* p, ed_dtype dtype
   clear_error();
   ED_CHECK_ARG(b != nullptr && p != nullptr, "ed_hv: basis or params is NULL");
   ED_CHECK_ARG(x != nullptr && y != nullptr, "ed_hv: x or y is NULL");
-  ED_CHECK_ARG(dtype == ED_F64 || dtype == ED_F32 || dtype == ED_F64_NATIVE,
+  ED_CHECK_ARG(dtype == ED_F64 || dtype == ED_F32 || dtype == ED_F64_NATIVE || is_complex(dtype),
                "ed_hv: unknown dtype %d", (int)dtype);
+  ED_CHECK_ARG(is_complex(dtype) || !b->has_tau(),
+               "ed_hv: the lattice has complex amplitudes; use ED_C32 or ED_C64");
   ED_CHECK_ARG(aligned16(x) && aligned16(y), "ed_hv: x and y must be 16-byte aligned");
-  const size_t es = dtype == ED_F32 ? 4 : 8;
+  const size_t es = dtype == ED_F32 ? 4 : dtype == ED_C32 ? 8 : dtype == ED_C64 ? 16 : 8;
   const char* xb = (const char*)x;
   const char* yb = (const char*)y;
   ED_CHECK_ARG(xb + b->dim * es <= yb || yb + b->dim * es <= xb, "ed_hv: x and y overlap");
   cudaStream_t s = (cudaStream_t)stream;
+  if (is_complex(dtype)) {
+    const ed_status rc = hvc_prepare(b, dtype);
+    if (rc != ED_OK) return rc;
+    return dtype == ED_C32 ? launch_hvc<float>(b, p->t, p->U, x, y, b->dn.dim, s)
+                           : launch_hvc<double>(b, p->t, p->U, x, y, b->dn.dim, s);
+  }
   const ed_status r = hv_prepare(b, dtype == ED_F32 ? ED_F32 : ED_F64_NATIVE);
   if (r != ED_OK) return r;
   if (dtype != ED_F32)

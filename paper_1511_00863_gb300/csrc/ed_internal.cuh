@@ -44,6 +44,10 @@ struct SpeciesTables {
   int32_t maxhops = 0;
   uint32_t* bits = nullptr;  // [dim]
   int32_t* hop = nullptr;    // [maxhops * dim], unused slots = dim
+  // Lattices with per-bond amplitudes only: amplitude index of each hop, 2 b + 1 when the
+  // state's particle sits at site j of bond b = (i, j) and hops to i, 2 b when it sits at i
+  // and hops to j; same layout as `hop`.
+  int32_t* hopa = nullptr;
 };
 
 }  // namespace ed
@@ -71,6 +75,11 @@ struct ed_basis {
   // padded to 32. The global index rank_up * dim_dn + rank_dn is unchanged (one factor is
   // 1); `up`/`dn` below are the kernels' view, user_up()/user_dn() the caller's.
   bool swapped = false;
+  // Per-bond relative amplitudes (device, n_bonds (re, im) pairs) when the lattice has them;
+  // then only the complex dtypes apply.
+  int32_t n_bonds = 0;
+  double2* tau = nullptr;
+  bool has_tau() const { return tau != nullptr; }
   const ed::SpeciesTables& user_up() const { return swapped ? dn : up; }
   const ed::SpeciesTables& user_dn() const { return swapped ? up : dn; }
 };
@@ -133,6 +142,15 @@ ed_status launch_hv(const ed_basis* b, double t, double U, const T* x, T* y, int
 // Set the kernel attributes launch_hv relies on (dynamic shared memory size); call before
 // the first launch on a device and outside stream capture.
 ed_status hv_prepare(const ed_basis* b, ed_dtype dtype);
+
+// Complex H.v (ed_hvc.cu) for ED_C32 (T = float) / ED_C64 (T = double): x, y are arrays of
+// (re, im) pairs with row stride ld pairs; with lz, fused with the Lanczos epilogue like
+// launch_hv (partial sums of the real dot product of the interleaved vectors).
+template <typename T>
+ed_status launch_hvc(const ed_basis* b, double t, double U, const void* x, void* y, int64_t ld,
+                     cudaStream_t s, const LzHvArgs* lz = nullptr, int* grid_out = nullptr);
+ed_status hvc_prepare(const ed_basis* b, ed_dtype dtype);
+inline bool is_complex(ed_dtype d) { return d == ED_C32 || d == ED_C64; }
 
 // FP64-accurate Lanczos path (int64 fixed point, ed_fixed.cu).
 struct FxRun {

@@ -234,10 +234,15 @@ static ed_status lz_launch_step(ed_lanczos* st, const ed_params* p, cudaStream_t
   int grid = 0;
   ed_status r;
   if (ev0) ED_TRY_CUDA(cudaEventRecord(ev0, s));
+  const ed_dtype dt = st->opts.dtype;
   if (st->plan) {
     grid = hv2_grid(st->plan);
     r = hv2_launch(st->plan, b, p->t, p->U, st->B[c], st->B[1 - c], st->S, c, st->pa, s);
-  } else if (st->opts.dtype == ED_F64_NATIVE)
+  } else if (dt == ED_C32) {
+    r = launch_hvc<float>(b, p->t, p->U, st->B[c], st->B[1 - c], st->ld, s, &lz, &grid);
+  } else if (dt == ED_C64) {
+    r = launch_hvc<double>(b, p->t, p->U, st->B[c], st->B[1 - c], st->ld, s, &lz, &grid);
+  } else if (dt == ED_F64_NATIVE)
     r = launch_hv<double>(b, p->t, p->U, (const double*)st->B[c], (double*)st->B[1 - c], st->ld,
                           s, &lz, &grid);
   else
@@ -245,13 +250,15 @@ static ed_status lz_launch_step(ed_lanczos* st, const ed_params* p, cudaStream_t
                          s, &lz, &grid);
   if (r != ED_OK) return r;
   if (ev1) ED_TRY_CUDA(cudaEventRecord(ev1, s));
-  const int ug = red_grid(st->n);
-  if (st->opts.dtype == ED_F64_NATIVE)
+  // the update works on scalars: a complex vector is 2 n of them (a_j, b_j are real)
+  const int64_t ns = is_complex(dt) ? 2 * st->n : st->n;
+  const int ug = red_grid(ns);
+  if (dt == ED_F64_NATIVE || dt == ED_C64)
     lz_update_kernel<double><<<ug, kRedThreads, 0, s>>>(
-        st->S, c, (const double*)st->B[c], (double*)st->B[1 - c], st->n, st->pa, grid, st->pb);
+        st->S, c, (const double*)st->B[c], (double*)st->B[1 - c], ns, st->pa, grid, st->pb);
   else
     lz_update_kernel<float><<<ug, kRedThreads, 0, s>>>(
-        st->S, c, (const float*)st->B[c], (float*)st->B[1 - c], st->n, st->pa, grid, st->pb);
+        st->S, c, (const float*)st->B[c], (float*)st->B[1 - c], ns, st->pa, grid, st->pb);
   ED_TRY_CUDA(cudaGetLastError());
   lz_finish_kernel<<<1, kRedThreads, 0, s>>>(st->S, c, st->pb, ug);
   ED_TRY_CUDA(cudaGetLastError());
@@ -263,7 +270,8 @@ static ed_status check_opts(const ed_opts* o) {
   ED_CHECK_ARG(o != nullptr, "opts is NULL");
   ED_CHECK_ARG(o->max_steps >= 1 && o->max_steps <= ED_MAX_STEPS,
                "max_steps = %d outside [1, %d]", o->max_steps, ED_MAX_STEPS);
-  ED_CHECK_ARG(o->dtype == ED_F64 || o->dtype == ED_F32 || o->dtype == ED_F64_NATIVE,
+  ED_CHECK_ARG(o->dtype == ED_F64 || o->dtype == ED_F32 || o->dtype == ED_F64_NATIVE ||
+                   is_complex(o->dtype),
                "unknown dtype %d", (int)o->dtype);
   ED_CHECK_ARG(o->reorth == 0, "reorth = %d is not supported (0 = none)", o->reorth);
   ED_CHECK_ARG(std::isfinite(o->tol), "tol is not finite");
@@ -384,12 +392,15 @@ static ed_status lz_alloc(const ed_basis* b, const ed_opts* o, cudaStream_t s, e
   ED_CHECK_ARG(b != nullptr, "basis is NULL");
   ed_status r = check_opts(o);
   if (r != ED_OK) return r;
+  ED_CHECK_ARG(is_complex(o->dtype) || !b->has_tau(),
+               "the lattice has complex amplitudes; use ED_C32 or ED_C64");
   ed_lanczos* st = new ed_lanczos();
   st->basis = b;
   st->opts = *o;
   cudaGetDevice(&st->device);
   st->stream = s;
-  st->esize = o->dtype == ED_F32 ? 4 : 8;
+  // bytes per element (a complex element is an (re, im) pair)
+  st->esize = o->dtype == ED_F32 ? 4 : o->dtype == ED_C32 ? 8 : o->dtype == ED_C64 ? 16 : 8;
   st->fx = o->dtype == ED_F64;
   if (st->fx) st->fxr = fx_make(b);
   st->ld = (b->dn.dim + 31) / 32 * 32;
@@ -415,7 +426,7 @@ static ed_status lz_alloc(const ed_basis* b, const ed_opts* o, cudaStream_t s, e
     set_error("Lanczos scalars: out of device memory");
     return fail(ED_ERR_OOM);
   }
-  if (o->dtype != ED_F64_NATIVE) {
+  if (o->dtype == ED_F32 || o->dtype == ED_F64) {
     int sched = o->schedule;
     if (sched < 0) {
       // autotune once per basis and dtype: time every variant on this run's zeroed buffers
@@ -458,7 +469,11 @@ static ed_status lz_reset(ed_lanczos* st, const ed_opts* o, const void* f1, int 
   h.scale[1] = 0.0;
   for (int i = 0; i < ED_MAX_STEPS + 2; ++i) h.E0[i] = NAN;
   ED_TRY_CUDA(cudaMemcpyAsync(st->S, &h, sizeof(h), cudaMemcpyHostToDevice, s));
-  const int64_t dim = b->dim, cols = b->dn.dim;
+  // a complex vector is seen as scalars: dim (re, im) pairs = 2 dim scalars, rows of 2 cols
+  // scalars with stride 2 ld, so the real kernels below write the interleaved layout
+  const int cx = is_complex(o->dtype) ? 2 : 1;
+  const int64_t dim = cx * b->dim, cols = cx * b->dn.dim, lds = cx * st->ld;
+  const bool dbl = o->dtype == ED_F64_NATIVE || o->dtype == ED_C64;
   const int g = red_grid(dim);
   ED_CHECK_ARG((int64_t)g <= st->npb, "internal: partial buffer too small");
   st->cur = 0;
@@ -472,19 +487,19 @@ static ed_status lz_reset(ed_lanczos* st, const ed_opts* o, const void* f1, int 
   }
   if (f1 == nullptr) {
     start_norm_kernel<<<g, kRedThreads, 0, s>>>(o->seed, dim, st->pb);
-    if (o->dtype == ED_F64_NATIVE)
-      start_write_kernel<double><<<g, kRedThreads, 0, s>>>(o->seed, dim, cols, st->ld, colpos,
+    if (dbl)
+      start_write_kernel<double><<<g, kRedThreads, 0, s>>>(o->seed, dim, cols, lds, colpos,
                                                            st->pb, g, (double*)st->B[0]);
     else
-      start_write_kernel<float><<<g, kRedThreads, 0, s>>>(o->seed, dim, cols, st->ld, colpos,
+      start_write_kernel<float><<<g, kRedThreads, 0, s>>>(o->seed, dim, cols, lds, colpos,
                                                           st->pb, g, (float*)st->B[0]);
     init_scalars_kernel<<<1, 32, 0, s>>>(st->S, st->pb, g, 0);
   } else {
-    if (o->dtype == ED_F64_NATIVE)
-      copy_in_kernel<double><<<g, kRedThreads, 0, s>>>((const double*)f1, dim, cols, st->ld,
+    if (dbl)
+      copy_in_kernel<double><<<g, kRedThreads, 0, s>>>((const double*)f1, dim, cols, lds,
                                                        colpos, (double*)st->B[0], st->pb);
     else
-      copy_in_kernel<float><<<g, kRedThreads, 0, s>>>((const float*)f1, dim, cols, st->ld,
+      copy_in_kernel<float><<<g, kRedThreads, 0, s>>>((const float*)f1, dim, cols, lds,
                                                       colpos, (float*)st->B[0], st->pb);
     init_scalars_kernel<<<1, kRedThreads, 0, s>>>(st->S, st->pb, g, 1);
   }
@@ -514,7 +529,10 @@ extern "C" ed_status ed_lanczos_init(const ed_basis* b, const ed_opts* o, const 
   clear_error();
   ED_CHECK_ARG(out != nullptr, "ed_lanczos_init: out is NULL");
   ed_status r = lz_init(b, o, f1, (cudaStream_t)stream, ED_MAX_STEPS + 1, true, out);
-  if (r == ED_OK) r = o->dtype == ED_F64 ? fx_prepare(b) : hv_prepare(b, o->dtype);
+  if (r == ED_OK)
+    r = o->dtype == ED_F64 ? fx_prepare(b)
+        : is_complex(o->dtype) ? hvc_prepare(b, o->dtype)
+                               : hv_prepare(b, o->dtype);
   if (r != ED_OK && *out) {
     ed_lanczos_destroy(*out);
     *out = nullptr;
@@ -705,7 +723,10 @@ static ed_status solve_on(ed_lanczos* st, const ed_basis* b, const ed_params* p,
   const int check = (o->tol > 0.0 || E0_hist) ? 1 : ED_MAX_STEPS + 1;
   ed_status r = lz_reset(st, o, f1, check, false);
   if (r != ED_OK) return r;
-  if ((r = (o->dtype == ED_F64 ? fx_prepare(b) : hv_prepare(b, o->dtype))) != ED_OK) return r;
+  if ((r = (o->dtype == ED_F64 ? fx_prepare(b)
+            : is_complex(o->dtype) ? hvc_prepare(b, o->dtype)
+                                   : hv_prepare(b, o->dtype))) != ED_OK)
+    return r;
   if (!st->graph || st->graph_t != p->t || st->graph_U != p->U) {
     if (st->graph) cudaGraphExecDestroy(st->graph);
     st->graph = nullptr;

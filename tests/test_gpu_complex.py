@@ -1,0 +1,150 @@
+"""Complex hopping amplitudes (ED_C32 / ED_C64) through the C ABI against the oracle
+(oracle/complex_hopping.py): H.v element by element, Lanczos coefficients from the same
+start vector, ground-state energies against dense diagonalisation, the flux-threaded ring's
+closed form, gauge and conjugation invariance, and the real limit."""
+import math
+
+import numpy as np
+import pytest
+
+import ed_inputs
+from oracle import complex_hopping as ch
+from oracle import dense, lanczos as olz
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EPS = {"c64": 2.0 ** -53, "c32": 2.0 ** -24}
+TDT = {"c64": torch.complex128, "c32": torch.complex64}
+
+
+@pytest.fixture(scope="module")
+def ed():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1511_00863_gb300 as m
+    return m
+
+
+def _rand_tb(nb, seed):
+    r = np.random.default_rng(seed)
+    return r.uniform(0.5, 1.5, nb) * np.exp(1j * r.uniform(-math.pi, math.pi, nb))
+
+
+def _cplx(raw):
+    return raw[0::2] + 1j * raw[1::2]
+
+
+HV_CASES = [
+    (6, ed_inputs.ring_bonds(6), 3, 2),
+    (8, ed_inputs.torus_bonds(2, 4), 2, 3),
+    (9, np.array([[0, 5], [3, 8], [1, 2], [7, 0], [6, 4], [2, 8], [5, 1], [4, 3]]), 4, 3),
+    (10, ed_inputs.ring_bonds(10), 4, 0),
+    (12, np.array([[i, (i + 1) % 12] for i in range(12)] + [[i, (i + 5) % 12] for i in range(12)]), 3, 4),
+]
+
+
+@pytest.mark.parametrize("case", HV_CASES)
+@pytest.mark.parametrize("dtype", ["c64", "c32"])
+@pytest.mark.parametrize("amplitudes", [True, False])
+def test_hv_elementwise(ed, case, dtype, amplitudes):
+    L, bonds, nu, nd = case
+    tb = _rand_tb(len(bonds), 7) if amplitudes else None
+    t, U = 0.8, 2.7
+    b = ed.ed_build_basis(L, bonds, nu, nd, t_bond=tb)
+    try:
+        dim = ed.ed_basis_dims(b)[2]
+        x = _cplx(ed_inputs.uniform_pm1(23, 2 * dim))
+        xd = torch.tensor(x, dtype=TDT[dtype], device="cuda")
+        yd = torch.empty_like(xd)
+        ed.ed_hv(b, t, U, xd, yd)
+        got = yd.cpu().numpy().astype(np.complex128)
+    finally:
+        ed.ed_basis_destroy(b)
+    H = ch.hamiltonian_csr_complex(L, bonds, tb if amplitudes else np.ones(len(bonds)), nu, nd, t, U)
+    xr = xd.cpu().numpy().astype(np.complex128)
+    ref = H @ xr
+    bound = 4 * (2 * len(bonds) + 2) * EPS[dtype] * (abs(H) @ np.abs(xr)) + 1e-300
+    assert np.all(np.abs(got - ref) <= bound), float((np.abs(got - ref) / bound).max())
+
+
+LZ_CASE = (11, np.array([[i, (i + 1) % 11] for i in range(11)] + [[0, 5], [2, 9], [3, 7], [1, 8], [4, 10], [6, 0]]), 3, 5)
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c32"])
+def test_alpha_beta_follow_oracle(ed, dtype):
+    L, bonds, nu, nd = LZ_CASE
+    tb = _rand_tb(len(bonds), 11)
+    t, U = 1.0, 3.0
+    H = ch.hamiltonian_csr_complex(L, bonds, tb, nu, nd, t, U)
+    f1 = olz.normalized_start(ed_inputs.start_vector_raw(17, 2 * H.shape[0]))
+    ref = olz.lanczos(ch.real_view_matvec(H), f1, max_steps=16, reorth=False, fixed_steps=True)
+    b = ed.ed_build_basis(L, bonds, nu, nd, t_bond=tb)
+    try:
+        fdev = torch.tensor(_cplx(f1), dtype=TDT[dtype], device="cuda")
+        res = ed.ed_lanczos_solve(b, t, U, ed.make_opts(max_steps=16, tol=0.0, dtype=dtype), f1=fdev,
+                                  raise_not_converged=False)
+    finally:
+        ed.ed_basis_destroy(b)
+    tol = 2e-5 if dtype == "c32" else 1e-11
+    assert np.allclose(res["alpha"], ref.alpha, rtol=tol, atol=tol)
+    assert np.allclose(res["beta"], ref.beta, rtol=tol, atol=tol)
+
+
+@pytest.mark.parametrize("case", HV_CASES[:3])
+def test_ground_state_energy_vs_dense(ed, case):
+    L, bonds, nu, nd = case
+    tb = _rand_tb(len(bonds), 13)
+    H = ch.hamiltonian_csr_complex(L, bonds, tb, nu, nd, 1.0, 4.0)
+    E = np.linalg.eigvalsh(H.toarray())[0]
+    b = ed.ed_build_basis(L, bonds, nu, nd, t_bond=tb)
+    try:
+        res = ed.ed_lanczos_solve(b, 1.0, 4.0, ed.make_opts(max_steps=400, tol=1e-13, seed=5, dtype="c64"))
+    finally:
+        ed.ed_basis_destroy(b)
+    assert abs(res["E0"] - E) <= 1e-10 * max(1.0, abs(E)), (res["E0"], E)
+
+
+@pytest.mark.parametrize("phi", [0.4, 1.3])
+def test_flux_ring_closed_form(ed, phi):
+    L, n = 12, 3
+    e = np.sort(-2.0 * np.cos(2 * np.pi * np.arange(L) / L + phi))
+    b = ed.ed_build_basis(L, ed_inputs.ring_bonds(L), n, n, t_bond=np.full(L, np.exp(1j * phi)))
+    try:
+        res = ed.ed_lanczos_solve(b, 1.0, 0.0, ed.make_opts(max_steps=400, tol=1e-13, seed=3, dtype="c64"))
+    finally:
+        ed.ed_basis_destroy(b)
+    assert abs(res["E0"] - 2 * e[:n].sum()) <= 1e-11 * abs(2 * e[:n].sum())
+
+
+def test_gauge_conjugation_and_real_limit(ed):
+    L, bonds, nu, nd = 12, ed_inputs.torus_bonds(3, 4), 3, 3
+    tb = _rand_tb(len(bonds), 19)
+    theta = np.random.default_rng(20).uniform(-math.pi, math.pi, L)
+    bb = np.asarray(bonds)
+    tg = tb * np.exp(1j * (theta[bb[:, 0]] - theta[bb[:, 1]]))
+    o = ed.make_opts(max_steps=500, tol=1e-13, seed=4, dtype="c64")
+    E = []
+    for amps in (tb, tg, np.conj(tb), np.ones(len(bonds))):
+        b = ed.ed_build_basis(L, bonds, nu, nd, t_bond=amps)
+        try:
+            E.append(ed.ed_lanczos_solve(b, 1.0, 2.0, o)["E0"])
+        finally:
+            ed.ed_basis_destroy(b)
+    assert abs(E[1] - E[0]) <= 1e-10 * abs(E[0]) and abs(E[2] - E[0]) <= 1e-10 * abs(E[0])
+    b = ed.ed_build_basis(L, bonds, nu, nd)
+    try:
+        Er = ed.ed_lanczos_solve(b, 1.0, 2.0, ed.make_opts(max_steps=500, tol=1e-13, seed=4))["E0"]
+    finally:
+        ed.ed_basis_destroy(b)
+    assert abs(E[3] - Er) <= 1e-11 * abs(Er)
+
+
+def test_real_dtype_on_complex_lattice_is_an_argument_error(ed):
+    b = ed.ed_build_basis(6, ed_inputs.ring_bonds(6), 2, 2, t_bond=_rand_tb(6, 1))
+    try:
+        with pytest.raises(ed.EdError) as ei:
+            ed.ed_lanczos_solve(b, 1.0, 1.0, ed.make_opts(dtype="f64"))
+        assert ei.value.status == ed.ED_ERR_ARG
+    finally:
+        ed.ed_basis_destroy(b)
