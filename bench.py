@@ -26,6 +26,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+import numpy as np  # noqa: E402
+
 import ed_inputs  # noqa: E402
 
 METRIC = "Lanczos step time & H·v HBM GB/s (% peak); time-to-E0 at 1e-8 vs plain FP64"
@@ -122,15 +124,21 @@ w = ed_inputs.workload(sys.argv[2]); nsamp = int(sys.argv[3]); reps = int(sys.ar
 L, b, nu, nd, t, U = w["n_sites"], w["bonds"], w["n_up"], w["n_dn"], w["t"], w["U"]
 import math
 dim = math.comb(L, nu) * math.comb(L, nd)
-x = ed_inputs.uniform_pm1(w["seed"], dim)
+tb = w.get("t_bond")
+x = ed_inputs.uniform_pm1(w["seed"], dim) if tb is None else ed_inputs.uniform_pm1(w["seed"], 2 * dim).view(np.complex128)
 rng = np.random.default_rng(0)
 times = []
 for r in range(reps):
     rows = np.sort(rng.choice(dim, size=nsamp, replace=False))
     t0 = time.perf_counter()
-    y = hamiltonian.hv_rows(L, b, nu, nd, t, U, x, rows)
+    if tb is None:
+        y = hamiltonian.hv_rows(L, b, nu, nd, t, U, x, rows)
+    else:
+        from oracle import complex_hopping
+        y = complex_hopping.hv_rows_complex(L, b, tb, nu, nd, t, U, x, rows)
     # the vector operations of Algorithm 1 on the same rows
-    f = x[rows]; q = y - 0.5 * f; a = float(q @ f); q = q - a * f; bn = float(np.sqrt(q @ q))
+    f = x[rows]; q = y - 0.5 * f; a = float(np.vdot(f, q).real); q = q - a * f
+    bn = float(np.sqrt(np.vdot(q, q).real))
     times.append(time.perf_counter() - t0)
 print(json.dumps({"dim": dim, "nsamp": nsamp, "times": times}))
 """
@@ -345,9 +353,9 @@ def bench_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w = ed_inputs.workload(args.workload)
     dtype = args.dtype or w["dtype"]
-    esize = 8 if dtype == "f64" else 4
+    esize = {"f64": 8, "f32": 4, "c32": 8, "c64": 16}[dtype]
     L, bonds, nu, nd, t, U = w["n_sites"], w["bonds"], w["n_up"], w["n_dn"], w["t"], w["U"]
-    basis = ed.ed_build_basis(L, bonds, nu, nd)
+    basis = ed.ed_build_basis(L, bonds, nu, nd, t_bond=w.get("t_bond"))
     du, dd, dim = ed.ed_basis_dims(basis)
     tabs = ed.ed_basis_tables(basis)
     K, W = args.steps, args.warmup
@@ -393,8 +401,12 @@ def bench_ours(args):
     # ---------------------------------------------------------------- end to end (C ABI)
     # start vector from pinned host memory, copied in the timed region; fixed K steps;
     # E0, a_j and b_j read back to the host by the call.
-    f1_host = torch.from_numpy(ed_inputs.start_vector_raw(w["seed"], dim)).to(
-        torch.float64 if dtype == "f64" else torch.float32).pin_memory()
+    if dtype in ("c32", "c64"):
+        f1_host = torch.from_numpy(ed_inputs.start_vector_raw(w["seed"], 2 * dim).view(np.complex128)).to(
+            torch.complex128 if dtype == "c64" else torch.complex64).pin_memory()
+    else:
+        f1_host = torch.from_numpy(ed_inputs.start_vector_raw(w["seed"], dim)).to(
+            torch.float64 if dtype == "f64" else torch.float32).pin_memory()
     f1_dev = torch.empty(dim, dtype=f1_host.dtype, device="cuda")
     eopts = ed.make_opts(max_steps=K, tol=0.0, seed=w["seed"], dtype=dtype, schedule=args.schedule)
 
@@ -426,6 +438,8 @@ def bench_ours(args):
     # ---------------------------------------------------------------- roofline
     peak, peak_kind = _peaks()
     table_bytes = du * (tabs["maxhops_up"] * 4 + 4) + dd * (tabs["maxhops_dn"] * 4 + 4)
+    if w.get("t_bond") is not None:  # amplitude index per hop
+        table_bytes += du * tabs["maxhops_up"] * 4 + dd * tabs["maxhops_dn"] * 4
     hv_bytes = 3 * esize * dim + table_bytes  # read f_j, read f_{j-1}, write w; + tables
     hv_launch_ms = hv_ms / K
     achieved = hv_bytes / (hv_launch_ms * 1e-3) / 1e9
@@ -454,7 +468,7 @@ def bench_ours(args):
                             "state, builds the H.v plan and captures the graph (first_call_s)"},
             "gpu_launches": 3 * K,
             "clocks": clk}
-    if ws == 1 and not args.no_extras:
+    if ws == 1 and not args.no_extras and w.get("t_bond") is None:
         line["time_to_E0"] = time_to_e0_headline(ed, basis, w)
         line["batched"] = batched_study(ed)
         line["learned_start"] = learned_start_study(ed)
@@ -477,7 +491,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="torus4x4_5_5")
-    ap.add_argument("--dtype", default=None, choices=[None, "f64", "f32"])
+    ap.add_argument("--dtype", default=None, choices=[None, "f64", "f32", "c32", "c64"])
     ap.add_argument("--cpu-rows", type=int, default=400000)
     ap.add_argument("--cpu-reps", type=int, default=8)
     ap.add_argument("--ref-rows", type=int, default=100000)

@@ -67,6 +67,34 @@ def uniform_pm1(seed: int, n: int, offset: int = 0) -> np.ndarray:
     return 2.0 * u - 1.0
 
 
+def checkerboard_lattice(Lx: int, Ly: int, phi: float = np.pi / 4, t2: float = 0.3,
+                         t3: float = -0.2):
+    """A checkerboard-type periodic Lx x Ly lattice with complex nearest-neighbour hoppings
+    (the paper's second geometry, Sec. 2.1 Fig. 1, whose amplitudes it does not print; these
+    are synthetic stand-ins): site x + Lx y, sublattice A where x + y is even.
+      * nearest neighbours (+x, +y): relative amplitude exp(+-i phi), the sign of the phase
+        set by the sublattice of the first site and flipped between x and y bonds;
+      * next-nearest (the two diagonals): real +-t2, alternating with the sublattice;
+      * third neighbours (+2x, +2y): real t3 (on a 4-wide axis the two neighbours at +-2
+        coincide; that pair is listed once).
+    Returns (bonds [n_bonds][2], complex amplitudes [n_bonds])."""
+    bonds, amp = [], []
+    def site(x, y):
+        return (x % Lx) + Lx * (y % Ly)
+    for y in range(Ly):
+        for x in range(Lx):
+            s, a = site(x, y), (x + y) % 2 == 0
+            bonds.append((s, site(x + 1, y))); amp.append(np.exp(1j * phi * (1 if a else -1)))
+            bonds.append((s, site(x, y + 1))); amp.append(np.exp(1j * phi * (-1 if a else 1)))
+            bonds.append((s, site(x + 1, y + 1))); amp.append(t2 if a else -t2)
+            bonds.append((s, site(x + 1, y - 1))); amp.append(-t2 if a else t2)
+            if Lx != 4 or x < 2:
+                bonds.append((s, site(x + 2, y))); amp.append(t3)
+            if Ly != 4 or y < 2:
+                bonds.append((s, site(x, y + 2))); amp.append(t3)
+    return np.array(bonds, dtype=np.int32), np.array(amp, dtype=np.complex128)
+
+
 def start_vector_raw(seed: int, dim: int) -> np.ndarray:
     """The un-normalised random start vector (Algorithm 1 requires norm 1; each side
     normalises it itself)."""
@@ -91,6 +119,10 @@ def workload(name: str) -> dict:
     if name == "ring26_13_0":     # L=26 ring, 13 particles of one spin, dim 10,400,600
         return dict(n_sites=26, bonds=ring_bonds(26), n_up=13, n_dn=0, t=1.0, U=4.0,
                     dtype="f64", seed=7)
+    if name == "checker4x4_5_5":  # checkerboard-type 4x4, complex NN hoppings, dim 4368^2
+        bonds, amp = checkerboard_lattice(4, 4)
+        return dict(n_sites=16, bonds=bonds, t_bond=amp, n_up=5, n_dn=5, t=1.0, U=4.0,
+                    dtype="c64", seed=8)
     if name == "ring18_9_9":      # L=18 ring, half filling, dim 48620^2 = 2.36e9, FP32
         return dict(n_sites=18, bonds=ring_bonds(18), n_up=9, n_dn=9, t=1.0, U=4.0,
                     dtype="f32", seed=6)

@@ -79,3 +79,14 @@ def test_real_view_lanczos_reaches_dense_ground_state():
     f1 = olz.normalized_start(ed_inputs.start_vector_raw(9, 2 * H.shape[0]))
     res = olz.lanczos(ch.real_view_matvec(H), f1, max_steps=300, tol=1e-14)
     assert abs(res.E0 - E) <= 1e-10 * abs(E)
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_matrix_free_rows_match_the_matrix(case):
+    L, bonds, nu, nd = case
+    tb = _rand_tb(len(bonds), 6)
+    H = ch.hamiltonian_csr_complex(L, bonds, tb, nu, nd, 0.9, 1.7)
+    r = np.random.default_rng(7)
+    x = r.normal(size=H.shape[0]) + 1j * r.normal(size=H.shape[0])
+    rows = np.arange(H.shape[0])
+    assert np.allclose(ch.hv_rows_complex(L, bonds, tb, nu, nd, 0.9, 1.7, x, rows), H @ x, atol=1e-13)
