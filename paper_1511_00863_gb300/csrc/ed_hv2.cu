@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "ed_hv2_kernel.cuh"
+#include "ed_hv2c_kernel.cuh"
 
 namespace ed {
 
@@ -52,11 +53,21 @@ static int optin_smem() {
   X(13, long long, 2, 2, 256, 3)   \
   X(14, float, 2, 4, 256, 4)
 
+// Complex FP32 variants (ED_C32; hv2c_kernel): id, R, V, T, MB.
+#define HV2C_KINDS(X)        \
+  X(20, 2, 2, 256, 4)        \
+  X(21, 1, 2, 256, 6)        \
+  X(22, 1, 2, 512, 3)        \
+  X(23, 2, 2, 512, 2)
+
 struct KindInfo {
   size_t smem;
   int R, V, G;
-  bool fx;
+  int mode;  // kHv2F32, kHv2Fx, kHv2C32
 };
+
+// Entries of the signed amplitude table of the complex kernel.
+static int hv2c_namp(const ed_basis* b) { return b->has_tau() ? 4 * b->n_bonds : 2; }
 
 static bool kind_info(int kind, const ed_basis* b, int ld, KindInfo* ki) {
   const int MH = b->up.maxhops > 0 ? b->up.maxhops : 1;
@@ -67,20 +78,32 @@ static bool kind_info(int kind, const ed_basis* b, int ld, KindInfo* ki) {
       ki->R = R_;                                                                         \
       ki->V = V_;                                                                         \
       ki->G = hv2_group<E, R_>();                                                         \
-      ki->fx = sizeof(E) == 8;                                                            \
+      ki->mode = sizeof(E) == 8 ? kHv2Fx : kHv2F32;                                       \
       return true;
     HV2_KINDS(HV2_INFO)
 #undef HV2_INFO
+#define HV2C_INFO(K, R_, V_, T, MB)                                                         \
+    case K:                                                                                 \
+      ki->smem = (size_t)(ld + 1) * 8 * R_ + (size_t)((hv2c_namp(b) + 1) & ~1) * 8 +         \
+                 (size_t)R_ * MH * 12;                                                      \
+      ki->R = R_;                                                                           \
+      ki->V = V_;                                                                           \
+      ki->G = hv2_group<float2, R_>();                                                      \
+      ki->mode = kHv2C32;                                                                   \
+      return true;
+    HV2C_KINDS(HV2C_INFO)
+#undef HV2C_INFO
     default:
       return false;
   }
 }
 
 // Whether variant `kind` runs this basis in this precision within the shared-memory limit.
-static bool kind_usable(int kind, const ed_basis* b, bool fixed_point, int ld, KindInfo* ki) {
+static bool kind_usable(int kind, const ed_basis* b, int mode, int ld, KindInfo* ki) {
   if (kind <= 0 || !kind_info(kind, b, ld, ki)) return false;
-  if (ki->fx != fixed_point || ki->smem > (size_t)optin_smem() || b->up.dim < ki->R) return false;
-  return ld <= 0xFFFF;  // the zero slot (slot ld) must fit the 16-bit table entries
+  if (ki->mode != mode || ki->smem > (size_t)optin_smem() || b->up.dim < ki->R) return false;
+  if (mode == kHv2C32 && hv2c_namp(b) > 0x10000) return false;  // 16-bit amplitude index
+  return ld <= 0xFFFF;  // the zero slot (slot ld) must fit the 16-bit slot field
 }
 
 void hv2_free(Hv2Plan* p) {
@@ -194,7 +217,9 @@ static std::vector<uint8_t> choose_slots(const std::vector<int32_t>& tcol, const
 // shared-memory slots. Variants with the same (V, G) share them; the basis caches them.
 struct DownTables {
   int V = 0, G = 0, ld = 0;
+  bool cplx = false;              // complex kernel: 32-bit entries slot | amplitude index << 16
   std::vector<uint16_t> tab;
+  std::vector<uint32_t> tab32;
   std::vector<uchar2> kpn;
   std::vector<uint8_t> lo;
   std::vector<uint32_t> pad;
@@ -208,10 +233,15 @@ static ed_status compute_down_tables(const ed_basis* b, int ld, const KindInfo& 
                                      DownTables& out) {
   const int64_t n = b->dn.dim;
   const int mh = b->dn.maxhops;
-  std::vector<int32_t> hop((size_t)mh * n);
+  const bool cplx = ki.mode == kHv2C32;
+  std::vector<int32_t> hop((size_t)mh * n), hopa;
   std::vector<uint32_t> bits((size_t)n);
   if (mh > 0)
     ED_TRY_CUDA(cudaMemcpyAsync(hop.data(), b->dn.hop, hop.size() * 4, cudaMemcpyDeviceToHost, s));
+  if (cplx && mh > 0 && b->dn.hopa) {
+    hopa.resize(hop.size());
+    ED_TRY_CUDA(cudaMemcpyAsync(hopa.data(), b->dn.hopa, hopa.size() * 4, cudaMemcpyDeviceToHost, s));
+  }
   ED_TRY_CUDA(cudaMemcpyAsync(bits.data(), b->dn.bits, bits.size() * 4, cudaMemcpyDeviceToHost, s));
   ED_TRY_CUDA(cudaStreamSynchronize(s));
   std::vector<int> np((size_t)n, 0), nn((size_t)n, 0);  // hops with sign +1 / -1
@@ -233,8 +263,12 @@ static ed_status compute_down_tables(const ed_basis* b, int ld, const KindInfo& 
   const int nchunks = (ld + chunk - 1) / chunk;
   std::vector<int> kp((size_t)nchunks, 0), kn((size_t)nchunks, 0), kcount((size_t)nchunks, 0);
   for (int64_t q = 0; q < n; ++q) {
-    kp[q / chunk] = std::max(kp[q / chunk], np[perm[q]]);
-    kn[q / chunk] = std::max(kn[q / chunk], nn[perm[q]]);
+    if (cplx) {  // one loop over all hops: the sign is in the amplitude
+      kp[q / chunk] = std::max(kp[q / chunk], np[perm[q]] + nn[perm[q]]);
+    } else {
+      kp[q / chunk] = std::max(kp[q / chunk], np[perm[q]]);
+      kn[q / chunk] = std::max(kn[q / chunk], nn[perm[q]]);
+    }
   }
   int rows = 1;
   for (int c = 0; c < nchunks; ++c) {
@@ -246,6 +280,7 @@ static ed_status compute_down_tables(const ed_basis* b, int ld, const KindInfo& 
     rows = std::max(rows, kcount[c]);
   }
   std::vector<int32_t> tcol((size_t)rows * ld, -1);  // target column, -1 = zero slot
+  std::vector<uint32_t> tamp(cplx ? tcol.size() : 0, 0u);  // signed amplitude index
   for (int64_t q = 0; q < n; ++q) {
     const int c = (int)(q / chunk);
     int ip = 0, in = kp[c];
@@ -253,17 +288,30 @@ static ed_status compute_down_tables(const ed_basis* b, int ld, const KindInfo& 
       const uint32_t h = (uint32_t)hop[(size_t)k * n + perm[q]];
       const uint32_t tg = h & kTargetMask;
       if ((int64_t)tg >= n) continue;
-      const int row = (h & kSignBit) ? in++ : ip++;
+      const int row = cplx ? ip++ : (h & kSignBit) ? in++ : ip++;
       tcol[(size_t)row * ld + q] = pos[tg];
+      if (cplx) {
+        const uint32_t num = hopa.empty() ? 0u : (uint32_t)hopa[(size_t)k * n + perm[q]];
+        tamp[(size_t)row * ld + q] = 2u * num + (h >> 31);
+      }
     }
   }
   out.lo = choose_slots(tcol, kcount, ld, ki.V, ki.G);
   const std::vector<uint8_t>& lo = out.lo;
-  std::vector<uint16_t>& tab = out.tab;
-  tab.assign((size_t)rows * ld, 0);
-  for (size_t i = 0; i < tcol.size(); ++i) {
-    const int32_t t = tcol[i];
-    tab[i] = (uint16_t)(t >= 0 ? (t & ~(ki.G - 1)) | lo[t] : ld);
+  out.cplx = cplx;
+  if (cplx) {
+    out.tab32.assign((size_t)rows * ld, 0u);
+    for (size_t i = 0; i < tcol.size(); ++i) {
+      const int32_t t = tcol[i];
+      out.tab32[i] = (t >= 0 ? (uint32_t)((t & ~(ki.G - 1)) | lo[t]) : (uint32_t)ld) | (tamp[i] << 16);
+    }
+  } else {
+    std::vector<uint16_t>& tab = out.tab;
+    tab.assign((size_t)rows * ld, 0);
+    for (size_t i = 0; i < tcol.size(); ++i) {
+      const int32_t t = tcol[i];
+      tab[i] = (uint16_t)(t >= 0 ? (t & ~(ki.G - 1)) | lo[t] : ld);
+    }
   }
   std::vector<uchar2>& kpnv = out.kpn;
   kpnv.resize((size_t)nchunks);
@@ -279,7 +327,9 @@ static ed_status compute_down_tables(const ed_basis* b, int ld, const KindInfo& 
 
 static ed_status upload_down_tables(const DownTables& t, int64_t n, cudaStream_t s, Hv2Plan* p) {
   const int ld = t.ld;
-  if (cudaMalloc(&p->dtab, t.tab.size() * 2) != cudaSuccess ||
+  const size_t tbytes = t.cplx ? t.tab32.size() * 4 : t.tab.size() * 2;
+  const void* tdata = t.cplx ? (const void*)t.tab32.data() : (const void*)t.tab.data();
+  if (cudaMalloc(&p->dtab, tbytes) != cudaSuccess ||
       cudaMalloc((void**)&p->kpn, t.kpn.size() * sizeof(uchar2)) != cudaSuccess ||
       cudaMalloc((void**)&p->slot_lo, (size_t)ld) != cudaSuccess ||
       cudaMalloc((void**)&p->dn_pad, (size_t)ld * 4) != cudaSuccess ||
@@ -287,7 +337,7 @@ static ed_status upload_down_tables(const DownTables& t, int64_t n, cudaStream_t
     set_error("H.v tables: out of device memory");
     return ED_ERR_OOM;
   }
-  ED_TRY_CUDA(cudaMemcpyAsync(p->dtab, t.tab.data(), t.tab.size() * 2, cudaMemcpyHostToDevice, s));
+  ED_TRY_CUDA(cudaMemcpyAsync(p->dtab, tdata, tbytes, cudaMemcpyHostToDevice, s));
   ED_TRY_CUDA(cudaMemcpyAsync(p->kpn, t.kpn.data(), t.kpn.size() * sizeof(uchar2),
                               cudaMemcpyHostToDevice, s));
   ED_TRY_CUDA(cudaMemcpyAsync(p->slot_lo, t.lo.data(), t.lo.size(), cudaMemcpyHostToDevice, s));
@@ -305,7 +355,7 @@ static ed_status down_tables(const ed_basis* b, int ld, const KindInfo& ki, cuda
   auto* cache = static_cast<std::deque<DownTables>*>(b->hv2_tables);
   if (!cache) b->hv2_tables = cache = new std::deque<DownTables>();
   for (const DownTables& t : *cache)
-    if (t.V == ki.V && t.G == ki.G && t.ld == ld) {
+    if (t.V == ki.V && t.G == ki.G && t.ld == ld && t.cplx == (ki.mode == kHv2C32)) {
       *out = &t;
       return ED_OK;
     }
@@ -324,20 +374,20 @@ void hv2_tables_free(const ed_basis* b) {
 }
 
 // Choose the kernel variant for this basis and element type, build the per-plan tables.
-ed_status hv2_build(const ed_basis* b, bool fixed_point, int ld, int schedule, cudaStream_t s,
+ed_status hv2_build(const ed_basis* b, int mode, int ld, int schedule, cudaStream_t s,
                     Hv2Plan** out) {
   *out = nullptr;
   // down-loop lengths are stored in 8 bits
   if (b->dn.maxhops > 255) return ED_OK;  // caller falls back to the general kernels
-  static const int pref_f32[] = {1, 4, 2, 6}, pref_fx[] = {8, 9, 12, 11};
-  const int* pref = fixed_point ? pref_fx : pref_f32;
+  static const int pref_f32[] = {1, 4, 2, 6}, pref_fx[] = {8, 9, 12, 11}, pref_c32[] = {20, 21, 22, 23};
+  const int* pref = mode == kHv2Fx ? pref_fx : mode == kHv2C32 ? pref_c32 : pref_f32;
   const int npref = 4;
   int kind = 0;
   KindInfo ki{};
   for (int i = -1; i < npref && !kind; ++i) {
     const int k = i < 0 ? schedule : pref[i];
     if (i >= 0 && b->up.dim < kMinRowsStaged) break;  // few rows: the general kernels
-    if (kind_usable(k, b, fixed_point, ld, &ki)) kind = k;
+    if (kind_usable(k, b, mode, ld, &ki)) kind = k;
   }
   if (!kind) return ED_OK;  // caller falls back to the general kernels
   Hv2Plan* p = new Hv2Plan();
@@ -359,6 +409,12 @@ ed_status hv2_build(const ed_basis* b, bool fixed_point, int ld, int schedule, c
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ki.smem);
   HV2_KINDS(HV2_ATTR)
 #undef HV2_ATTR
+#define HV2C_ATTR(K, R_, V, T, MB)                                                         \
+  if (kind == K)                                                                          \
+    e = cudaFuncSetAttribute(hv2c_kernel<R_, V, T, MB>,                                   \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ki.smem);
+  HV2C_KINDS(HV2C_ATTR)
+#undef HV2C_ATTR
   if (e != cudaSuccess) {
     hv2_free(p);
     set_error("H.v tables: %s", cudaGetErrorString(e));
@@ -372,13 +428,14 @@ const int32_t* hv2_colpos(const Hv2Plan* p) { return p ? p->colpos : nullptr; }
 
 int hv2_grid(const Hv2Plan* p) { return p ? p->grid : 0; }
 
-ed_status hv2_autotune(const ed_basis* b, bool fixed_point, int ld, void* x, void* y,
+ed_status hv2_autotune(const ed_basis* b, int mode, int ld, void* x, void* y,
                        const LzScalars* S, void* partial, cudaStream_t s, int* kind) {
   *kind = 0;
   if (b->up.dim < kMinRowsStaged) return ED_OK;  // few rows: the general kernels
-  static const int cand_f32[] = {1, 2, 3, 4, 5, 6, 7, 14}, cand_fx[] = {8, 9, 10, 11, 12, 13};
-  const int* cand = fixed_point ? cand_fx : cand_f32;
-  const int nc = fixed_point ? 6 : 8;
+  static const int cand_f32[] = {1, 2, 3, 4, 5, 6, 7, 14}, cand_fx[] = {8, 9, 10, 11, 12, 13},
+                   cand_c32[] = {20, 21, 22, 23};
+  const int* cand = mode == kHv2Fx ? cand_fx : mode == kHv2C32 ? cand_c32 : cand_f32;
+  const int nc = mode == kHv2Fx ? 6 : mode == kHv2C32 ? 4 : 8;
   constexpr int kReps = 5;
   cudaEvent_t ev[kReps + 1];
   for (auto& e : ev) ED_TRY_CUDA(cudaEventCreate(&e));
@@ -386,9 +443,9 @@ ed_status hv2_autotune(const ed_basis* b, bool fixed_point, int ld, void* x, voi
   ed_status r = ED_OK;
   for (int i = 0; i < nc && r == ED_OK; ++i) {
     KindInfo ki;
-    if (!kind_usable(cand[i], b, fixed_point, ld, &ki)) continue;
+    if (!kind_usable(cand[i], b, mode, ld, &ki)) continue;
     Hv2Plan* p = nullptr;
-    if ((r = hv2_build(b, fixed_point, ld, cand[i], s, &p)) != ED_OK) break;
+    if ((r = hv2_build(b, mode, ld, cand[i], s, &p)) != ED_OK) break;
     if (!p || p->kind != cand[i]) {
       hv2_free(p);
       continue;
@@ -441,6 +498,30 @@ ed_status hv2_launch(const Hv2Plan* p, const ed_basis* b, double t, double U, co
                                                              partial);
   HV2_KINDS(HV2_LAUNCH)
 #undef HV2_LAUNCH
+  if (p->kind >= 20) {
+    Hv2cArgs c;
+    c.up_bits = b->up.bits;
+    c.dn_bits = p->dn_pad;
+    c.dtab = (const uint32_t*)p->dtab;
+    c.kpn = p->kpn;
+    c.slot_lo = p->slot_lo;
+    c.hop_up = b->up.hop;
+    c.hopa_up = b->up.hopa;
+    c.order = b->up_order;
+    c.tau = b->tau;
+    c.dim_up = b->up.dim;
+    c.ld = p->ld;
+    c.maxhops_up = b->up.maxhops;
+    c.namp = hv2c_namp(b);
+    c.t = (float)t;
+    c.U = (float)U;
+#define HV2C_LAUNCH(K, R_, V, T, MB)                                                          \
+    if (p->kind == K)                                                                          \
+      hv2c_kernel<R_, V, T, MB><<<p->grid, T, p->smem, s>>>(c, (const float2*)x, (float2*)y, S, \
+                                                             cur, (double*)partial);
+    HV2C_KINDS(HV2C_LAUNCH)
+#undef HV2C_LAUNCH
+  }
   ED_TRY_CUDA(cudaGetLastError());
   return ED_OK;
 }

@@ -65,7 +65,7 @@ struct ed_basis {
   // Workspaces of ed_lanczos_solve kept between calls (ed_lanczos.cu); freed with the basis.
   mutable void* solve_cache = nullptr;
   // Fused H.v variant chosen by timing for this basis, per dtype (0 = not tuned yet).
-  mutable int tuned_kind[3] = {0, 0, 0};
+  mutable int tuned_kind[5] = {0, 0, 0, 0, 0};
   // Host-built down tables of the fused H.v per (V, G) geometry (ed_hv2.cu); freed with the
   // basis.
   mutable void* hv2_tables = nullptr;
@@ -185,7 +185,9 @@ ed_status fx_psi_finish(const ed_basis* b, const long long* P, long long* part, 
 // NULL when no variant fits in shared memory (the general kernels are used then).
 struct Hv2Plan;
 // schedule: -1 = default variant, else a variant id (see ed_hv2.cu) if it fits.
-ed_status hv2_build(const ed_basis* b, bool fixed_point, int ld, int schedule, cudaStream_t s,
+// mode: kHv2F32 (FP32 vectors), kHv2Fx (int64 fixed point), kHv2C32 (complex FP32).
+enum { kHv2F32 = 0, kHv2Fx = 1, kHv2C32 = 2 };
+ed_status hv2_build(const ed_basis* b, int mode, int ld, int schedule, cudaStream_t s,
                     Hv2Plan** out);
 void hv2_free(Hv2Plan* p);
 int hv2_grid(const Hv2Plan* p);
@@ -194,7 +196,7 @@ const int32_t* hv2_colpos(const Hv2Plan* p);
 int hv2_kind(const Hv2Plan* p);
 // Time every fused H.v variant that fits on x (f_j) and y (f_{j-1} / w) with scalars S
 // (zeroed: a neutral step) and return the fastest variant id (0 if none fits).
-ed_status hv2_autotune(const ed_basis* b, bool fixed_point, int ld, void* x, void* y,
+ed_status hv2_autotune(const ed_basis* b, int mode, int ld, void* x, void* y,
                        const LzScalars* S, void* partial, cudaStream_t s, int* kind);
 ed_status hv2_launch(const Hv2Plan* p, const ed_basis* b, double t, double U, const void* x,
                      void* y, const LzScalars* S, int cur, void* partial, cudaStream_t s);

@@ -49,18 +49,26 @@ start_norm_kernel(uint64_t seed, int64_t n, double* __restrict__ partial) {
   if (threadIdx.x == 0) partial[blockIdx.x] = v;
 }
 
-// out[(i / cols) * ld + colpos[i % cols]] = raw_i / ||raw|| rounded to T (colpos NULL:
-// the identity).
+// Scalar i of the vector (row r = i / cols, column c = i % cols) goes to out[r ld + p] with
+// p = cx colpos[c / cx] + c % cx (cx = 2 for the (re, im) scalars of a complex element) or
+// p = c when colpos is NULL.
+__device__ __forceinline__ int64_t col_of(const int32_t* colpos, int64_t c, int cx) {
+  if (!colpos) return c;
+  const int64_t e = c / cx;
+  return cx * (int64_t)colpos[e] + (c - e * cx);
+}
+
+// out[row, col_of(c)] = raw_i / ||raw|| rounded to T.
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
 start_write_kernel(uint64_t seed, int64_t n, int64_t cols, int64_t ld, const int32_t* __restrict__ colpos,
-                   const double* __restrict__ partial, int nparts, T* __restrict__ out) {
+                   int cx, const double* __restrict__ partial, int nparts, T* __restrict__ out) {
   __shared__ double red[33];
   const double inv = 1.0 / sqrt(block_sum_array(partial, nparts, red));
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = i / cols, c = i - r * cols;
-    out[r * ld + (colpos ? colpos[c] : c)] = (T)(start_element(seed, (uint64_t)i) * inv);
+    out[r * ld + col_of(colpos, c, cx)] = (T)(start_element(seed, (uint64_t)i) * inv);
   }
 }
 
@@ -68,14 +76,15 @@ start_write_kernel(uint64_t seed, int64_t n, int64_t cols, int64_t ld, const int
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
 copy_in_kernel(const T* __restrict__ src, int64_t n, int64_t cols, int64_t ld,
-               const int32_t* __restrict__ colpos, T* __restrict__ dst, double* __restrict__ partial) {
+               const int32_t* __restrict__ colpos, int cx, T* __restrict__ dst,
+               double* __restrict__ partial) {
   __shared__ double red[33];
   DotAcc<T> acc;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = i / cols, c = i - r * cols;
     const T v = src[i];
-    dst[r * ld + (colpos ? colpos[c] : c)] = v;
+    dst[r * ld + col_of(colpos, c, cx)] = v;
     acc.add(v, v);
   }
   const double v = block_sum(acc.get(), red);
@@ -291,10 +300,10 @@ extern "C" ed_status ed_start_vector(int64_t dim, uint64_t seed, ed_dtype dtype,
   ED_TRY_CUDA(cudaMallocAsync((void**)&part, g * sizeof(double), s));
   start_norm_kernel<<<g, kRedThreads, 0, s>>>(seed, dim, part);
   if (dtype != ED_F32)
-    start_write_kernel<double><<<g, kRedThreads, 0, s>>>(seed, dim, dim, dim, nullptr, part, g,
+    start_write_kernel<double><<<g, kRedThreads, 0, s>>>(seed, dim, dim, dim, nullptr, 1, part, g,
                                                          (double*)out);
   else
-    start_write_kernel<float><<<g, kRedThreads, 0, s>>>(seed, dim, dim, dim, nullptr, part, g,
+    start_write_kernel<float><<<g, kRedThreads, 0, s>>>(seed, dim, dim, dim, nullptr, 1, part, g,
                                                         (float*)out);
   cudaError_t e = cudaGetLastError();
   cudaFreeAsync(part, s);
@@ -354,10 +363,10 @@ extern "C" ed_status ed_start_vector_noalloc(int64_t dim, uint64_t seed, ed_dtyp
   cudaStream_t s = (cudaStream_t)stream;
   start_norm_kernel<<<g, kRedThreads, 0, s>>>(seed, dim, part);
   if (dtype != ED_F32)
-    start_write_kernel<double><<<g, kRedThreads, 0, s>>>(seed, dim, dim, dim, nullptr, part, g,
+    start_write_kernel<double><<<g, kRedThreads, 0, s>>>(seed, dim, dim, dim, nullptr, 1, part, g,
                                                          (double*)out);
   else
-    start_write_kernel<float><<<g, kRedThreads, 0, s>>>(seed, dim, dim, dim, nullptr, part, g,
+    start_write_kernel<float><<<g, kRedThreads, 0, s>>>(seed, dim, dim, dim, nullptr, 1, part, g,
                                                         (float*)out);
   ED_TRY_CUDA(cudaGetLastError());
   return ED_OK;
@@ -426,7 +435,8 @@ static ed_status lz_alloc(const ed_basis* b, const ed_opts* o, cudaStream_t s, e
     set_error("Lanczos scalars: out of device memory");
     return fail(ED_ERR_OOM);
   }
-  if (o->dtype == ED_F32 || o->dtype == ED_F64) {
+  if (o->dtype == ED_F32 || o->dtype == ED_F64 || o->dtype == ED_C32) {
+    const int mode = st->fx ? kHv2Fx : o->dtype == ED_C32 ? kHv2C32 : kHv2F32;
     int sched = o->schedule;
     if (sched < 0) {
       // autotune once per basis and dtype: time every variant on this run's zeroed buffers
@@ -436,13 +446,13 @@ static ed_status lz_alloc(const ed_basis* b, const ed_opts* o, cudaStream_t s, e
         ED_TRY_CUDA(cudaMemsetAsync(st->S, 0, sizeof(LzScalars), s));
         for (int i = 0; i < 2; ++i) ED_TRY_CUDA(cudaMemsetAsync(st->B[i], 0, st->n * st->esize, s));
         int k = 0;
-        ed_status tr = hv2_autotune(b, st->fx, (int)st->ld, st->B[0], st->B[1], st->S, st->pa, s, &k);
+        ed_status tr = hv2_autotune(b, mode, (int)st->ld, st->B[0], st->B[1], st->S, st->pa, s, &k);
         if (tr != ED_OK) return fail(tr);
         tuned = k > 0 ? k : -1;
       }
       sched = tuned > 0 ? tuned : -1;
     }
-    ed_status pr = hv2_build(b, st->fx, (int)st->ld, sched, s, &st->plan);
+    ed_status pr = hv2_build(b, mode, (int)st->ld, sched, s, &st->plan);
     if (pr != ED_OK) return fail(pr);
   }
   *out = st;
@@ -488,19 +498,19 @@ static ed_status lz_reset(ed_lanczos* st, const ed_opts* o, const void* f1, int 
   if (f1 == nullptr) {
     start_norm_kernel<<<g, kRedThreads, 0, s>>>(o->seed, dim, st->pb);
     if (dbl)
-      start_write_kernel<double><<<g, kRedThreads, 0, s>>>(o->seed, dim, cols, lds, colpos,
+      start_write_kernel<double><<<g, kRedThreads, 0, s>>>(o->seed, dim, cols, lds, colpos, cx,
                                                            st->pb, g, (double*)st->B[0]);
     else
-      start_write_kernel<float><<<g, kRedThreads, 0, s>>>(o->seed, dim, cols, lds, colpos,
+      start_write_kernel<float><<<g, kRedThreads, 0, s>>>(o->seed, dim, cols, lds, colpos, cx,
                                                           st->pb, g, (float*)st->B[0]);
     init_scalars_kernel<<<1, 32, 0, s>>>(st->S, st->pb, g, 0);
   } else {
     if (dbl)
       copy_in_kernel<double><<<g, kRedThreads, 0, s>>>((const double*)f1, dim, cols, lds,
-                                                       colpos, (double*)st->B[0], st->pb);
+                                                       colpos, cx, (double*)st->B[0], st->pb);
     else
       copy_in_kernel<float><<<g, kRedThreads, 0, s>>>((const float*)f1, dim, cols, lds,
-                                                      colpos, (float*)st->B[0], st->pb);
+                                                      colpos, cx, (float*)st->B[0], st->pb);
     init_scalars_kernel<<<1, kRedThreads, 0, s>>>(st->S, st->pb, g, 1);
   }
   const cudaError_t e = cudaGetLastError();

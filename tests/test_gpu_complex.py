@@ -148,3 +148,49 @@ def test_real_dtype_on_complex_lattice_is_an_argument_error(ed):
         assert ei.value.status == ed.ED_ERR_ARG
     finally:
         ed.ed_basis_destroy(b)
+
+
+@pytest.mark.parametrize("variant", [20, 21, 22, 23])
+def test_every_complex_variant_follows_oracle(ed, variant):
+    """The fused complex FP32 H.v variants (schedule ids 20-23) on a lattice whose down rows
+    span several warp chunks with a ragged tail: a_j, b_{j+1} follow the oracle."""
+    L, bonds, nu, nd = LZ_CASE
+    tb = _rand_tb(len(bonds), 31)
+    t, U = 1.0, 2.0
+    H = ch.hamiltonian_csr_complex(L, bonds, tb, nu, nd, t, U)
+    f1 = olz.normalized_start(ed_inputs.start_vector_raw(37, 2 * H.shape[0]))
+    ref = olz.lanczos(ch.real_view_matvec(H), f1, max_steps=16, reorth=False, fixed_steps=True)
+    b = ed.ed_build_basis(L, bonds, nu, nd, t_bond=tb)
+    try:
+        opts = ed.make_opts(max_steps=16, tol=0.0, dtype="c32", schedule=variant)
+        st = ed.ed_lanczos_init(b, opts)
+        try:
+            assert ed.ed_lanczos_schedule(st) == variant
+        finally:
+            ed.ed_lanczos_destroy(st)
+        fdev = torch.tensor(_cplx(f1), dtype=torch.complex64, device="cuda")
+        res = ed.ed_lanczos_solve(b, t, U, opts, f1=fdev, raise_not_converged=False)
+    finally:
+        ed.ed_basis_destroy(b)
+    assert np.allclose(res["alpha"], ref.alpha, rtol=2e-5, atol=2e-5)
+    assert np.allclose(res["beta"], ref.beta, rtol=2e-5, atol=2e-5)
+
+
+def test_checkerboard_c32_matches_c64(ed):
+    """The checkerboard-type 4x4 workload (dim 19,079,424): the fused complex FP32 path and
+    the FP64 complex path reach the same ground-state energy within FP32 accuracy."""
+    w = ed_inputs.workload("checker4x4_5_5")
+    b = ed.ed_build_basis(w["n_sites"], w["bonds"], w["n_up"], w["n_dn"], t_bond=w["t_bond"])
+    try:
+        o32 = ed.make_opts(max_steps=300, tol=1e-7, seed=w["seed"], dtype="c32")
+        st = ed.ed_lanczos_init(b, o32)
+        try:
+            assert ed.ed_lanczos_schedule(st) >= 20
+        finally:
+            ed.ed_lanczos_destroy(st)
+        e32 = ed.ed_lanczos_solve(b, w["t"], w["U"], o32, raise_not_converged=False)["E0"]
+        e64 = ed.ed_lanczos_solve(b, w["t"], w["U"], ed.make_opts(max_steps=300, tol=1e-11, seed=w["seed"],
+                                                                  dtype="c64"))["E0"]
+    finally:
+        ed.ed_basis_destroy(b)
+    assert abs(e32 - e64) <= 2e-5 * abs(e64), (e32, e64)
