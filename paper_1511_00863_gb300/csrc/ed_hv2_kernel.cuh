@@ -15,15 +15,17 @@
 //  * The R rows are staged once into shared memory, interleaved so that one vector load
 //    (R elements: 8 bytes for 2 x FP32, 16 bytes for 2 x int64) serves every row at once.
 //    Column p goes to slot (p & ~(G-1)) | lo[p], lo a permutation inside each aligned group
-//    of G = 128 / (R sizeof(E)) columns (G slots span all 32 banks), chosen on the host so
-//    that the gathers of one request fall in distinct bank groups as far as possible; the
-//    staging and epilogue accesses of a warp stay conflict-free.
+//    of G = 128 / (R sizeof(E)) columns (G slots span all 32 banks, so slot mod G is the
+//    bank group); the staging and epilogue accesses of a warp stay conflict-free. Slots
+//    ld .. ld + G - 1 hold zeros, one per bank group.
 //  * Down part: a per-plan table gives, for hop k of column p, the slot of the target
 //    (16 bits); padding points at a zero slot. Within a chunk of 32 V columns (one warp) the
 //    hops with fermion sign +1 come first and those with -1 after, each group padded to the
 //    chunk's largest count, so the sign costs nothing per element; the columns are ordered
-//    by (hop count, positive-hop count) to keep that padding small. Consecutive threads
-//    read consecutive table entries (coalesced).
+//    by (hop count, positive-hop count) to keep that padding small. The host chooses lo and
+//    the order of each column's hops within its sign group (and the zero slot of each
+//    padding entry) so that the G lanes of one shared-memory phase hit distinct bank groups
+//    in as many steps as it can. Consecutive threads read consecutive table entries.
 //  * Up part: each row's hop list is sorted by sign into shared memory once per CTA; the
 //    threads then stream the neighbour rows with V-wide coalesced loads (L2-resident reuse).
 //  * Diagonal: U popc(up[u] & dn[d]) x on the integer pipe.
@@ -107,7 +109,7 @@ hv2_kernel(Hv2Args a, const E* __restrict__ x, E* __restrict__ y, const LzScalar
   const int MH = a.maxhops_up > 0 ? a.maxhops_up : 1;
   Pack<E, R>* xs = reinterpret_cast<Pack<E, R>*>(smem);
   int64_t* upoff = reinterpret_cast<int64_t*>(
-      smem + ((size_t)(ld + 1) * sizeof(Pack<E, R>) + 15) / 16 * 16);
+      smem + ((size_t)(ld + G) * sizeof(Pack<E, R>) + 15) / 16 * 16);
   uint32_t* upraw = reinterpret_cast<uint32_t*>(upoff + R * MH);
   const int64_t g0 = (int64_t)blockIdx.x * R;
   int64_t urow[R];
@@ -117,15 +119,16 @@ hv2_kernel(Hv2Args a, const E* __restrict__ x, E* __restrict__ y, const LzScalar
     urow[r] = g < a.dim_up ? (a.order ? (int64_t)a.order[g] : g) : a.dim_up;  // dim_up = none
   }
 
-  // ---- stage the R rows (one d per thread: R coalesced loads, one vector store)
-  for (int d = threadIdx.x; d <= ld; d += T) {
+  // ---- stage the R rows (one d per thread: R coalesced loads, one vector store); slots
+  // ld .. ld + G - 1 are zero, one in each bank group
+  for (int d = threadIdx.x; d < ld + G; d += T) {
     Pack<E, R> p;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int64_t u = urow[r];
       p.v[r] = (d < ld && u < a.dim_up) ? x[u * ld + d] : E(0);
     }
-    xs[d < ld ? (d & ~(G - 1)) | a.slot_lo[d] : ld] = p;
+    xs[d < ld ? (d & ~(G - 1)) | a.slot_lo[d] : d] = p;
   }
   // ---- up-hop lists: raw entries, then per row positives first, negatives after
   for (int i = threadIdx.x; i < R * a.maxhops_up; i += T) {
@@ -190,7 +193,7 @@ hv2_kernel(Hv2Args a, const E* __restrict__ x, E* __restrict__ y, const LzScalar
       for (int v = 0; v < V; ++v) acc[r][v] = E(0);
     // ---- down part: gathers inside the staged rows. The chunk's table rows hold its
     // positive hops first (kpn.x rows), then its negative ones (kpn.y rows); padding points
-    // at the zero slot.
+    // at a zero slot.
     const uchar2 kpn = a.kpn[d0 / (32 * V)];
     const uint16_t* tp = a.dtab + d0;
     const int kend = kpn.x + kpn.y;

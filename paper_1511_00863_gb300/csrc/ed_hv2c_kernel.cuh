@@ -64,7 +64,7 @@ hv2c_kernel(Hv2cArgs a, const float2* __restrict__ x, float2* __restrict__ y,
   const int ld = a.ld;
   const int MH = a.maxhops_up > 0 ? a.maxhops_up : 1;
   Pack<float2, R>* xs = reinterpret_cast<Pack<float2, R>*>(smem);
-  float2* amp = reinterpret_cast<float2*>(xs + (ld + 1));
+  float2* amp = reinterpret_cast<float2*>(xs + (ld + G));
   int64_t* upoff = reinterpret_cast<int64_t*>(amp + ((a.namp + 1) & ~1));
   int32_t* upamp = reinterpret_cast<int32_t*>(upoff + R * MH);
   __shared__ int nup_s[R];
@@ -75,15 +75,16 @@ hv2c_kernel(Hv2cArgs a, const float2* __restrict__ x, float2* __restrict__ y,
     const int64_t g = g0 + r;
     urow[r] = g < a.dim_up ? (a.order ? (int64_t)a.order[g] : g) : a.dim_up;
   }
-  // ---- stage the R rows into their slots, the amplitude table, the up-hop lists
-  for (int d = threadIdx.x; d <= ld; d += T) {
+  // ---- stage the R rows into their slots (zero slots ld .. ld + G - 1), the amplitude
+  // table, the up-hop lists
+  for (int d = threadIdx.x; d < ld + G; d += T) {
     Pack<float2, R> p;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int64_t u = urow[r];
       p.v[r] = (d < ld && u < a.dim_up) ? x[u * ld + d] : make_float2(0.f, 0.f);
     }
-    xs[d < ld ? (d & ~(G - 1)) | a.slot_lo[d] : ld] = p;
+    xs[d < ld ? (d & ~(G - 1)) | a.slot_lo[d] : d] = p;
   }
   for (int i = threadIdx.x; i < a.namp; i += T) amp[i] = hv2c_amp(a, i);
   for (int i = threadIdx.x; i < R * a.maxhops_up; i += T) {
