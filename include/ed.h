@@ -298,6 +298,34 @@ ed_status ed_mlp_infer(ed_mlp* mlp, const ed_basis* basis, double U, ed_dtype dt
 
 void ed_mlp_destroy(ed_mlp* mlp);
 
+/* ed_hv_down_tables - HOST ONLY (no GPU, no CUDA call): the down-hop tables the fused
+ * Lanczos H.v builds for one species and one kernel geometry, by the same code the plan
+ * uses (the down part of H.v, Sec. 4 Eq. 6; the layout is this library's). For inspection
+ * and tests.
+ *  hop      [maxhops][dim] int32 (HOST): target rank | sign << 31 (bit 31 set = fermion
+ *           sign -1); entries whose rank (bits 0..29) is >= dim are padding.
+ *  hop_amp  NULL, or [maxhops][dim] amplitude numbers (complex entries only; NULL = 0).
+ *  bits     [dim] uint32 (HOST): bit strings in rank order.
+ *  ld       row length of the library's vectors: dim rounded up to a multiple of 32.
+ *  V, G     columns per thread (1..8) and shared-memory slots per bank group (8, 16, 32).
+ *  complex_entries  0: entries are slots (16-bit in the kernel); 1: slot | signed amplitude
+ *           index << 16, index 2 a + s for amplitude number a and sign bit s.
+ * Outputs, caller-owned HOST arrays:
+ *  table    [rows_cap][ld]: entry of hop step k of column p at table[k ld + p]: the slot
+ *           of the target column q, (q & ~(G-1)) | slot_lo[q], or a zero slot ld .. ld+G-1.
+ *  rows     the number of table rows (set also when rows_cap is too small).
+ *  kpn      [2 ceil(ld / (32 V))]: per chunk of 32 V columns, the rows of +1 hops, then the
+ *           rows of -1 hops (complex entries: all hops, then 0).
+ *  slot_lo  [ld]: slot of column p within its aligned group of G columns.
+ *  colpos   [dim]: column of each down rank (hop count descending, then +1-hop count
+ *           descending, then rank).
+ * Returns ED_ERR_ARG for inconsistent sizes, rows_cap < rows, or more than 255 hops of one
+ * sign in a column. */
+ed_status ed_hv_down_tables(const int32_t* hop, const int32_t* hop_amp, const uint32_t* bits,
+                            int64_t dim, int32_t maxhops, int32_t ld, int32_t V, int32_t G,
+                            int32_t complex_entries, uint32_t* table, int32_t rows_cap,
+                            int32_t* rows, uint8_t* kpn, uint8_t* slot_lo, int32_t* colpos);
+
 /* ed_selftest_barrier_timeout - failure-detection self-test of the bounded group barrier
  * used by ed_lanczos_solve_batched: a cooperative launch of `ctas` CTAs (2..64) in which
  * the last CTA never arrives at the barrier; the others must give up after timeout_ms

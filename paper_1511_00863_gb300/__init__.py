@@ -83,6 +83,9 @@ _SIGS = {
                                   c_uint64, POINTER(c_double)]),
     "ed_mlp_infer": (c_int, [c_void_p, c_void_p, c_double, c_int, c_void_p]),
     "ed_mlp_destroy": (None, [c_void_p]),
+    "ed_hv_down_tables": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32, c_int32,
+                                  c_int32, c_int32, c_void_p, c_int32, POINTER(c_int32), c_void_p,
+                                  c_void_p, c_void_p]),
     "ed_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -168,6 +171,32 @@ def ed_basis_dims(basis) -> tuple[int, int, int]:
     du, dd, d = c_int64(), c_int64(), c_int64()
     _check(_lib.ed_basis_dims(basis, byref(du), byref(dd), byref(d)))
     return du.value, dd.value, d.value
+
+
+def ed_hv_down_tables(hop, bits, V: int, G: int, hop_amp=None, complex_entries: bool = False):
+    """Host-only: the fused H.v's down tables of one species (no GPU needed).
+
+    hop: int32 [maxhops][dim] (target | sign << 31), bits: uint32 [dim], hop_amp: optional
+    int32 [maxhops][dim]. Returns dict(table [rows][ld] uint32, kpn [chunks][2] uint8,
+    slot_lo [ld] uint8, colpos [dim] int32, ld).
+    """
+    hop = np.ascontiguousarray(hop, dtype=np.int32)
+    bits = np.ascontiguousarray(bits, dtype=np.uint32)
+    mh, dim = (hop.shape if hop.ndim == 2 else (0, bits.size))
+    ld = (dim + 31) // 32 * 32
+    amp = None if hop_amp is None else np.ascontiguousarray(hop_amp, dtype=np.int32)
+    cap = max(1, 2 * mh)
+    table = np.zeros((cap, ld), dtype=np.uint32)
+    kpn = np.zeros(2 * ((ld + 32 * V - 1) // (32 * V)), dtype=np.uint8)
+    lo = np.zeros(ld, dtype=np.uint8)
+    colpos = np.zeros(dim, dtype=np.int32)
+    rows = c_int32(0)
+    _check(_lib.ed_hv_down_tables(hop.ctypes.data if mh else None,
+                                  None if amp is None else amp.ctypes.data, bits.ctypes.data,
+                                  dim, mh, ld, V, G, int(complex_entries), table.ctypes.data, cap,
+                                  byref(rows), kpn.ctypes.data, lo.ctypes.data, colpos.ctypes.data))
+    return {"table": table[:rows.value].copy(), "kpn": kpn.reshape(-1, 2), "slot_lo": lo,
+            "colpos": colpos, "ld": ld}
 
 
 def ed_basis_filling(basis):

@@ -5,12 +5,11 @@
 #include <cstring>
 #include <deque>
 #include <mutex>
-#include <numeric>
-#include <random>
 #include <vector>
 
 #include "ed_hv2_kernel.cuh"
 #include "ed_hv2c_kernel.cuh"
+#include "ed_tables.h"
 
 namespace ed {
 
@@ -117,272 +116,11 @@ void hv2_free(Hv2Plan* p) {
   delete p;
 }
 
-// Down-gather groups. One warp-wide gather of the kernel (hop step k, one of the V columns
-// of each lane) is served in phases of G lanes (G R-element slots fill the 32 banks once);
-// a phase costs as many shared-memory wavefronts as the largest number of distinct slots
-// in one bank group (slot mod G). A group is one chunk, one sign (table rows [k0, k0 + K):
-// the positive hops, then the negative ones; one group of all hops for the complex kernel),
-// one column v of the lanes and one phase: G columns whose hops run in the same K steps.
-struct GatherGroup {
-  int c, v, p;  // chunk, column within the lane, first lane of the phase
-  int k0, K;    // table rows
-};
-
-static std::vector<GatherGroup> gather_groups(int ld, int V, int G, const std::vector<int>& kp,
-                                              const std::vector<int>& kn) {
-  std::vector<GatherGroup> gg;
-  const int nch = (int)kp.size();
-  for (int c = 0; c < nch; ++c)
-    for (int sg = 0; sg < 2; ++sg) {
-      const int k0 = sg ? kp[c] : 0, K = sg ? kn[c] : kp[c];
-      if (K == 0) continue;
-      for (int v = 0; v < V; ++v)
-        for (int p = 0; p < 32; p += G)
-          if (c * 32 * V + p * V + v < ld) gg.push_back({c, v, p, k0, K});
-    }
-  return gg;
-}
-
-static inline int group_column(const GatherGroup& g, int l, int V) {
-  return g.c * 32 * V + (g.p + l) * V + g.v;
-}
-
-// Slot map: lo[p] for every column, a permutation inside each aligned group of G columns
-// (so slot mod G = lo[p]). The hops of a group can be reordered per lane (below), so what
-// matters is how many of the group's hops land in each bank group: at most K each allows a
-// conflict-free order (a bipartite graph of maximum degree K has a K-edge-colouring). The
-// search lowers the excess over K, summed over bank groups and groups (squares as the tie
-// break): take a group with an over-full and an under-full bank group, move one target of
-// the first to the second by swapping lo with the column of its aligned group that holds
-// it, keep the swap unless the affected groups get worse. Fixed seed: the result depends
-// only on the tables.
-static std::vector<uint8_t> choose_slots(const std::vector<int32_t>& tcol,
-                                         const std::vector<GatherGroup>& gg, int ld, int V,
-                                         int G) {
-  const int ng = (int)gg.size();
-  std::vector<int> goff{0}, gcol, gcnt, tmp;  // per group: distinct targets and multiplicity
-  for (const GatherGroup& g : gg) {
-    tmp.clear();
-    for (int l = 0; l < G; ++l) {
-      const int q = group_column(g, l, V);
-      if (q >= ld) continue;
-      for (int k = 0; k < g.K; ++k) {
-        const int t = tcol[(size_t)(g.k0 + k) * ld + q];
-        if (t >= 0) tmp.push_back(t);
-      }
-    }
-    std::sort(tmp.begin(), tmp.end());
-    for (size_t i = 0; i < tmp.size();) {
-      size_t j = i;
-      while (j < tmp.size() && tmp[j] == tmp[i]) ++j;
-      gcol.push_back(tmp[i]);
-      gcnt.push_back((int)(j - i));
-      i = j;
-    }
-    goff.push_back((int)gcol.size());
-  }
-  std::vector<int> ooff((size_t)ld + 1, 0), ogrp, ocnt;  // groups that gather each column
-  for (int x : gcol) ++ooff[x + 1];
-  for (int i = 0; i < ld; ++i) ooff[i + 1] += ooff[i];
-  ogrp.resize(gcol.size());
-  ocnt.resize(gcol.size());
-  {
-    std::vector<int> fill(ooff.begin(), ooff.end() - 1);
-    for (int g = 0; g < ng; ++g)
-      for (int j = goff[g]; j < goff[g + 1]; ++j) {
-        ogrp[fill[gcol[j]]] = g;
-        ocnt[fill[gcol[j]]++] = gcnt[j];
-      }
-  }
-  std::vector<uint8_t> col((size_t)ld);
-  for (int i = 0; i < ld; ++i) col[i] = (uint8_t)(i % G);
-  std::vector<int> h((size_t)ng * G, 0);  // hops of each group per bank group
-  for (int g = 0; g < ng; ++g)
-    for (int j = goff[g]; j < goff[g + 1]; ++j) h[(size_t)g * G + col[gcol[j]]] += gcnt[j];
-  auto f = [](long e) { return e > 0 ? 1024 * e + e * e : 0L; };  // cost of an excess e
-  // a swap changes only bank groups co and cu of the groups gathering a or b
-  auto pair_cost = [&](int g, int co, int cu) {
-    return f(h[(size_t)g * G + co] - gg[g].K) + f(h[(size_t)g * G + cu] - gg[g].K);
-  };
-  std::mt19937 rng(12345u);
-  std::vector<long> mark((size_t)ng, -1);
-  std::vector<int> aff;
-  const long iters = ng > 0 ? 48L * ld : 0;
-  for (long it = 0; it < iters; ++it) {
-    const int g = (int)(rng() % (uint32_t)ng);
-    const int nt = goff[g + 1] - goff[g];
-    if (nt == 0) continue;
-    const int a = gcol[goff[g] + (int)(rng() % (uint32_t)nt)];
-    const int co = col[a];
-    const int* hg = &h[(size_t)g * G];
-    if (hg[co] <= gg[g].K) continue;
-    int under[32], nu = 0;
-    for (int b = 0; b < G; ++b)
-      if (hg[b] < gg[g].K) under[nu++] = b;
-    if (!nu) continue;
-    const int cu = under[rng() % (uint32_t)nu];
-    int b = -1;
-    for (int q = a & ~(G - 1); q < (a & ~(G - 1)) + G; ++q)
-      if (col[q] == cu) b = q;
-    if (b < 0) continue;
-    aff.clear();
-    for (int j = ooff[a]; j < ooff[a + 1]; ++j)
-      if (mark[ogrp[j]] != it) mark[ogrp[j]] = it, aff.push_back(ogrp[j]);
-    for (int j = ooff[b]; j < ooff[b + 1]; ++j)
-      if (mark[ogrp[j]] != it) mark[ogrp[j]] = it, aff.push_back(ogrp[j]);
-    long before = 0, after = 0;
-    for (int x : aff) before += pair_cost(x, co, cu);
-    auto move = [&](int from, int to) {
-      for (int j = ooff[a]; j < ooff[a + 1]; ++j) {
-        h[(size_t)ogrp[j] * G + from] -= ocnt[j];
-        h[(size_t)ogrp[j] * G + to] += ocnt[j];
-      }
-      for (int j = ooff[b]; j < ooff[b + 1]; ++j) {
-        h[(size_t)ogrp[j] * G + to] -= ocnt[j];
-        h[(size_t)ogrp[j] * G + from] += ocnt[j];
-      }
-    };
-    move(co, cu);
-    for (int x : aff) after += pair_cost(x, co, cu);
-    if (after <= before) {
-      std::swap(col[a], col[b]);
-    } else {
-      move(cu, co);
-    }
-  }
-  return col;
-}
-
-// Hop order inside each group: the hops of the G lanes are the edges of a bipartite graph
-// between lanes and bank groups, and the K steps colour its edges, so that no lane takes
-// two hops in one step. Each bank group is split into nodes of at most K hops, so every
-// node has degree <= K and a K-edge-colouring exists (Koenig); it is built edge by edge,
-// swapping two colours along an alternating path where the free ones differ. A step then
-// meets a bank group as often as that group has nodes used in it: once when its hops fit.
-// Padding entries become the zero slot (ld + bank group) of a bank group the step leaves
-// free. Rows of tcol (and the amplitude indices `tamp`, when given) are permuted within
-// each group's rows; a zero slot is stored as ld + bank group.
-static void schedule_gathers(std::vector<int32_t>& tcol, std::vector<uint32_t>& tamp,
-                             const std::vector<GatherGroup>& gg, const std::vector<uint8_t>& lo,
-                             int ld, int V, int G) {
-  std::vector<int> eu, ew, erow, ec, at, path, base, deg;
-  std::vector<int32_t> old_t;
-  std::vector<uint32_t> old_a;
-  std::vector<uint32_t> used;
-  for (const GatherGroup& g : gg) {
-    const int K = g.K;
-    deg.assign((size_t)G, 0);
-    for (int l = 0; l < G; ++l) {
-      const int q = group_column(g, l, V);
-      if (q >= ld) continue;
-      for (int k = 0; k < K; ++k) {
-        const int t = tcol[(size_t)(g.k0 + k) * ld + q];
-        if (t >= 0) ++deg[lo[t]];
-      }
-    }
-    base.assign((size_t)G + 1, G);  // node ids: lanes [0, G), then the bank-group nodes
-    for (int b = 0; b < G; ++b) base[b + 1] = base[b] + (deg[b] + K - 1) / K;
-    const int nnodes = base[G];
-    eu.clear(), ew.clear(), erow.clear();
-    std::vector<int> seen((size_t)G, 0);
-    for (int l = 0; l < G; ++l) {
-      const int q = group_column(g, l, V);
-      if (q >= ld) continue;
-      for (int k = 0; k < K; ++k) {
-        const int t = tcol[(size_t)(g.k0 + k) * ld + q];
-        if (t < 0) continue;
-        const int b = lo[t];
-        eu.push_back(l);
-        ew.push_back(base[b] + seen[b]++ / K);
-        erow.push_back(k);
-      }
-    }
-    const int E = (int)eu.size();
-    ec.assign((size_t)E, -1);
-    at.assign((size_t)nnodes * K, -1);
-    bool ok = true;
-    for (int e = 0; e < E && ok; ++e) {
-      const int u = eu[e], w = ew[e];
-      int a = -1, b = -1;
-      for (int s = 0; s < K && a < 0; ++s)
-        if (at[(size_t)u * K + s] < 0) a = s;
-      for (int s = 0; s < K && b < 0; ++s)
-        if (at[(size_t)w * K + s] < 0) b = s;
-      if (a < 0 || b < 0) {
-        ok = false;
-        break;
-      }
-      if (at[(size_t)w * K + a] >= 0) {  // swap colours a and b along the path from w
-        path.clear();
-        int node = w, want = a;
-        for (int pe; (pe = at[(size_t)node * K + want]) >= 0;) {
-          path.push_back(pe);
-          if ((int)path.size() > E) {
-            ok = false;
-            break;
-          }
-          node = eu[pe] == node ? ew[pe] : eu[pe];
-          want = want == a ? b : a;
-        }
-        if (!ok) break;
-        for (int pe : path) at[(size_t)eu[pe] * K + ec[pe]] = at[(size_t)ew[pe] * K + ec[pe]] = -1;
-        for (int pe : path) {
-          ec[pe] = ec[pe] == a ? b : a;
-          at[(size_t)eu[pe] * K + ec[pe]] = at[(size_t)ew[pe] * K + ec[pe]] = pe;
-        }
-      }
-      ec[e] = a;
-      at[(size_t)u * K + a] = at[(size_t)w * K + a] = e;
-    }
-    if (!ok) ec.assign((size_t)E, -1);  // cannot happen; keep the original order
-    used.assign((size_t)K, 0u);
-    for (int e = 0; e < E; ++e) {
-      const int s = ec[e] >= 0 ? ec[e] : erow[e];
-      const int q = group_column(g, eu[e], V);
-      used[s] |= 1u << lo[tcol[(size_t)(g.k0 + erow[e]) * ld + q]];
-    }
-    // write the lanes back in their new order, padding on a free zero slot
-    for (int l = 0, e = 0; l < G; ++l) {
-      const int q = group_column(g, l, V);
-      if (q >= ld) continue;
-      old_t.resize((size_t)K);
-      old_a.resize((size_t)K);
-      for (int k = 0; k < K; ++k) {
-        old_t[k] = tcol[(size_t)(g.k0 + k) * ld + q];
-        if (!tamp.empty()) old_a[k] = tamp[(size_t)(g.k0 + k) * ld + q];
-        tcol[(size_t)(g.k0 + k) * ld + q] = -1;
-      }
-      for (; e < E && eu[e] == l; ++e) {
-        const int s = ec[e] >= 0 ? ec[e] : erow[e];
-        tcol[(size_t)(g.k0 + s) * ld + q] = old_t[erow[e]];
-        if (!tamp.empty()) tamp[(size_t)(g.k0 + s) * ld + q] = old_a[erow[e]];
-      }
-      for (int k = 0; k < K; ++k) {
-        int32_t& t = tcol[(size_t)(g.k0 + k) * ld + q];
-        if (t >= 0) continue;
-        const uint32_t freeb = ~used[k] & (G == 32 ? 0xFFFFFFFFu : ((1u << G) - 1u));
-        t = ld + (freeb ? __builtin_ctz(freeb) : 0);
-        if (!tamp.empty()) tamp[(size_t)(g.k0 + k) * ld + q] = 0u;
-      }
-    }
-  }
-}
-
 // Down-state column order and per-geometry tables, built on the host from the basis tables:
 // columns ordered by hop count (most first), then by +1-hop count, then by rank; per chunk of
 // 32 V columns the table rows [0, kp) hold the +1 hops and [kp, kp + kn) the -1 hops as
 // shared-memory slots, each column's hops in the order schedule_gathers gives them.
 // Variants with the same (V, G) share them; the basis caches them.
-struct DownTables {
-  int V = 0, G = 0, ld = 0;
-  bool cplx = false;              // complex kernel: 32-bit entries slot | amplitude index << 16
-  std::vector<uint16_t> tab;
-  std::vector<uint32_t> tab32;
-  std::vector<uchar2> kpn;
-  std::vector<uint8_t> lo;
-  std::vector<uint32_t> pad;
-  std::vector<int32_t> pos;
-};
 static std::mutex g_tables_mu;
 
 // Column order of the down states (by hop count, most first; ties by rank) and the tables of
@@ -402,85 +140,8 @@ static ed_status compute_down_tables(const ed_basis* b, int ld, const KindInfo& 
   }
   ED_TRY_CUDA(cudaMemcpyAsync(bits.data(), b->dn.bits, bits.size() * 4, cudaMemcpyDeviceToHost, s));
   ED_TRY_CUDA(cudaStreamSynchronize(s));
-  std::vector<int> np((size_t)n, 0), nn((size_t)n, 0);  // hops with sign +1 / -1
-  for (int k = 0; k < mh; ++k)
-    for (int64_t d = 0; d < n; ++d) {
-      const uint32_t h = (uint32_t)hop[(size_t)k * n + d];
-      if ((int64_t)(h & kTargetMask) < n) ++((h & kSignBit) ? nn : np)[d];
-    }
-  std::vector<int32_t> perm((size_t)n), pos((size_t)n);
-  std::iota(perm.begin(), perm.end(), 0);
-  std::stable_sort(perm.begin(), perm.end(), [&](int32_t x, int32_t y) {
-    const int cx = np[x] + nn[x], cy = np[y] + nn[y];
-    return cx != cy ? cx > cy : np[x] > np[y];
-  });
-  for (int64_t q = 0; q < n; ++q) pos[perm[q]] = (int32_t)q;
-
-  // per chunk: rows [0, kp) positive hops, [kp, kp + kn) negative hops
-  const int chunk = 32 * ki.V;
-  const int nchunks = (ld + chunk - 1) / chunk;
-  std::vector<int> kp((size_t)nchunks, 0), kn((size_t)nchunks, 0), kcount((size_t)nchunks, 0);
-  for (int64_t q = 0; q < n; ++q) {
-    if (cplx) {  // one loop over all hops: the sign is in the amplitude
-      kp[q / chunk] = std::max(kp[q / chunk], np[perm[q]] + nn[perm[q]]);
-    } else {
-      kp[q / chunk] = std::max(kp[q / chunk], np[perm[q]]);
-      kn[q / chunk] = std::max(kn[q / chunk], nn[perm[q]]);
-    }
-  }
-  int rows = 1;
-  for (int c = 0; c < nchunks; ++c) {
-    if (kp[c] > 255 || kn[c] > 255) {
-      set_error("H.v tables: more than 255 down hops of one sign");
-      return ED_ERR_ARG;
-    }
-    kcount[c] = kp[c] + kn[c];
-    rows = std::max(rows, kcount[c]);
-  }
-  std::vector<int32_t> tcol((size_t)rows * ld, -1);  // target column, -1 = zero slot
-  std::vector<uint32_t> tamp(cplx ? tcol.size() : 0, 0u);  // signed amplitude index
-  for (int64_t q = 0; q < n; ++q) {
-    const int c = (int)(q / chunk);
-    int ip = 0, in = kp[c];
-    for (int k = 0; k < mh; ++k) {
-      const uint32_t h = (uint32_t)hop[(size_t)k * n + perm[q]];
-      const uint32_t tg = h & kTargetMask;
-      if ((int64_t)tg >= n) continue;
-      const int row = cplx ? ip++ : (h & kSignBit) ? in++ : ip++;
-      tcol[(size_t)row * ld + q] = pos[tg];
-      if (cplx) {
-        const uint32_t num = hopa.empty() ? 0u : (uint32_t)hopa[(size_t)k * n + perm[q]];
-        tamp[(size_t)row * ld + q] = 2u * num + (h >> 31);
-      }
-    }
-  }
-  const std::vector<GatherGroup> gg = gather_groups(ld, ki.V, ki.G, kp, kn);
-  out.lo = choose_slots(tcol, gg, ld, ki.V, ki.G);
-  const std::vector<uint8_t>& lo = out.lo;
-  schedule_gathers(tcol, tamp, gg, lo, ld, ki.V, ki.G);
-  // slot of a table entry: the target's, a zero slot as stored, or the first zero slot
-  auto slot = [&](int32_t t) {
-    return (uint32_t)(t < 0 ? ld : t >= ld ? t : (t & ~(ki.G - 1)) | lo[t]);
-  };
-  out.cplx = cplx;
-  if (cplx) {
-    out.tab32.assign((size_t)rows * ld, 0u);
-    for (size_t i = 0; i < tcol.size(); ++i) out.tab32[i] = slot(tcol[i]) | (tamp[i] << 16);
-  } else {
-    std::vector<uint16_t>& tab = out.tab;
-    tab.assign((size_t)rows * ld, 0);
-    for (size_t i = 0; i < tcol.size(); ++i) tab[i] = (uint16_t)slot(tcol[i]);
-  }
-  std::vector<uchar2>& kpnv = out.kpn;
-  kpnv.resize((size_t)nchunks);
-  for (int c = 0; c < nchunks; ++c) kpnv[c] = make_uchar2((unsigned char)kp[c], (unsigned char)kn[c]);
-  out.pad.assign((size_t)ld, 0u);
-  for (int64_t q = 0; q < n; ++q) out.pad[q] = bits[perm[q]];
-  out.pos = pos;
-  out.V = ki.V;
-  out.G = ki.G;
-  out.ld = ld;
-  return ED_OK;
+  return build_down_tables(hop.data(), hopa.empty() ? nullptr : hopa.data(), bits.data(), n, mh,
+                           ld, ki.V, ki.G, cplx, out);
 }
 
 static ed_status upload_down_tables(const DownTables& t, int64_t n, cudaStream_t s, Hv2Plan* p) {
@@ -488,7 +149,7 @@ static ed_status upload_down_tables(const DownTables& t, int64_t n, cudaStream_t
   const size_t tbytes = t.cplx ? t.tab32.size() * 4 : t.tab.size() * 2;
   const void* tdata = t.cplx ? (const void*)t.tab32.data() : (const void*)t.tab.data();
   if (cudaMalloc(&p->dtab, tbytes) != cudaSuccess ||
-      cudaMalloc((void**)&p->kpn, t.kpn.size() * sizeof(uchar2)) != cudaSuccess ||
+      cudaMalloc((void**)&p->kpn, t.kpn.size()) != cudaSuccess ||
       cudaMalloc((void**)&p->slot_lo, (size_t)ld) != cudaSuccess ||
       cudaMalloc((void**)&p->dn_pad, (size_t)ld * 4) != cudaSuccess ||
       cudaMalloc((void**)&p->colpos, (size_t)(n > 0 ? n : 1) * 4) != cudaSuccess) {
@@ -496,8 +157,7 @@ static ed_status upload_down_tables(const DownTables& t, int64_t n, cudaStream_t
     return ED_ERR_OOM;
   }
   ED_TRY_CUDA(cudaMemcpyAsync(p->dtab, tdata, tbytes, cudaMemcpyHostToDevice, s));
-  ED_TRY_CUDA(cudaMemcpyAsync(p->kpn, t.kpn.data(), t.kpn.size() * sizeof(uchar2),
-                              cudaMemcpyHostToDevice, s));
+  ED_TRY_CUDA(cudaMemcpyAsync(p->kpn, t.kpn.data(), t.kpn.size(), cudaMemcpyHostToDevice, s));
   ED_TRY_CUDA(cudaMemcpyAsync(p->slot_lo, t.lo.data(), t.lo.size(), cudaMemcpyHostToDevice, s));
   ED_TRY_CUDA(cudaMemcpyAsync(p->dn_pad, t.pad.data(), t.pad.size() * 4, cudaMemcpyHostToDevice, s));
   ED_TRY_CUDA(cudaMemcpyAsync(p->colpos, t.pos.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));

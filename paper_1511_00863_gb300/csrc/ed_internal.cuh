@@ -8,6 +8,7 @@
 #include <cstdio>
 
 #include "ed.h"
+#include "ed_tables.h"  // hop-entry layout (kTargetMask, kSignBit)
 
 namespace ed {
 
@@ -35,8 +36,6 @@ void clear_error();
 
 constexpr int kMaxSites = 32;
 constexpr int kBinomStride = 33;          // C[n * 33 + k], n, k in [0, 32]
-constexpr uint32_t kTargetMask = 0x3FFFFFFFu;  // hop entry: target rank in bits 0..29
-constexpr uint32_t kSignBit = 0x80000000u;     // hop entry: bit 31 = negative fermion sign
 
 // Hop table of one species: entry k of state r at hop[k * dim + r].
 struct SpeciesTables {
@@ -91,6 +90,10 @@ inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 
 // Row-staged H.v kernels run one CTA per few up rows; with fewer rows than this the
 // element-parallel global kernels are chosen instead (automatic selection only).
 constexpr int64_t kMinRowsStaged = 64;
+// CTAs per SM of the fixed-point update pass (its register bound allows them; more warps
+// hide the HBM latency of this ALU-heavy streaming pass). Its grid is at most this many CTAs
+// per SM, four int64 partial words each.
+constexpr int kFxUpdateCtasPerSm = 6;
 
 // Number of SMs of the current device (cached per device).
 int sm_count();
