@@ -354,7 +354,7 @@ fx_hv_global_kernel(FxHvArgs a, const long long* __restrict__ x, long long* __re
   fx_block_reduce(dot, 0, part + 4 * blockIdx.x);
 }
 
-__global__ void __launch_bounds__(kFxThreads, kFxUpdateCtasPerSm)
+__global__ void __launch_bounds__(kFxThreads)
 fx_update_kernel(LzScalars* S, int cur, const long long* __restrict__ xc, long long* __restrict__ xp,
                  int64_t n, const long long* __restrict__ pa, int na, long long* __restrict__ pb) {
   if (S->status != 0) return;
@@ -514,12 +514,6 @@ fx_psi_norm_kernel(const long long* __restrict__ P, int64_t n, long long* __rest
 }
 
 // ------------------------------------------------------------------ host side
-static int fx_update_grid(int64_t n) {
-  const int64_t want = (n + kFxThreads - 1) / kFxThreads;
-  const int64_t cap = (int64_t)sm_count() * kFxUpdateCtasPerSm;
-  return (int)(want < 1 ? 1 : (want < cap ? want : cap));
-}
-
 static int fx_red_grid(int64_t n) {
   const int64_t want = (n + kFxThreads - 1) / kFxThreads;
   const int64_t cap = (int64_t)sm_count() * 4;
@@ -646,7 +640,7 @@ ed_status fx_step(const ed_basis* b, const FxRun& fx, double t, double U, long l
   ED_TRY_CUDA(cudaGetLastError());
   if (ev1) ED_TRY_CUDA(cudaEventRecord(ev1, s));
   const int64_t n = b->up.dim * ld;
-  const int ug = fx_update_grid(n);
+  const int ug = fx_red_grid(n);
   fx_update_kernel<<<ug, kFxThreads, 0, s>>>(S, cur, B[cur], B[1 - cur], n, pa, grid, pb);
   fx_finish_kernel<<<1, kRedThreads, 0, s>>>(S, cur, pb, ug);
   ED_TRY_CUDA(cudaGetLastError());

@@ -90,10 +90,6 @@ inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 
 // Row-staged H.v kernels run one CTA per few up rows; with fewer rows than this the
 // element-parallel global kernels are chosen instead (automatic selection only).
 constexpr int64_t kMinRowsStaged = 64;
-// CTAs per SM of the fixed-point update pass (its register bound allows them; more warps
-// hide the HBM latency of this ALU-heavy streaming pass). Its grid is at most this many CTAs
-// per SM, four int64 partial words each.
-constexpr int kFxUpdateCtasPerSm = 6;
 
 // Number of SMs of the current device (cached per device).
 int sm_count();

@@ -416,7 +416,7 @@ static ed_status lz_alloc(const ed_basis* b, const ed_opts* o, cudaStream_t s, e
   st->n = b->up.dim * st->ld;
   // partial sums: one double per CTA, or four int64 words per CTA on the fixed-point path
   st->npa = hv_max_grid(b) * (st->fx ? 4 : 1);
-  st->npb = (int64_t)sm_count() * (st->fx ? 4 * kFxUpdateCtasPerSm : 4);
+  st->npb = (int64_t)sm_count() * 4 * (st->fx ? 6 : 1);
   auto fail = [&](ed_status e) {
     ed_lanczos_destroy(st);
     return e;
