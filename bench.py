@@ -163,6 +163,24 @@ def _dist():
     return ws, rank, local
 
 
+def _max_over_ranks(values, device):
+    """Element-wise maximum over all ranks (every rank gets it); the values unchanged on a
+    single process. The collective also orders the ranks like a barrier."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    tt = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return [float(v) for v in tt.tolist()]
+
+
+def _whole_job_rate(ws, units_per_rank, t_max_s):
+    """Units all ranks processed per second of the slowest rank (weak scaling: every rank
+    does the same work)."""
+    return ws * units_per_rank / t_max_s
+
+
 def _workload_config(name, dim, du, dd, dtype):
     w = ed_inputs.workload(name)
     return {"workload": f"{name}: periodic lattice, {w['n_sites']} sites, N_up={w['n_up']}, "
@@ -389,14 +407,9 @@ def bench_ours(args):
     clk = clocks.stop(local) if rank == 0 else None
     E_K, steps_done = ed.ed_lanczos_energy(st)
     ed.ed_lanczos_destroy(st)
-    t_max = ms
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms, hv_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max, hv_ms = float(tt[0]), float(tt[1])
+    t_max, hv_ms = _max_over_ranks([ms, hv_ms], "cuda")
     ms_per_step = t_max / K
-    value = ws * K / (t_max / 1e3)
+    value = _whole_job_rate(ws, K, t_max / 1e3)
 
     # ---------------------------------------------------------------- end to end (C ABI)
     # start vector from pinned host memory, copied in the timed region; fixed K steps;
@@ -425,11 +438,7 @@ def bench_ours(args):
     _, first_s = e2e_call()
     res, e2e_s = e2e_call()
     barrier()
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt[0])
+    (e2e_s,) = _max_over_ranks([e2e_s], "cuda")
     d2h = 3 * (ed.ED_MAX_STEPS + 2) * 8 + 8 * math.ceil(K / 16)
 
     if rank != 0:
@@ -460,7 +469,7 @@ def bench_ours(args):
             "config": _workload_config(args.workload, dim, du, dd, dtype),
             "hv_ms_per_step": hv_launch_ms, "E0_after_steps": E_K, "steps_done": steps_done,
             "roofline": roofline,
-            "e2e": {"value": ws * K / e2e_s, "unit": "lanczos_steps/s",
+            "e2e": {"value": _whole_job_rate(ws, K, e2e_s), "unit": "lanczos_steps/s",
                     "h2d_bytes_per_step": dim * esize / K, "d2h_bytes_per_step": d2h / K,
                     "E0": res["E0"], "api": "ed_lanczos_solve (f1 from pinned host memory)",
                     "first_call_s": first_s,
