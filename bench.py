@@ -475,7 +475,9 @@ def bench_ours(args):
                     "first_call_s": first_s,
                     "note": "second call on the basis; the first also allocates the cached "
                             "state, builds the H.v plan and captures the graph (first_call_s)"},
-            "gpu_launches": 3 * K,
+            # per timed step: (plan,) fused H.v, update, finish; the FP64-accurate path's
+            # plan kernel sets the next H.v's integer coefficients
+            "gpu_launches": (4 if dtype == "f64" else 3) * K,
             "clocks": clk}
     if ws == 1 and not args.no_extras and w.get("t_bond") is None:
         line["time_to_E0"] = time_to_e0_headline(ed, basis, w)
