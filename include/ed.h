@@ -304,7 +304,8 @@ void ed_mlp_destroy(ed_mlp* mlp);
  * and tests.
  *  hop      [maxhops][dim] int32 (HOST): target rank | sign << 31 (bit 31 set = fermion
  *           sign -1); entries whose rank (bits 0..29) is >= dim are padding.
- *  hop_amp  NULL, or [maxhops][dim] amplitude numbers (complex entries only; NULL = 0).
+ *  hop_amp  NULL, or [maxhops][dim] amplitude numbers a, 0 <= 2 a + 1 < 65536 (complex
+ *           entries only; NULL = 0).
  *  bits     [dim] uint32 (HOST): bit strings in rank order.
  *  ld       row length of the library's vectors: dim rounded up to a multiple of 32.
  *  V, G     columns per thread (1..8) and shared-memory slots per bank group (8, 16, 32).
@@ -319,8 +320,8 @@ void ed_mlp_destroy(ed_mlp* mlp);
  *  slot_lo  [ld]: slot of column p within its aligned group of G columns.
  *  colpos   [dim]: column of each down rank (hop count descending, then +1-hop count
  *           descending, then rank).
- * Returns ED_ERR_ARG for inconsistent sizes, rows_cap < rows, or more than 255 hops of one
- * sign in a column. */
+ * Returns ED_ERR_ARG for inconsistent sizes, rows_cap < rows, an amplitude number out of
+ * range, or more than 255 hops of one sign in a column. */
 ed_status ed_hv_down_tables(const int32_t* hop, const int32_t* hop_amp, const uint32_t* bits,
                             int64_t dim, int32_t maxhops, int32_t ld, int32_t V, int32_t G,
                             int32_t complex_entries, uint32_t* table, int32_t rows_cap,

@@ -316,8 +316,12 @@ ed_status build_down_tables(const int32_t* hop, const int32_t* hopa, const uint3
       const int row = cplx ? ip++ : (h & kSignBit) ? in++ : ip++;
       tcol[(size_t)row * ld + q] = pos[tg];
       if (cplx) {
-        const uint32_t num = hopa ? (uint32_t)hopa[(size_t)k * n + perm[q]] : 0u;
-        tamp[(size_t)row * ld + q] = 2u * num + (h >> 31);
+        const int32_t num = hopa ? hopa[(size_t)k * n + perm[q]] : 0;
+        if (num < 0 || 2 * (int64_t)num + 1 > 0xFFFF) {  // the index field has 16 bits
+          set_error("H.v tables: amplitude number %d out of range", num);
+          return ED_ERR_ARG;
+        }
+        tamp[(size_t)row * ld + q] = 2u * (uint32_t)num + (h >> 31);
       }
     }
   }
@@ -352,7 +356,6 @@ ed_status build_down_tables(const int32_t* hop, const int32_t* hopa, const uint3
   out.rows = rows;
   return ED_OK;
 }
-
 
 }  // namespace ed
 

@@ -160,3 +160,8 @@ def test_bad_geometry():
     with pytest.raises(ed.EdError) as e:
         ed.ed_hv_down_tables(hop, bits, 2, 12)
     assert e.value.status == ed.ED_ERR_ARG
+    bad = amp.copy()
+    bad[0, 0] = 40000  # 2 a + 1 does not fit the 16-bit index field
+    with pytest.raises(ed.EdError) as e:
+        ed.ed_hv_down_tables(hop, bits, 2, 16, hop_amp=bad, complex_entries=True)
+    assert e.value.status == ed.ED_ERR_ARG
