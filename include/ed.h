@@ -102,8 +102,9 @@ typedef struct {
  *             ED_F32, complex pairs for ED_C32 / ED_C64. The seeded complex start vector
  *             takes element i = (r_2i, r_2i+1) from the real sequence of ed_start_vector
  *             over 2 dim entries, scaled to unit norm.
- *  schedule   fused H.v kernel variant (1..7 for ED_F32, 8..13 for ED_F64; a variant of
- *             the other precision or one that does not fit falls back to the default one,
+ *  schedule   fused H.v kernel variant (1..7 and 14 for ED_F32, 8..13 for ED_F64, 20..23
+ *             for ED_C32; a variant of another precision or one that does not fit falls
+ *             back to the default one,
  *             see ed_lanczos_schedule); -1 = for bases of at least 2^22 states, the fastest
  *             variant for this basis and dtype, found by timing every variant that fits on
  *             the first run's buffers and remembered by the basis; smaller bases take the
