@@ -19,5 +19,8 @@ Module map:
                complex hoppings) and its real view
   mlp          the learned start-vector network, its loss and gradient (no counterpart in
                the paper; test oracle of the library's MLP kernels)
+  bethe        ground-state energy of the periodic Hubbard ring from the Lieb-Wu
+               Bethe-ansatz equations (an exact method of its own, used to pin the
+               full-size ring workloads beyond the explicit matrix's reach)
 """
-from . import basis, hamiltonian, tridiag, lanczos, dense, mlp, observables, complex_hopping  # noqa: F401
+from . import basis, hamiltonian, tridiag, lanczos, dense, mlp, observables, complex_hopping, bethe  # noqa: F401

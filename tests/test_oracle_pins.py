@@ -256,3 +256,56 @@ def test_lanczos_full_reorth_keeps_orthogonality():
     w_H = np.linalg.eigvalsh(H.toarray())
     assert w_T[0] >= w_H[0] - 1e-10 and w_T[-1] <= w_H[-1] + 1e-10
     assert abs(w_T[0] - w_H[0]) <= 1e-10
+
+
+# ------------------------------------------------- error-bound scale |H| |x| of the H.v tests
+RANDOM_BONDS = (9, np.array([[0, 5], [3, 8], [1, 2], [7, 0], [6, 4], [2, 8], [5, 1], [8, 3]]),
+                4, 3, 1.3, -1.5)
+
+
+@pytest.mark.parametrize("case", CASES + [RANDOM_BONDS])
+def test_abs_rows_match_abs_matrix(case):
+    """(|H| |x|)_g from the hops out of each state equals |H| @ |x| with H built column by
+    column (Eq. 1 plus the on-site term): every row, a U of either sign, a doubled bond
+    (the 2x4 lattice) and a bond listed in both orders (the random list)."""
+    H = hamiltonian.hamiltonian_csr(*case)
+    x = ed_inputs.uniform_pm1(17, H.shape[0])
+    rows = np.arange(H.shape[0])
+    ref = abs(H) @ np.abs(x)
+    got = hamiltonian.hv_abs_rows(*case, x, rows)
+    assert np.all(got >= 0)
+    assert np.allclose(got, ref, rtol=1e-14, atol=0)
+    # and it bounds the signed rows term by term
+    assert np.all(np.abs(hamiltonian.hv_rows(*case, x, rows)) <= got * (1 + 1e-14))
+
+
+# ------------------------------------------------------------------ Bethe-ansatz ring pin
+from oracle import bethe  # noqa: E402
+
+
+@pytest.mark.parametrize("L,nu,nd", [(4, 2, 2), (6, 3, 3), (8, 4, 4), (6, 2, 2), (5, 2, 2),
+                                     (7, 3, 2), (6, 1, 1), (9, 3, 3)])
+@pytest.mark.parametrize("U", [0.5, 4.0, 8.0])
+def test_bethe_ansatz_matches_diagonalisation(L, nu, nd, U):
+    """The Lieb-Wu ring energy equals the oracle's E0 (dense eigh, or Algorithm 1 with full
+    reorthogonalisation above the dense limit) on small periodic rings: half filling with
+    odd and even particle numbers per spin (the 16-site ring workload is even), and open-
+    shell fillings whose ground state has higher spin."""
+    E_bethe = bethe.ring_ground_energy(L, nu, nd, U)
+    bonds = ed_inputs.ring_bonds(L)
+    if math.comb(L, nu) * math.comb(L, nd) <= 2000:
+        ref = dense.spectrum(L, bonds, nu, nd, 1.0, U)[0]
+    else:
+        ref = _lanczos_E0(L, bonds, nu, nd, 1.0, U, tol=1e-15, steps=400)
+    assert abs(E_bethe - ref) <= 1e-12 * abs(ref), (E_bethe, ref)
+
+
+def test_bethe_quantum_number_parity():
+    """I_j integers for even M, half-odd for odd M; J_a integers for odd N - M, half-odd for
+    even N - M; both sets consecutive."""
+    for N, M in [(16, 8), (12, 6), (5, 2), (4, 1), (7, 3)]:
+        I, J = bethe.ground_state_numbers(16, N, M)
+        assert len(I) == N and len(J) == M
+        assert np.all(np.diff(I) == 1) and np.all(np.diff(J) == 1)
+        assert np.all((I - (0.0 if M % 2 == 0 else 0.5)) % 1.0 == 0.0)
+        assert np.all((J - (0.0 if (N - M) % 2 == 1 else 0.5)) % 1.0 == 0.0)
