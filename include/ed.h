@@ -55,8 +55,12 @@ typedef enum {
  *                 than 510 hops per state), hop sums and dot products exact in integers.
  *                 GB300 executes FP64 arithmetic at about 1/70 of its FP32 rate; this path
  *                 runs no FP64 instruction per vector element.
- *  ED_F32         FP32 vectors and FP32 H.v arithmetic; a_j, b_j, dot-product accumulation
- *                 and the tridiagonal eigensolve in FP64.
+ *  ED_F32         FP32 vectors and FP32 H.v arithmetic; a_j, b_j and the tridiagonal
+ *                 eigensolve in FP64. Dot products and norms: each thread accumulates its
+ *                 products as a compensated FP32 pair (exact product by FMA, error-free
+ *                 sums: the Dot2 scheme of Ogita, Rump & Oishi 2005, about twice FP32
+ *                 precision), converted to FP64 once per thread and summed in FP64 across
+ *                 threads and CTAs.
  *  ED_F64_NATIVE  FP64 vectors and FP64 arithmetic throughout (the plain method).
  *  ED_C32         complex vectors (interleaved re, im) of FP32 pairs, complex FP32 H.v
  *                 arithmetic; a_j, b_j (real for Hermitian H), dot products and the
@@ -96,7 +100,20 @@ typedef struct {
  *  max_steps  Krylov dimension cap m (1..ED_MAX_STEPS).
  *  tol        stop when |E0(j) - E0(j-1)| <= tol * max(|E0(j)|, 1) (E0(j) = lowest
  *             eigenvalue of T_j); tol <= 0 runs exactly max_steps steps.
- *  reorth     0 = none (Algorithm 1 as printed). Other values are reserved.
+ *  reorth     0 = none (Algorithm 1 as printed, two work vectors).
+ *             1 = full: the run stores every Lanczos vector f_1..f_m on the device (in the
+ *                 run's own storage: FP32, FP64 or int64 fixed point) and, at every step,
+ *                 removes from q = w - a_j f_j its components along f_1..f_j by two passes
+ *                 of classical Gram-Schmidt; dot products in FP64 (ED_F64_NATIVE),
+ *                 compensated FP32 summed in FP64 (ED_F32) or exact integers (ED_F64).
+ *             2 = partial (Simon 1984): the level of orthogonality is estimated from the
+ *                 a_j, b_j recurrence on the device, and the same passes run only at the
+ *                 steps where it exceeds sqrt(eps) (and the step after).
+ *             Modes 1 and 2 need (max_steps + 1) stored vectors of device memory (ED_ERR_OOM
+ *             otherwise) and apply to the real dtypes only (ED_ERR_ARG for complex ones
+ *             and for ed_lanczos_solve_batched). Algorithm 1 itself (Sec. 2.2) has no
+ *             reorthogonalisation; without it, copies of converged eigenvalues appear in
+ *             T_m after many steps (E0 is unaffected).
  *  seed       SplitMix64 seed of the random start vector when f1 == NULL.
  *  dtype      see ed_dtype; f1 vectors are FP64 for ED_F64 and ED_F64_NATIVE, FP32 for
  *             ED_F32, complex pairs for ED_C32 / ED_C64. The seeded complex start vector
@@ -225,8 +242,8 @@ ed_status ed_lanczos_solve(const ed_basis* basis, const ed_params* params, const
 /* ed_lanczos_solve_batched - Algorithm 1 for n independent instances (basis i with
  * params[i], a HOST array of n) in one persistent cooperative kernel launch, captured in a
  * CUDA graph. opts apply to every instance (dtype must be ED_F32: FP32 vectors and H.v,
- * FP64 a_j, b_j, dot-product accumulation and tridiagonal solve; start vector of opts->seed
- * for every instance). The convergence test of opts is evaluated every 4 steps.
+ * dot products as for ED_F32 (compensated FP32 per thread, FP64 across threads), FP64 a_j,
+ * b_j and tridiagonal solve; start vector of opts->seed for every instance; reorth 0). The convergence test of opts is evaluated every 4 steps.
  * opts->schedule picks how instances are packed onto groups of CTAs (0..5; 5 sizes groups
  * in proportion to each instance's work); -1 lets the
  * library time every schedule on this batch with a short run and keep the fastest (cached

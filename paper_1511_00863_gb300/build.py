@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libed.so")
 SOURCES = ["ed_basis.cu", "ed_hv.cu", "ed_hv2.cu", "ed_lanczos.cu", "ed_fixed.cu", "ed_batched.cu", "ed_mlp.cu",
-           "ed_observables.cu", "ed_hvc.cu", "ed_tables.cpp"]
+           "ed_observables.cu", "ed_hvc.cu", "ed_reorth.cu", "ed_tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

@@ -607,6 +607,7 @@ extern "C" ed_status ed_lanczos_solve_batched(int32_t n, const ed_basis* const* 
   clear_error();
   ED_CHECK_ARG(n >= 1 && bases && params && o && E0, "ed_lanczos_solve_batched: bad arguments");
   ED_CHECK_ARG(o->dtype == ED_F32, "ed_lanczos_solve_batched: dtype must be ED_F32");
+  ED_CHECK_ARG(o->reorth == 0, "ed_lanczos_solve_batched: reorth must be 0 (none)");
   ED_CHECK_ARG(o->max_steps >= 1 && o->max_steps <= ED_MAX_STEPS, "max_steps out of range");
   ED_CHECK_ARG(o->schedule >= -1 && o->schedule < kNumScheds, "schedule %d out of range", o->schedule);
   cudaStream_t user = (cudaStream_t)stream;

@@ -617,7 +617,8 @@ ed_status fx_copy_in(const ed_basis* b, const FxRun& fx, const double* f1, long 
 
 ed_status fx_step(const ed_basis* b, const FxRun& fx, double t, double U, long long* const B[2],
                   int cur, int64_t ld, LzScalars* S, long long* pa, long long* pb,
-                  cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, const Hv2Plan* plan) {
+                  cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, const Hv2Plan* plan,
+                  const Reorth* ro) {
   fx_plan_kernel<<<1, 32, 0, s>>>(S, cur, t, U, fx.hops, fx.nmax, fx.vb);
   if (ev0) ED_TRY_CUDA(cudaEventRecord(ev0, s));
   const FxHvArgs a = fx_args(b, ld);
@@ -642,8 +643,13 @@ ed_status fx_step(const ed_basis* b, const FxRun& fx, double t, double U, long l
   const int64_t n = b->up.dim * ld;
   const int ug = fx_red_grid(n);
   fx_update_kernel<<<ug, kFxThreads, 0, s>>>(S, cur, B[cur], B[1 - cur], n, pa, grid, pb);
+  if (ro) {
+    const ed_status r = ro_apply(ro, S, B[1 - cur], pb, ug, s);
+    if (r != ED_OK) return r;
+  }
   fx_finish_kernel<<<1, kRedThreads, 0, s>>>(S, cur, pb, ug);
   ED_TRY_CUDA(cudaGetLastError());
+  if (ro) return ro_store(ro, S, 1 - cur, B[1 - cur], s);
   return ED_OK;
 }
 

@@ -151,6 +151,8 @@ ed_status launch_hvc(const ed_basis* b, double t, double U, const void* x, void*
 ed_status hvc_prepare(const ed_basis* b, ed_dtype dtype);
 inline bool is_complex(ed_dtype d) { return d == ED_C32 || d == ED_C64; }
 
+struct Reorth;  // stored Lanczos vectors for reorthogonalisation (ed_reorth.cu)
+
 // FP64-accurate Lanczos path (int64 fixed point, ed_fixed.cu).
 struct FxRun {
   int vb;      // vector bound exponent: |X| <= 2^vb
@@ -170,7 +172,8 @@ ed_status fx_copy_in(const ed_basis* b, const FxRun& fx, const double* f1, long 
 // One step of Algorithm 1 on the fixed-point buffers (cur holds f_j, the other f_{j-1}).
 ed_status fx_step(const ed_basis* b, const FxRun& fx, double t, double U, long long* const B[2],
                   int cur, int64_t ld, LzScalars* S, long long* pa, long long* pb,
-                  cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, const struct Hv2Plan* plan);
+                  cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, const struct Hv2Plan* plan,
+                  const Reorth* ro = nullptr);
 ed_status fx_prepare(const ed_basis* b);
 // Ground-state vector (ed_lanczos_ground_state): P += round(y_j scale[cur] 2^60 X_cur),
 // and the final normalised, sign-gauged FP64 vector. part: >= 6 * 4 * sm_count longs.
@@ -179,6 +182,20 @@ ed_status fx_psi_accum(const ed_basis* b, const LzScalars* S, int cur, const dou
                        cudaStream_t s);
 ed_status fx_psi_finish(const ed_basis* b, const long long* P, long long* part, double* out,
                         cudaStream_t s);
+
+// Reorthogonalisation of the Lanczos residual (ed_reorth.cu; ed_opts.reorth 1 = full,
+// 2 = partial): the run keeps every Lanczos vector on the device.
+ed_status ro_create(int mode, ed_dtype dtype, int64_t n, int max_steps, int64_t dim, Reorth** out);
+void ro_free(Reorth* r);
+ed_status ro_prepare(const Reorth* r);
+// Start of a run: clear the estimates, store f_1 (buffer 0).
+ed_status ro_reset(const Reorth* r, const LzScalars* S, const void* buf0, cudaStream_t s);
+// After the finish pass: store f_{j+1} (buffer buf, scale S->scale[buf]) in slot S->j.
+ed_status ro_store(const Reorth* r, const LzScalars* S, int buf, const void* src, cudaStream_t s);
+// Between the update pass (residual Q, its partial norm records pb[nb]) and the finish pass.
+ed_status ro_apply(const Reorth* r, const LzScalars* S, void* Q, void* pb, int nb, cudaStream_t s);
+// Number of steps reorthogonalised so far in the current run (synchronises s).
+ed_status ro_count(const Reorth* r, cudaStream_t s, int* count);
 
 // Lanczos-fused H.v on the library's padded vectors (ed_hv2.cu). hv2_build leaves *out
 // NULL when no variant fits in shared memory (the general kernels are used then).

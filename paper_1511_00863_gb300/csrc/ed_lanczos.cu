@@ -225,6 +225,7 @@ struct ed_lanczos {
   bool fx = false;     // ED_F64: int64 fixed-point buffers (ed_fixed.cu)
   FxRun fxr{};
   Hv2Plan* plan = nullptr;  // fused H.v on the padded layout (ed_hv2.cu), if it fits
+  Reorth* ro = nullptr;     // stored Lanczos vectors when opts.reorth != 0 (ed_reorth.cu)
   cudaGraphExec_t graph = nullptr;
 };
 
@@ -235,7 +236,7 @@ static ed_status lz_launch_step(ed_lanczos* st, const ed_params* p, cudaStream_t
   if (st->fx) {
     long long* const B[2] = {(long long*)st->B[0], (long long*)st->B[1]};
     ed_status r = fx_step(b, st->fxr, p->t, p->U, B, c, st->ld, st->S, (long long*)st->pa,
-                          (long long*)st->pb, s, ev0, ev1, st->plan);
+                          (long long*)st->pb, s, ev0, ev1, st->plan, st->ro);
     if (r == ED_OK) st->cur = 1 - c;
     return r;
   }
@@ -269,8 +270,10 @@ static ed_status lz_launch_step(ed_lanczos* st, const ed_params* p, cudaStream_t
     lz_update_kernel<float><<<ug, kRedThreads, 0, s>>>(
         st->S, c, (const float*)st->B[c], (float*)st->B[1 - c], ns, st->pa, grid, st->pb);
   ED_TRY_CUDA(cudaGetLastError());
+  if (st->ro && (r = ro_apply(st->ro, st->S, st->B[1 - c], st->pb, ug, s)) != ED_OK) return r;
   lz_finish_kernel<<<1, kRedThreads, 0, s>>>(st->S, c, st->pb, ug);
   ED_TRY_CUDA(cudaGetLastError());
+  if (st->ro && (r = ro_store(st->ro, st->S, 1 - c, st->B[1 - c], s)) != ED_OK) return r;
   st->cur = 1 - c;
   return ED_OK;
 }
@@ -282,7 +285,10 @@ static ed_status check_opts(const ed_opts* o) {
   ED_CHECK_ARG(o->dtype == ED_F64 || o->dtype == ED_F32 || o->dtype == ED_F64_NATIVE ||
                    is_complex(o->dtype),
                "unknown dtype %d", (int)o->dtype);
-  ED_CHECK_ARG(o->reorth == 0, "reorth = %d is not supported (0 = none)", o->reorth);
+  ED_CHECK_ARG(o->reorth >= 0 && o->reorth <= 2, "reorth = %d outside 0 (none), 1 (full), 2 (partial)",
+               o->reorth);
+  ED_CHECK_ARG(o->reorth == 0 || !is_complex(o->dtype),
+               "reorthogonalisation is available for the real dtypes only");
   ED_CHECK_ARG(std::isfinite(o->tol), "tol is not finite");
   return ED_OK;
 }
@@ -380,6 +386,7 @@ extern "C" void ed_lanczos_destroy(ed_lanczos* st) {
   if (st->stream) cudaStreamSynchronize(st->stream);
   if (st->graph) cudaGraphExecDestroy(st->graph);
   if (st->plan) hv2_free(st->plan);
+  if (st->ro) ro_free(st->ro);
   for (int i = 0; i < 2; ++i)
     if (st->B[i]) cudaFree(st->B[i]);
   if (st->S) cudaFree(st->S);
@@ -427,6 +434,10 @@ static ed_status lz_alloc(const ed_basis* b, const ed_opts* o, cudaStream_t s, e
                 (long long)(st->n * st->esize));
       return fail(ED_ERR_OOM);
     }
+  }
+  if (o->reorth != 0) {
+    const ed_status rr = ro_create(o->reorth, o->dtype, st->n, o->max_steps, b->dim, &st->ro);
+    if (rr != ED_OK) return fail(rr);
   }
   if (cudaMalloc((void**)&st->S, sizeof(LzScalars)) != cudaSuccess ||
       cudaMalloc((void**)&st->pa, st->npa * sizeof(double)) != cudaSuccess ||
@@ -489,11 +500,13 @@ static ed_status lz_reset(ed_lanczos* st, const ed_opts* o, const void* f1, int 
   st->cur = 0;
   const int32_t* colpos = hv2_colpos(st->plan);  // NULL: rank order (general kernels)
   if (st->fx) {
-    return f1 == nullptr
+    const ed_status r = f1 == nullptr
         ? fx_start(b, st->fxr, o->seed, (long long*)st->B[0], st->ld, colpos, st->S,
                    (long long*)st->pb, s)
         : fx_copy_in(b, st->fxr, (const double*)f1, (long long*)st->B[0], st->ld, colpos, st->S,
                      (long long*)st->pb, s);
+    if (r != ED_OK || !st->ro) return r;
+    return ro_reset(st->ro, st->S, st->B[0], s);
   }
   if (f1 == nullptr) {
     start_norm_kernel<<<g, kRedThreads, 0, s>>>(o->seed, dim, st->pb);
@@ -518,6 +531,7 @@ static ed_status lz_reset(ed_lanczos* st, const ed_opts* o, const void* f1, int 
     set_error("Lanczos init: %s", cudaGetErrorString(e));
     return ED_ERR_CUDA;
   }
+  if (st->ro) return ro_reset(st->ro, st->S, st->B[0], s);
   return ED_OK;
 }
 
@@ -707,7 +721,7 @@ struct SolveCache {
   std::mutex mu;
   cudaStream_t stream = nullptr;
   struct Entry {
-    int dtype, schedule;
+    int dtype, schedule, reorth, slots;  // slots: stored vectors (reorth runs), else 0
     ed_lanczos* st;
   };
   std::vector<Entry> entries;
@@ -837,11 +851,14 @@ extern "C" ed_status ed_lanczos_solve(const ed_basis* b, const ed_params* p, con
   cudaEventDestroy(ev);
   ed_lanczos* st = nullptr;
   if (cached) {
+    const int slots = o->reorth ? o->max_steps : 0;
     for (auto& e : C->entries)
-      if (e.dtype == (int)o->dtype && e.schedule == o->schedule) st = e.st;
+      if (e.dtype == (int)o->dtype && e.schedule == o->schedule && e.reorth == o->reorth &&
+          e.slots >= slots)
+        st = e.st;
     if (!st) {
       if ((r = lz_alloc(b, o, s, &st)) != ED_OK) return r;
-      C->entries.push_back({(int)o->dtype, o->schedule, st});
+      C->entries.push_back({(int)o->dtype, o->schedule, o->reorth, slots, st});
     }
     return solve_on(st, b, p, o, f1, E0, steps, alpha, beta, E0_hist);
   }
