@@ -124,6 +124,55 @@ def test_mlp_inference_vs_oracle(ed, fill):
         ed.ed_basis_destroy(b)
 
 
+def test_mlp_inference_vs_unrounded_forward(ed):
+    """The network evaluated with bfloat16 weights but without rounding the first layer's
+    output or the U input (the plain definition of the network on rounded parameters)
+    against the GPU's tensor-core inference, which feeds the second layer bfloat16
+    activations and bfloat16(U/8): the difference must stay inside the bound those two
+    roundings (relative 2^-8 at most, taken twice as a margin) propagate through the
+    layers (tanh is 1-Lipschitz), plus FP32 accumulation at every layer."""
+    L, U = 8, 2.5
+    nu, nd = 3, 4
+    b = ed.ed_build_basis(L, ed_inputs.ring_bonds(L), nu, nd)
+    net = ed.ed_mlp_create(L, 13)
+    try:
+        dim = ed.ed_basis_dims(b)[2]
+        P = omlp.param_count(L)
+        params = (np.random.default_rng(6).normal(size=P) * 0.3).astype(np.float32)
+        _set_params(ed, net, params)
+        out = torch.empty(dim, dtype=torch.float64, device="cuda")
+        ed.ed_mlp_infer(net, b, U, out)
+        got = out.cpu().numpy()
+    finally:
+        ed.ed_mlp_destroy(net)
+        ed.ed_basis_destroy(b)
+    up = obasis.species_states(L, nu)
+    dn = obasis.species_states(L, nd)
+    g = np.arange(dim)
+    x = omlp.features(up[g // len(dn)], dn[g % len(dn)], L, U, round_inputs=False)
+    pr = omlp.bf16_round(params)            # bfloat16 weights, used as given below
+    a, z, (_, h1, h2) = omlp.forward(pr, x, L, round_weights=False)
+    W1, b1, W2, b2, W3, b3 = omlp.unpack(pr, L)
+    u = 2.0 ** -8
+    f32 = 1e-5                                                     # FP32 sums and tanhf
+    dh1 = np.abs(W1[2 * L]) * abs(U / 8.0) * u                  # bf16(U/8)
+    dh1 = dh1[None, :] + f32 * (np.abs(x) @ np.abs(W1) + np.abs(b1)[None, :])
+    dh1 = dh1 + (np.abs(h1) + dh1) * u                           # bf16(h1)
+    dh2 = dh1 @ np.abs(W2) + f32 * (np.abs(h1) @ np.abs(W2) + np.abs(b2)[None, :])
+    acc = f32 * (np.abs(h2) @ np.abs(W3) + np.abs(b3)[None, :])
+    da = dh2 @ np.abs(W3[:, 0]) + acc[:, 0]
+    dz = dh2 @ np.abs(W3[:, 1]) + acc[:, 1]
+    sure = np.abs(z) > dz
+    assert sure.mean() > 0.5
+    assert np.all(np.sign(got[sure]) == np.where(z[sure] >= 0, 1.0, -1.0))
+    err = np.abs(np.log(np.abs(got)) - a)
+    assert np.all(err <= da), float(np.max(err / da))
+    # the bound adds every rounding with the worst sign; actual roundings are of random sign
+    # (on the CPU, the oracle's rounded forward pass sits at a median of 0.3% of the bound)
+    assert np.median(err / da) < 0.05
+    assert np.median(err) > 0.0   # the roundings are really there: not a tautology
+
+
 def test_learned_start_saves_iterations(ed):
     """Train on ground states at U = 0, 1, ..., 8 of the L=10 ring at 5/5 (dim 63504), start
     Algorithm 1 from the network's prediction at held-out U: same E0 (oracle tolerance),

@@ -4,7 +4,10 @@ ed_start_vector_noalloc serves callers that must not allocate device memory whil
 run (an application whose memory pool owns the device, or a latency-critical loop that
 cannot accept an allocation's synchronisation). Its scratch is a static device array that
 every call reuses, so this test makes two calls in a row, with different sizes and seeds,
-and compares each with ed_start_vector on the same inputs. This file is collected last.
+and compares each with ed_start_vector on the same inputs. Both entry points run the same
+kernels with the same launch shape, so the outputs must agree bit for bit: a stale or
+overlapping scratch slot would change the norm and show up in every element. This file is
+collected last.
 """
 import numpy as np
 import pytest
@@ -12,23 +15,18 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-EPS64 = 2.0 ** -53
-EPS32 = 2.0 ** -24
-
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_noalloc_start_vector_matches_allocating_entry_point(dtype):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import paper_1511_00863_gb300 as ed
-    eps = EPS64 if dtype == torch.float64 else EPS32
     for n, seed in ((1_000_003, 11), (4099, 12)):   # two calls in a row, shrinking size
         ref = torch.empty(n, dtype=dtype, device="cuda")
         got = torch.full((n,), float("nan"), dtype=dtype, device="cuda")
         ed.ed_start_vector(n, seed, ref)
         ed.ed_start_vector_noalloc(n, seed, got)
         torch.cuda.synchronize()
-        r = ref.double().cpu().numpy()
         g = got.double().cpu().numpy()
         assert np.all(np.isfinite(g))
-        assert np.all(np.abs(g - r) <= 2 * eps * np.abs(r))
+        assert torch.equal(got, ref)
