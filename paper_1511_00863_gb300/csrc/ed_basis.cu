@@ -22,6 +22,19 @@ void set_error(const char* fmt, ...) {
 }
 void clear_error() { g_err[0] = 0; }
 
+int smem_optin_max() {
+  static int cache[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!cache[dev]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cache[dev] = v > 0 ? v : 48 * 1024;
+  }
+  return cache[dev];
+}
+
 int sm_count() {
   static int cache[64] = {0};
   int dev = 0;

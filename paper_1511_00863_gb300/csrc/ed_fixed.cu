@@ -576,11 +576,9 @@ ed_status fx_psi_finish(const ed_basis* b, const long long* P, long long* part, 
 ed_status fx_prepare(const ed_basis* b) {
   const int R = fx_rows(b);
   if (R == 2)
-    ED_TRY_CUDA(cudaFuncSetAttribute(fx_hv_staged_kernel<2>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fx_smem<2>(b)));
+    ED_TRY_CUDA(allow_max_smem(fx_hv_staged_kernel<2>));
   if (R == 1)
-    ED_TRY_CUDA(cudaFuncSetAttribute(fx_hv_staged_kernel<1>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fx_smem<1>(b)));
+    ED_TRY_CUDA(allow_max_smem(fx_hv_staged_kernel<1>));
   return ED_OK;
 }
 

@@ -220,10 +220,8 @@ ed_status launch_hv(const ed_basis* b, double t, double U, const T* x, T* y, int
 template <typename T, int R>
 static ed_status set_smem_attr(const ed_basis* b) {
   const int sm = (int)staged_smem<T, R>(b);
-  ED_TRY_CUDA(cudaFuncSetAttribute(hv_staged_kernel<T, R, false>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  ED_TRY_CUDA(cudaFuncSetAttribute(hv_staged_kernel<T, R, true>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  ED_TRY_CUDA(allow_max_smem(hv_staged_kernel<T, R, false>));
+  ED_TRY_CUDA(allow_max_smem(hv_staged_kernel<T, R, true>));
   return ED_OK;
 }
 
@@ -240,8 +238,11 @@ ed_status hv_prepare(const ed_basis* b, ed_dtype dtype) {
 }
 
 int64_t hv_max_grid(const ed_basis* b) {
-  const int64_t staged = b->up.dim;  // R >= 1 rows per CTA
-  const int64_t g = global_grid(b);
+  // row-staged kernels (real, complex, fixed point, fused): at most one CTA per up row;
+  // element-parallel kernels of every path: at most 8 CTAs per SM (the fixed-point general
+  // kernel launches twice its reduction grid, <= 2 x 4 per SM)
+  const int64_t staged = b->up.dim;
+  const int64_t g = (int64_t)sm_count() * 8;
   return staged > g ? staged : g;
 }
 

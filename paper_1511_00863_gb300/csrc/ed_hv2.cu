@@ -223,14 +223,12 @@ ed_status hv2_build(const ed_basis* b, int mode, int ld, int schedule, cudaStrea
   cudaError_t e = cudaSuccess;
 #define HV2_ATTR(K, E, R_, V, T, MB)                                                     \
   if (kind == K)                                                                          \
-    e = cudaFuncSetAttribute(hv2_kernel<E, R_, V, T, MB>,                                 \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ki.smem);
+    e = allow_max_smem(hv2_kernel<E, R_, V, T, MB>);
   HV2_KINDS(HV2_ATTR)
 #undef HV2_ATTR
 #define HV2C_ATTR(K, R_, V, T, MB)                                                         \
   if (kind == K)                                                                          \
-    e = cudaFuncSetAttribute(hv2c_kernel<R_, V, T, MB>,                                   \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ki.smem);
+    e = allow_max_smem(hv2c_kernel<R_, V, T, MB>);
   HV2C_KINDS(HV2C_ATTR)
 #undef HV2C_ATTR
   if (e != cudaSuccess) {

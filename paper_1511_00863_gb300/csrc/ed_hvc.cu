@@ -294,11 +294,11 @@ template <typename T>
 static ed_status hvc_prepare_t(const ed_basis* b) {
   const int R = hvc_rows<T>(b);
   if (R == 2) {
-    ED_TRY_CUDA(cudaFuncSetAttribute(hvc_staged_kernel<T, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hvc_smem<T, 2>(b)));
-    ED_TRY_CUDA(cudaFuncSetAttribute(hvc_staged_kernel<T, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hvc_smem<T, 2>(b)));
+    ED_TRY_CUDA(allow_max_smem(hvc_staged_kernel<T, 2, true>));
+    ED_TRY_CUDA(allow_max_smem(hvc_staged_kernel<T, 2, false>));
   } else if (R == 1) {
-    ED_TRY_CUDA(cudaFuncSetAttribute(hvc_staged_kernel<T, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hvc_smem<T, 1>(b)));
-    ED_TRY_CUDA(cudaFuncSetAttribute(hvc_staged_kernel<T, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hvc_smem<T, 1>(b)));
+    ED_TRY_CUDA(allow_max_smem(hvc_staged_kernel<T, 1, true>));
+    ED_TRY_CUDA(allow_max_smem(hvc_staged_kernel<T, 1, false>));
   }
   return ED_OK;
 }

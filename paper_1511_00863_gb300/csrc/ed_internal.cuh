@@ -93,6 +93,20 @@ constexpr int64_t kMinRowsStaged = 64;
 
 // Number of SMs of the current device (cached per device).
 int sm_count();
+// Largest dynamic shared memory a CTA may opt in to on the current device (cached).
+int smem_optin_max();
+// Allow `kernel` the device's whole opt-in dynamic shared memory. The attribute is global
+// to the kernel, not to a launch: setting it to one basis's need would make the captured
+// graphs of a basis that needs more fail, so it is only ever raised to the maximum.
+template <typename K>
+inline cudaError_t allow_max_smem(K kernel) {
+  cudaFuncAttributes fa;
+  const cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  // the opt-in limit covers the kernel's static shared memory too
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem_optin_max() - (int)fa.sharedSizeBytes);
+}
 
 // Free the solve workspaces cached on a basis (called by ed_basis_destroy).
 void lz_cache_free(const ed_basis* b);
@@ -196,6 +210,10 @@ ed_status ro_store(const Reorth* r, const LzScalars* S, int buf, const void* src
 ed_status ro_apply(const Reorth* r, const LzScalars* S, void* Q, void* pb, int nb, cudaStream_t s);
 // Number of steps reorthogonalised so far in the current run (synchronises s).
 ed_status ro_count(const Reorth* r, cudaStream_t s, int* count);
+// Ritz vector psi = sum_{k<m} y_{k+1} f_{k+1} of a run with stored FP32 vectors, written as
+// a dense FP64 vector in rank order (y: device, 1-based; colpos: column of each down rank).
+ed_status ro_ritz_vector(const Reorth* r, const double* y, int m, int64_t dim, int64_t cols,
+                         int64_t ld, const int32_t* colpos, double* psi, cudaStream_t s);
 
 // Lanczos-fused H.v on the library's padded vectors (ed_hv2.cu). hv2_build leaves *out
 // NULL when no variant fits in shared memory (the general kernels are used then).
@@ -217,7 +235,8 @@ ed_status hv2_autotune(const ed_basis* b, int mode, int ld, void* x, void* y,
 ed_status hv2_launch(const Hv2Plan* p, const ed_basis* b, double t, double U, const void* x,
                      void* y, const LzScalars* S, int cur, void* partial, cudaStream_t s);
 
-// Upper bound on the number of CTAs launch_hv uses (size of the partial-sum buffer).
+// Upper bound on the number of CTAs of any H.v launch of a Lanczos step (launch_hv,
+// launch_hvc, the fixed-point kernels, the fused plans): the size of the partial-sum buffer.
 int64_t hv_max_grid(const ed_basis* b);
 
 // ---------------------------------------------------------------- reductions

@@ -505,7 +505,7 @@ ed_status mlp_grad(ed_mlp* M, const ed_basis* b, double U, const int64_t* idx, c
                    int64_t n, double wscale, int adam, float lr) {
   cudaStream_t s = M->stream;
   const size_t sm = grad_smem(M->d);
-  ED_TRY_CUDA(cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  ED_TRY_CUDA(allow_max_smem(mlp_grad_kernel));
   mlp_grad_kernel<<<M->ncta, kMThreads, sm, s>>>(M->params, M->L, (float)U, b->user_up().bits,
                                                   b->user_dn().bits, b->user_dn().dim, idx, tgt, n,
                                                   wscale, M->partial, M->lpart);
@@ -633,12 +633,12 @@ extern "C" ed_status ed_mlp_infer(ed_mlp* M, const ed_basis* b, double U, ed_dty
   const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sm_count() * 3);
   ED_TRY_CUDA(cudaMemsetAsync(M->err, 0, sizeof(int), M->stream));
   if (dtype == ED_F32) {
-    ED_TRY_CUDA(cudaFuncSetAttribute(mlp_infer_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    ED_TRY_CUDA(allow_max_smem(mlp_infer_tc_kernel<float>));
     mlp_infer_tc_kernel<float><<<grid, kTcRows, sm, M->stream>>>(
         M->params, M->L, (float)U, b->user_up().bits, b->user_dn().bits, b->user_dn().dim, b->dim,
         (float*)out, M->err);
   } else {
-    ED_TRY_CUDA(cudaFuncSetAttribute(mlp_infer_tc_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    ED_TRY_CUDA(allow_max_smem(mlp_infer_tc_kernel<double>));
     mlp_infer_tc_kernel<double><<<grid, kTcRows, sm, M->stream>>>(
         M->params, M->L, (float)U, b->user_up().bits, b->user_dn().bits, b->user_dn().dim, b->dim,
         (double*)out, M->err);
