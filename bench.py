@@ -67,6 +67,64 @@ def _peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+# ----------------------------------------------------------------------------- references
+# Stored oracle energies (tests/golden, written by scripts that call only oracle/): the
+# references of every accuracy figure below, never a value the GPU produced.
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def golden_lanczos(name):
+    out = {"ab": []}
+    for line in open(os.path.join(GOLDEN, name)):
+        f = line.split()
+        if not f or f[0].startswith("#"):
+            continue
+        if f[0] == "ab":
+            out["ab"].append((float(f[2]), float(f[3])))
+        elif len(f) == 2:
+            out[f[0]] = float(f[1])
+    return out
+
+
+def golden_bethe(workload, U):
+    for line in open(os.path.join(GOLDEN, "bethe_rings.txt")):
+        f = line.split()
+        if f and not f[0].startswith("#") and f[0] == workload and abs(float(f[4]) - U) < 1e-15:
+            return float(f[5])
+    return None
+
+
+def golden_batched():
+    out = {}
+    for line in open(os.path.join(GOLDEN, "batched_E0.txt")):
+        f = line.split()
+        if f and not f[0].startswith("#"):
+            out[int(f[0])] = float(f[6])
+    return out
+
+
+def reference_E0(name, U):
+    """(E0, source) of a workload from the stored oracle values, or (None, None)."""
+    if name == "torus4x4_5_5" and U == 4.0:
+        return golden_lanczos("lanczos_torus4x4_5_5_U4.txt")["E0"], \
+            "oracle Algorithm 1, full reorthogonalisation (tests/golden/lanczos_torus4x4_5_5_U4.txt)"
+    if name == "ring12_3_3" and U == 4.0:
+        return golden_lanczos("lanczos_ring12_3_3_U4.txt")["E0"], \
+            "oracle Algorithm 1 on the explicit H (tests/golden/lanczos_ring12_3_3_U4.txt)"
+    if name.startswith("ring"):
+        E = golden_bethe(name, U)
+        if E is not None:
+            return E, "oracle Lieb-Wu Bethe-ansatz energy (tests/golden/bethe_rings.txt)"
+    return None, None
+
+
+DTYPE_LABEL = {"f64": "int64", "f64n": "f64", "f32": "f32", "c32": "f32", "c64": "f64"}
+STORAGE = {"f64": "int64 fixed point with one FP64 scale per vector (FP64-accurate: >= 53 bits "
+                  "per element relative to the vector's largest; exact hop sums and dot products)",
+           "f64n": "FP64 vectors, FP64 arithmetic", "f32": "FP32 vectors and H.v, FP64 scalars",
+           "c32": "complex FP32 vectors", "c64": "complex FP64 vectors"}
+
+
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi samples every 200 ms while the timed region runs."""
@@ -181,11 +239,12 @@ def _whole_job_rate(ws, units_per_rank, t_max_s):
     return ws * units_per_rank / t_max_s
 
 
-def _workload_config(name, dim, du, dd, dtype):
+def _workload_config(name):
     w = ed_inputs.workload(name)
+    du, dd = math.comb(w["n_sites"], w["n_up"]), math.comb(w["n_sites"], w["n_dn"])
     return {"workload": f"{name}: periodic lattice, {w['n_sites']} sites, N_up={w['n_up']}, "
                         f"N_dn={w['n_dn']}, t={w['t']}, U={w['U']}",
-            "dim": dim, "dim_up": du, "dim_dn": dd, "vector_dtype": dtype,
+            "dim": du * dd, "dim_up": du, "dim_dn": dd,
             "start": f"SplitMix64 seed {w['seed']}",
             "l2": "inputs larger than L2: two Lanczos vectors of dim elements (no flush)",
             "parallelism": "replicas (one independent Lanczos run per GPU)"}
@@ -207,31 +266,65 @@ def _timed(fn):
     return out, time.perf_counter() - t0
 
 
+def _steps_to(hist, ref, rel):
+    m = _first_within(hist, ref, rel)
+    best = float(min(abs(x - ref) for x in hist) / abs(ref)) if len(hist) else float("nan")
+    return m, best
+
+
+def _mixed_arm(ed, basis, t, U, seed, E_ref, rel, f1_fn=None):
+    """FP32 Lanczos + Ritz vector + FP64-accurate Lanczos from it (ed_lanczos_solve_mixed):
+    the fastest FP32 tolerance of (1e-8, 1e-9, 1e-10), refinement to |dE0| <= rel / 100,
+    whose E0 is within `rel` of the reference; wall time of the whole call (and of f1_fn,
+    e.g. the network's inference, when given)."""
+    best = None
+    for tol32 in (1e-8, 1e-9, 1e-10):
+        opts = ed.make_opts(max_steps=400, tol=tol32, seed=seed, dtype="f32")
+        def call():
+            f1 = f1_fn() if f1_fn else None
+            return ed.ed_lanczos_solve_mixed(basis, t, U, opts, f1=f1, refine_steps=200,
+                                             refine_tol=rel / 100, raise_not_converged=False)
+        call()   # first call on the basis allocates the FP32 state and its stored vectors
+        res, sec = _timed(call)
+        err = abs(res["E0"] - E_ref) / abs(E_ref)
+        rec = {"fp32_tol": tol32, "steps_fp32": res["steps32"], "steps_fp64": res["steps64"],
+               "refine_tol": rel / 100, "seconds": sec, "rel_err": err,
+               "rel_err_fp32_phase": abs(res["E0_fp32"] - E_ref) / abs(E_ref),
+               "residual": res["residual"]}
+        if err <= rel and (best is None or sec < best["seconds"]):
+            best = rec
+    if best is None:
+        rec["note"] = "no tolerance reached the target"
+        return rec
+    return best
+
+
 def time_to_e0_headline(ed, basis, w, rel=1e-8):
-    """Steps and wall time for E0 within `rel` of the converged FP64-accurate value, on the
-    bench workload: FP64-accurate (int64 fixed point), native FP64, FP32."""
+    """Steps and wall time to E0 within `rel` of the oracle's E0 on the bench workload:
+    FP64-accurate (int64 fixed point), native FP64 (the plain method), FP32 alone, and FP32 +
+    FP64-accurate refinement (ed_lanczos_solve_mixed)."""
     t, U, seed = w["t"], w["U"], w["seed"]
-    ref = ed.ed_lanczos_solve(basis, t, U, ed.make_opts(max_steps=800, tol=1e-14, seed=seed),
-                              raise_not_converged=False)
-    E_ref = ref["E0"]
-    out = {"E0_ref": E_ref, "rel": rel}
+    E_ref, src = reference_E0(w["name"], U)
+    out = {"E0_ref": E_ref, "E0_ref_source": src, "rel": rel}
     for name, dt in (("f64_fixed", "f64"), ("f64_native", "f64n"), ("f32", "f32")):
-        h = ref["E0_hist"] if dt == "f64" else ed.ed_lanczos_solve(
-            basis, t, U, ed.make_opts(max_steps=400, tol=0.0, seed=seed, dtype=dt),
-            raise_not_converged=False)["E0_hist"]
-        m = _first_within(h, E_ref, rel)
-        rec = {"steps": m, "best_rel_err": float(min(abs(x - E_ref) for x in h) / abs(E_ref))}
+        h = ed.ed_lanczos_solve(basis, t, U, ed.make_opts(max_steps=400, tol=0.0, seed=seed, dtype=dt),
+                                raise_not_converged=False)["E0_hist"]
+        m, best = _steps_to(h, E_ref, rel)
+        rec = {"steps": m, "best_rel_err": best}
         if m:
             _, sec = _timed(lambda: ed.ed_lanczos_solve(
                 basis, t, U, ed.make_opts(max_steps=m, tol=0.0, seed=seed, dtype=dt), history=False))
             rec["seconds"] = sec
         out[name] = rec
+    out["f32_mixed"] = _mixed_arm(ed, basis, t, U, seed, E_ref, rel)
     return out
 
 
 def learned_start_study(ed, rel=1e-8, train_steps=1500, batch=16384):
     """L14 ring 7/7: ground states at U = 0, 0.5, ..., 8 train the network; at 16 held-out U
-    compare steps/time to E0 within `rel` from the random start and from the learned start."""
+    compare steps/time to E0 within `rel` of the oracle's (Bethe-ansatz) E0 from the random
+    start and from the learned start: FP64-accurate Lanczos, native FP64 from the random
+    start (the plain method), and FP32 + FP64-accurate refinement from the learned start."""
     import numpy as np
     import torch
     w = ed_inputs.workload("ring14_7_7")
@@ -262,54 +355,57 @@ def learned_start_study(ed, rel=1e-8, train_steps=1500, batch=16384):
         f32 = torch.empty(dim, dtype=torch.float32, device="cuda")
         for U in ed_inputs.heldout_U():
             U = float(U)
-            ref = ed.ed_lanczos_solve(basis, 1.0, U, ed.make_opts(max_steps=800, tol=1e-14, seed=5),
-                                      raise_not_converged=False)
-            m_rand = _first_within(ref["E0_hist"], ref["E0"], rel)
-            ed.ed_mlp_infer(net, basis, U, f64)
-            lr_ = ed.ed_lanczos_solve(basis, 1.0, U, ed.make_opts(max_steps=800, tol=0.0, seed=5), f1=f64,
-                                      raise_not_converged=False)
-            m_lrn = _first_within(lr_["E0_hist"], ref["E0"], rel)
-            ed.ed_mlp_infer(net, basis, U, f32)
-            l32 = ed.ed_lanczos_solve(basis, 1.0, U, ed.make_opts(max_steps=400, tol=0.0, seed=5, dtype="f32"),
-                                      f1=f32, raise_not_converged=False)
-            m_32 = _first_within(l32["E0_hist"], ref["E0"], 1e-6)
-            if not (m_rand and m_lrn):
-                recs.append({"U": U, "steps_random": m_rand, "steps_learned": m_lrn, "s_random": float("nan"),
-                             "s_learned": float("nan")})
-                continue
-            _, t_rand = _timed(lambda: ed.ed_lanczos_solve(basis, 1.0, U, ed.make_opts(max_steps=m_rand, tol=0.0, seed=5),
-                                                           history=False))
-            def _lrn():
-                ed.ed_mlp_infer(net, basis, U, f64)
-                return ed.ed_lanczos_solve(basis, 1.0, U, ed.make_opts(max_steps=m_lrn, tol=0.0, seed=5), f1=f64,
-                                           history=False)
-            _, t_lrn = _timed(_lrn)
-            r = {"U": U, "steps_random": m_rand, "steps_learned": m_lrn, "s_random": t_rand, "s_learned": t_lrn,
-                 "f32_learned_steps_to_1e-6": m_32,
-                 "f32_learned_best_rel_err": float(np.min(np.abs(l32["E0_hist"] - ref["E0"])) / abs(ref["E0"]))}
-            if m_32:
-                def _l32():
-                    ed.ed_mlp_infer(net, basis, U, f32)
-                    return ed.ed_lanczos_solve(basis, 1.0, U, ed.make_opts(max_steps=m_32, tol=0.0, seed=5, dtype="f32"),
-                                               f1=f32, history=False)
-                _, r["s_f32_learned_to_1e-6"] = _timed(_l32)
+            E_ref = golden_bethe("ring14_7_7", U)
+            r = {"U": U, "E0_ref": E_ref}
+            for key, dt, learned in (("random_f64", "f64", False), ("learned_f64", "f64", True),
+                                     ("random_f64_native", "f64n", False)):
+                if learned:
+                    ed.ed_mlp_infer(net, basis, U, f64)
+                h = ed.ed_lanczos_solve(basis, 1.0, U, ed.make_opts(max_steps=400, tol=0.0, seed=5, dtype=dt),
+                                        f1=f64 if learned else None, raise_not_converged=False)["E0_hist"]
+                m, best = _steps_to(h, E_ref, rel)
+                r["steps_" + key], r["best_rel_err_" + key] = m, best
+                if m:
+                    def _call():
+                        if learned:
+                            ed.ed_mlp_infer(net, basis, U, f64)
+                        return ed.ed_lanczos_solve(basis, 1.0, U, ed.make_opts(max_steps=m, tol=0.0, seed=5, dtype=dt),
+                                                   f1=f64 if learned else None, history=False)
+                    _, r["s_" + key] = _timed(_call)
+                else:
+                    r["s_" + key] = float("nan")
+            def _infer32():
+                ed.ed_mlp_infer(net, basis, U, f32)
+                return f32
+            mx = _mixed_arm(ed, basis, 1.0, U, 5, E_ref, rel, f1_fn=_infer32)
+            r["learned_f32_mixed"] = mx
+            r["s_learned_f32_mixed"] = mx["seconds"] if mx["rel_err"] <= rel else float("nan")
             recs.append(r)
         mean = lambda k: float(np.nanmean([np.nan if r[k] is None else r[k] for r in recs]))
         return {"workload": "ring14_7_7 (dim 11,778,624), train U = 0, 0.5, ..., 8; 16 held-out U",
+                "E0_ref_source": "oracle Lieb-Wu Bethe-ansatz energy per held-out U (tests/golden/bethe_rings.txt)",
                 "ground_states_s": t_gs, "train_s": t_train, "train_steps": train_steps, "batch": batch,
                 "final_loss": float(np.mean(losses[-17:])), "rel": rel,
-                "mean_steps_random": mean("steps_random"), "mean_steps_learned": mean("steps_learned"),
-                "mean_s_random": mean("s_random"), "mean_s_learned": mean("s_learned"),
+                "mean_steps_random_f64": mean("steps_random_f64"),
+                "mean_steps_learned_f64": mean("steps_learned_f64"),
+                "mean_s_random_f64": mean("s_random_f64"), "mean_s_learned_f64": mean("s_learned_f64"),
+                "mean_s_random_f64_native": mean("s_random_f64_native"),
+                "mean_s_learned_f32_mixed": mean("s_learned_f32_mixed"),
+                "all_learned_f32_mixed_within_rel": bool(all(r["learned_f32_mixed"]["rel_err"] <= rel for r in recs)),
                 "per_U": recs}
     finally:
         ed.ed_mlp_destroy(net)
         ed.ed_basis_destroy(basis)
 
 
-def batched_study(ed):
-    """256 instances: one batched FP32 launch vs sequential FP64-accurate solves."""
+def batched_study(ed, rel=1e-8):
+    """256 instances: one batched FP32 launch; sequential FP64-accurate solves; sequential
+    FP32 + FP64-accurate refinement solves. Errors against the oracle's E0 of every
+    instance."""
     import numpy as np
     insts = ed_inputs.batched_instances()
+    ref = golden_batched()
+    E_ref = np.array([ref[i] for i in range(len(insts))])
     bases = [ed.ed_build_basis(w["n_sites"], w["bonds"], w["n_up"], w["n_dn"]) for w in insts]
     try:
         ts = [w["t"] for w in insts]
@@ -320,40 +416,159 @@ def batched_study(ed):
         def _seq():
             return [ed.ed_lanczos_solve(b, t, U, ed.make_opts(max_steps=600, tol=1e-12, seed=4),
                                         raise_not_converged=False)["E0"] for b, t, U in zip(bases, ts, Us)]
-        # first solve on each basis (state allocation, H.v plan, graph capture), then again
-        ref, t_cold = _timed(_seq)
-        ref2, t_s = _timed(_seq)
-        ref = np.array(ref)
-        err = np.abs(res["E0"] - ref) / np.maximum(1.0, np.abs(ref))
+        seq, t_cold = _timed(_seq)      # first solve on each basis (allocation, plan, graph)
+        seq2, t_s = _timed(_seq)
+        mopts = ed.make_opts(max_steps=300, tol=1e-9, seed=4, dtype="f32")
+        def _mixed():
+            return [ed.ed_lanczos_solve_mixed(b, t, U, mopts, refine_steps=300, refine_tol=rel / 100,
+                                              raise_not_converged=False)["E0"]
+                    for b, t, U in zip(bases, ts, Us)]
+        _mixed()
+        mix, t_m = _timed(_mixed)
+        rerr = lambda E: np.abs(np.asarray(E) - E_ref) / np.maximum(1.0, np.abs(E_ref))
+        eb, es, em = rerr(res["E0"]), rerr(seq), rerr(mix)
         return {"instances": len(insts), "sum_dim": int(sum(ed.ed_basis_dims(b)[2] for b in bases)),
+                "E0_ref_source": "oracle E0 of every instance (tests/golden/batched_E0.txt)", "rel": rel,
                 "batched_f32_s": t_b, "schedule": res["schedule"],
-                "batched_max_steps": int(res["steps"].max()), "sequential_f64_s": t_s,
-                "sequential_f64_first_solves_s": t_cold,
-                "speedup": t_s / t_b, "max_rel_err_vs_f64": float(err.max()),
-                "median_rel_err_vs_f64": float(np.median(err)),
-                "repeat_identical": bool(np.array_equal(ref, np.array(ref2)))}
+                "batched_max_steps": int(res["steps"].max()),
+                "batched_max_rel_err": float(eb.max()), "batched_median_rel_err": float(np.median(eb)),
+                "batched_frac_within_rel": float(np.mean(eb <= rel)),
+                "sequential_f64_s": t_s, "sequential_f64_first_solves_s": t_cold,
+                "sequential_f64_max_rel_err": float(es.max()),
+                "sequential_f32_mixed_s": t_m, "sequential_f32_mixed_max_rel_err": float(em.max()),
+                "speedup_batched_vs_sequential_f64": t_s / t_b,
+                "repeat_identical": bool(np.array_equal(np.array(seq), np.array(seq2)))}
     finally:
         for b in bases:
             ed.ed_basis_destroy(b)
 
 
+def _run_steps(ed, basis, w, dtype, K, W, schedule=-1):
+    """W warm-up and K timed Lanczos steps on the device: (ms per step, fused H.v ms, variant)."""
+    import torch
+    st = ed.ed_lanczos_init(basis, ed.make_opts(max_steps=ed.ED_MAX_STEPS, tol=0.0, seed=w["seed"],
+                                                dtype=dtype, schedule=schedule))
+    try:
+        variant = ed.ed_lanczos_schedule(st)
+        ed.ed_lanczos_run(st, w["t"], w["U"], W)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        hv = ed.ed_lanczos_run(st, w["t"], w["U"], K, time_hv=True)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / K, hv / K, variant
+    finally:
+        ed.ed_lanczos_destroy(st)
+
+
+def _hv_roofline(dim, du, dd, tabs, esize, hv_ms, workload, dtype, variant, t_bond=False):
+    peak, peak_kind = _peaks()
+    table_bytes = du * (tabs["maxhops_up"] * 4 + 4) + dd * (tabs["maxhops_dn"] * 4 + 4)
+    if t_bond:  # amplitude index per hop
+        table_bytes += du * tabs["maxhops_up"] * 4 + dd * tabs["maxhops_dn"] * 4
+    hv_bytes = 3 * esize * dim + table_bytes  # read f_j, read f_{j-1}, write w; + tables
+    achieved = hv_bytes / (hv_ms * 1e-3) / 1e9
+    traffic = None
+    rec = MEASURED_TRAFFIC.get((workload, dtype, variant))
+    if rec and _sources_sha256() == TRAFFIC_SOURCES_SHA256:
+        traffic = rec["bytes"]
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "kernel": (f"hv2_kernel variant {variant} (fused Lanczos H.v)" if variant > 0 else
+                       "general H.v kernels (rows too few or too long for the fused kernel)"),
+            "bytes_per_launch": hv_bytes, "launch_ms": hv_ms,
+            "peak_source": f"{peak_kind} HBM copy bandwidth"}
+
+
+def workload_record(ed, name, K=20, W=3):
+    """Step time, fused H.v roofline and E0 error against the oracle for one workload in the
+    FP32 and FP64-accurate forms (plus the FP32 + refinement form)."""
+    w = dict(ed_inputs.workload(name), name=name)
+    basis = ed.ed_build_basis(w["n_sites"], w["bonds"], w["n_up"], w["n_dn"])
+    try:
+        du, dd, dim = ed.ed_basis_dims(basis)
+        tabs = ed.ed_basis_tables(basis)
+        E_ref, src = reference_E0(name, w["U"])
+        out = {"config": _workload_config(name), "E0_ref": E_ref, "E0_ref_source": src}
+        for dt in ("f32", "f64"):
+            ms, hv, variant = _run_steps(ed, basis, w, dt, K, W)
+            res = ed.ed_lanczos_solve(basis, w["t"], w["U"],
+                                      ed.make_opts(max_steps=600, tol=1e-12 if dt == "f64" else 1e-9,
+                                                   seed=w["seed"], dtype=dt), raise_not_converged=False)
+            out[dt] = {"dtype": DTYPE_LABEL[dt], "storage": STORAGE[dt], "ms_per_step": ms, "hv_ms": hv,
+                       "roofline": _hv_roofline(dim, du, dd, tabs, 4 if dt == "f32" else 8, hv, name, dt,
+                                                variant),
+                       "E0": res["E0"], "steps": res["steps"],
+                       "E0_rel_err": abs(res["E0"] - E_ref) / abs(E_ref) if E_ref else None}
+        mx = ed.ed_lanczos_solve_mixed(basis, w["t"], w["U"], ed.make_opts(max_steps=600, tol=1e-9,
+                                                                          seed=w["seed"], dtype="f32"),
+                                       refine_steps=200, refine_tol=1e-12, raise_not_converged=False)
+        out["f32_mixed"] = {"E0": mx["E0"], "steps_fp32": mx["steps32"], "steps_fp64": mx["steps64"],
+                            "E0_rel_err": abs(mx["E0"] - E_ref) / abs(E_ref) if E_ref else None}
+        return out
+    finally:
+        ed.ed_basis_destroy(basis)
+
+
+FULL_STEP_CODE = r"""
+import os, sys, time, json
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+import ed_inputs
+from oracle import hamiltonian
+w = ed_inputs.workload(sys.argv[2])
+L, b, nu, nd, t, U = w["n_sites"], w["bonds"], w["n_up"], w["n_dn"], w["t"], w["U"]
+import math
+dim = math.comb(L, nu) * math.comb(L, nd)
+f = ed_inputs.uniform_pm1(w["seed"], dim)
+f /= np.sqrt(f @ f)
+f_prev = ed_inputs.uniform_pm1(w["seed"] + 1, dim)
+f_prev /= np.sqrt(f_prev @ f_prev)
+chunk = 1 << 20
+t0 = time.perf_counter()
+y = np.empty(dim)
+for lo in range(0, dim, chunk):   # H f by the oracle's matrix-free rows, every row
+    rows = np.arange(lo, min(lo + chunk, dim))
+    y[lo:lo + len(rows)] = hamiltonian.hv_rows(L, b, nu, nd, t, U, f, rows)
+q = y - 0.5 * f_prev              # the rest of one step of Algorithm 1
+a = float(q @ f); q -= a * f
+bn = float(np.sqrt(q @ q))
+print(json.dumps({"dim": dim, "seconds": time.perf_counter() - t0}))
+"""
+
+
+def run_oracle_full_step(workload: str) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", FULL_STEP_CODE, ROOT, workload], capture_output=True,
+                         text=True, env=env, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
 def bench_reference(args):
+    """The oracle (plain FP64 CPU code, one core) on the same workload: one full Lanczos step
+    (every row of H f by the oracle's matrix-free rows, then the vector operations of
+    Algorithm 1) measured, and W + K row-sampled steps as a cross-check."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
     w = args.workload
+    full = run_oracle_full_step(w)
     nsamp = args.ref_rows
     d = run_oracle_sample(w, nsamp, args.warmup + args.steps)
     times = d["times"][args.warmup:]
-    sps = len(times) * (nsamp / d["dim"]) / sum(times)
+    sampled = len(times) * (nsamp / d["dim"]) / sum(times)
+    sps = 1.0 / full["seconds"]
     line = {"impl": "reference", "metric": METRIC, "value": sps, "unit": "lanczos_steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 / sps, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * full["seconds"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w, "dim": d["dim"]},
+            "config": _workload_config(w),
+            "full_step_s": full["seconds"], "sampled_steps_per_s": sampled,
             "cpu_baseline": {"value": sps, "unit": "lanczos_steps/s", "cores": 1, "kind": "oracle",
-                             "sample": f"oracle matrix-free H.v rows + vector ops on {nsamp} random "
-                                       f"rows of {d['dim']} per step, scaled to full steps"},
+                             "sample": f"one full Lanczos step of the oracle (matrix-free H.v over all "
+                                       f"{d['dim']} rows + vector ops) measured; {len(times)} further "
+                                       f"steps sampled on {nsamp} random rows each as a cross-check"},
             "e2e": {"value": sps, "unit": "lanczos_steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -369,9 +584,9 @@ def bench_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    w = ed_inputs.workload(args.workload)
+    w = dict(ed_inputs.workload(args.workload), name=args.workload)
     dtype = args.dtype or w["dtype"]
-    esize = {"f64": 8, "f32": 4, "c32": 8, "c64": 16}[dtype]
+    esize = {"f64": 8, "f64n": 8, "f32": 4, "c32": 8, "c64": 16}[dtype]
     L, bonds, nu, nd, t, U = w["n_sites"], w["bonds"], w["n_up"], w["n_dn"], w["t"], w["U"]
     basis = ed.ed_build_basis(L, bonds, nu, nd, t_bond=w.get("t_bond"))
     du, dd, dim = ed.ed_basis_dims(basis)
@@ -419,7 +634,7 @@ def bench_ours(args):
             torch.complex128 if dtype == "c64" else torch.complex64).pin_memory()
     else:
         f1_host = torch.from_numpy(ed_inputs.start_vector_raw(w["seed"], dim)).to(
-            torch.float64 if dtype == "f64" else torch.float32).pin_memory()
+            torch.float32 if dtype == "f32" else torch.float64).pin_memory()
     f1_dev = torch.empty(dim, dtype=f1_host.dtype, device="cuda")
     eopts = ed.make_opts(max_steps=K, tol=0.0, seed=w["seed"], dtype=dtype, schedule=args.schedule)
 
@@ -444,30 +659,13 @@ def bench_ours(args):
     if rank != 0:
         ed.ed_basis_destroy(basis)
         return 0
-    # ---------------------------------------------------------------- roofline
-    peak, peak_kind = _peaks()
-    table_bytes = du * (tabs["maxhops_up"] * 4 + 4) + dd * (tabs["maxhops_dn"] * 4 + 4)
-    if w.get("t_bond") is not None:  # amplitude index per hop
-        table_bytes += du * tabs["maxhops_up"] * 4 + dd * tabs["maxhops_dn"] * 4
-    hv_bytes = 3 * esize * dim + table_bytes  # read f_j, read f_{j-1}, write w; + tables
-    hv_launch_ms = hv_ms / K
-    achieved = hv_bytes / (hv_launch_ms * 1e-3) / 1e9
-    traffic = None
-    rec = MEASURED_TRAFFIC.get((args.workload, dtype, variant))
-    if rec and _sources_sha256() == TRAFFIC_SOURCES_SHA256:
-        traffic = rec["bytes"]
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": (f"hv2_kernel variant {variant} (fused Lanczos H.v)" if variant > 0 else
-                           "general H.v kernels (fx_hv_global_kernel / hv_global_kernel: rows "
-                           "too few or too long for the fused kernel)"),
-                "bytes_per_launch": hv_bytes, "launch_ms": hv_launch_ms,
-                "peak_source": f"{peak_kind} HBM copy bandwidth"}
+    roofline = _hv_roofline(dim, du, dd, tabs, esize, hv_ms / K, args.workload, dtype, variant,
+                            t_bond=w.get("t_bond") is not None)
     line = {"metric": METRIC, "value": value, "unit": "lanczos_steps/s", "n_gpus": ws,
             "steps": K, "warmup": W, "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-            "config": _workload_config(args.workload, dim, du, dd, dtype),
-            "hv_ms_per_step": hv_launch_ms, "E0_after_steps": E_K, "steps_done": steps_done,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_LABEL[dtype], "data": "synthetic",
+            "config": _workload_config(args.workload), "vector_storage": STORAGE[dtype],
+            "hv_ms_per_step": hv_ms / K, "E0_after_steps": E_K, "steps_done": steps_done,
             "roofline": roofline,
             "e2e": {"value": _whole_job_rate(ws, K, e2e_s), "unit": "lanczos_steps/s",
                     "h2d_bytes_per_step": dim * esize / K, "d2h_bytes_per_step": d2h / K,
@@ -479,8 +677,30 @@ def bench_ours(args):
             # plan kernel sets the next H.v's integer coefficients
             "gpu_launches": (4 if dtype == "f64" else 3) * K,
             "clocks": clk}
-    if ws == 1 and not args.no_extras and w.get("t_bond") is None:
+    if ws == 1 and not args.no_extras and w.get("t_bond") is None and dtype == "f64":
+        # the plain method (native FP64 arithmetic) on the same workload, for comparison
+        ms_n, hv_n, _ = _run_steps(ed, basis, w, "f64n", 10, 2)
+        line["f64_native"] = {"dtype": "f64", "storage": STORAGE["f64n"], "ms_per_step": ms_n,
+                              "hv_ms": hv_n, "steps": 10}
+        E_ref, src = reference_E0(args.workload, U)
+        line["E0_check"] = {"E0_ref": E_ref, "E0_ref_source": src}
+        if E_ref is not None:
+            conv = ed.ed_lanczos_solve(basis, t, U, ed.make_opts(max_steps=600, tol=1e-12, seed=w["seed"]),
+                                       raise_not_converged=False)
+            line["E0_check"].update({"E0": conv["E0"], "steps": conv["steps"],
+                                     "rel_err": abs(conv["E0"] - E_ref) / abs(E_ref)})
         line["time_to_E0"] = time_to_e0_headline(ed, basis, w)
+        line["ring16_8_8"] = workload_record(ed, "ring16_8_8")
+        c1 = ed_inputs.workload("ring12_3_3")
+        b1 = ed.ed_build_basis(c1["n_sites"], c1["bonds"], c1["n_up"], c1["n_dn"])
+        try:
+            E1, s1 = reference_E0("ring12_3_3", 4.0)
+            r1 = ed.ed_lanczos_solve(b1, 1.0, 4.0, ed.make_opts(max_steps=200, tol=1e-12, seed=c1["seed"]),
+                                     raise_not_converged=False)
+            line["ring12_3_3"] = {"E0": r1["E0"], "steps": r1["steps"], "E0_ref": E1, "E0_ref_source": s1,
+                                  "rel_err": abs(r1["E0"] - E1) / abs(E1)}
+        finally:
+            ed.ed_basis_destroy(b1)
         line["batched"] = batched_study(ed)
         line["learned_start"] = learned_start_study(ed)
     if ws == 1 and not args.no_cpu_baseline:
@@ -489,7 +709,8 @@ def bench_ours(args):
                                 "kind": "oracle",
                                 "sample": f"{args.cpu_reps} x oracle matrix-free H.v rows + vector "
                                           f"ops on {args.cpu_rows} random rows of {d['dim']}, "
-                                          "scaled to full Lanczos steps"}
+                                          "scaled to full Lanczos steps (the reference arm measures "
+                                          "one full step)"}
     ed.ed_basis_destroy(basis)
     print(json.dumps(line), flush=True)
     return 0
@@ -502,7 +723,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="torus4x4_5_5")
-    ap.add_argument("--dtype", default=None, choices=[None, "f64", "f32", "c32", "c64"])
+    ap.add_argument("--dtype", default=None, choices=[None, "f64", "f64n", "f32", "c32", "c64"],
+                    help="f64: FP64-accurate int64 fixed point; f64n: native FP64")
     ap.add_argument("--cpu-rows", type=int, default=400000)
     ap.add_argument("--cpu-reps", type=int, default=8)
     ap.add_argument("--ref-rows", type=int, default=100000)

@@ -239,6 +239,31 @@ ed_status ed_lanczos_solve(const ed_basis* basis, const ed_params* params, const
                            const void* f1, void* stream, double* E0, int32_t* steps,
                            double* alpha, double* beta, double* E0_hist);
 
+/* ed_lanczos_solve_mixed - E0 to FP64 accuracy with most steps in FP32. Algorithm 1
+ * (Sec. 2.2) runs in FP32 (ED_F32 vectors and H.v) from f1 (an FP32 DEVICE vector of dim
+ * elements, or NULL for the seeded start vector of opts->seed) until the convergence test of
+ * opts (tol, max_steps) passes, keeping its Lanczos vectors on the device; the Ritz vector
+ * psi = sum_j y_j f_j of T_m for its lowest eigenvalue is assembled, and Algorithm 1 runs
+ * again in FP64-accurate form (ED_F64) from psi, for at most refine_steps (>= 1) steps with
+ * the convergence test |E0(j) - E0(j-1)| <= refine_tol max(|E0(j)|, 1) (refine_tol <= 0:
+ * exactly refine_steps steps). Its first step gives a_1 = psi.H psi / psi.psi, the Rayleigh
+ * quotient, free of the FP32 rounding of the first phase; the further steps improve on it
+ * from a start vector that is already close to the ground state, so the refined run needs
+ * few steps, and whatever psi is, its E0 is the FP64-accurate Lanczos value.
+ * Outputs (HOST): E0 (the refined run's E0), *steps32 and *E0_fp32 (the FP32 phase's steps
+ * and energy), *steps64 (the refined run's steps), *residual = ||H psi - a_1 psi|| / ||psi||
+ * (b_2 of the refined run; by the Kato-Temple inequality a_1 - E0_exact <= residual^2 / gap);
+ * the four are optional. Returns ED_ERR_NOT_CONVERGED (E0 still set) when the refined run
+ * reaches refine_steps with refine_tol > 0. opts->dtype must be ED_F32, opts->reorth 0, the
+ * lattice real. The FP32 phase keeps its vectors on the device: it stops after at most as
+ * many steps as fit in half the free device memory and in 96 GB, and after at most dim
+ * steps. The paper has no mixed-precision form; this is the FP32 variant's route to a
+ * 1e-8-accurate E0. Synchronises `stream`. */
+ed_status ed_lanczos_solve_mixed(const ed_basis* basis, const ed_params* params,
+                                 const ed_opts* opts, const void* f1, int32_t refine_steps,
+                                 double refine_tol, void* stream, double* E0, int32_t* steps32,
+                                 double* E0_fp32, int32_t* steps64, double* residual);
+
 /* ed_lanczos_solve_batched - Algorithm 1 for n independent instances (basis i with
  * params[i], a HOST array of n) in one persistent cooperative kernel launch, captured in a
  * CUDA graph. opts apply to every instance (dtype must be ED_F32: FP32 vectors and H.v,

@@ -68,6 +68,9 @@ _SIGS = {
     "ed_lanczos_solve": (c_int, [c_void_p, POINTER(ed_params), POINTER(ed_opts), c_void_p, c_void_p,
                                  POINTER(c_double), POINTER(c_int32), POINTER(c_double),
                                  POINTER(c_double), POINTER(c_double)]),
+    "ed_lanczos_solve_mixed": (c_int, [c_void_p, POINTER(ed_params), POINTER(ed_opts), c_void_p, c_int32,
+                                       c_double, c_void_p, POINTER(c_double), POINTER(c_int32),
+                                       POINTER(c_double), POINTER(c_int32), POINTER(c_double)]),
     "ed_lanczos_solve_batched": (c_int, [c_int32, POINTER(c_void_p), POINTER(ed_params),
                                          POINTER(ed_opts), c_void_p, POINTER(c_double),
                                          POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)]),
@@ -303,6 +306,23 @@ def ed_lanczos_solve(basis, t: float, U: float, opts: ed_opts, f1=None, stream=N
     n = steps.value
     return dict(status=s, E0=E0.value, steps=n, alpha=np.array(alpha[:n]), beta=np.array(beta[:n]),
                 E0_hist=np.array(hist[:n]) if history else None)
+
+
+def ed_lanczos_solve_mixed(basis, t: float, U: float, opts: ed_opts, f1=None, refine_steps: int = 64,
+                           refine_tol: float = 1e-12, stream=None, raise_not_converged: bool = True) -> dict:
+    """FP32 Lanczos, its Ritz vector, then FP64-accurate Lanczos from it (at most
+    refine_steps steps, convergence test refine_tol)."""
+    dim = ed_basis_dims(basis)[2]
+    p = ed_params(t, U)
+    E0, e32, res = c_double(), c_double(), c_double()
+    s32, s64 = c_int32(), c_int32()
+    s = _lib.ed_lanczos_solve_mixed(basis, byref(p), byref(opts), _ptr(f1, opts.dtype, dim), refine_steps,
+                                    refine_tol, _stream(stream), byref(E0), byref(s32), byref(e32),
+                                    byref(s64), byref(res))
+    if s < 0 and not (s == ED_ERR_NOT_CONVERGED and not raise_not_converged):
+        _check(s)
+    return dict(status=s, E0=E0.value, steps32=s32.value, E0_fp32=e32.value, steps64=s64.value,
+                residual=res.value)
 
 
 def ed_lanczos_solve_batched(bases, ts, Us, opts: ed_opts, stream=None,

@@ -12,6 +12,7 @@
 // Once the run stops (breakdown, convergence, max_steps) every later kernel returns at
 // entry; ed_lanczos_solve replays a captured two-step CUDA graph and reads the status
 // between batches of replays.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -278,15 +279,17 @@ static ed_status lz_launch_step(ed_lanczos* st, const ed_params* p, cudaStream_t
   return ED_OK;
 }
 
-static ed_status check_opts(const ed_opts* o) {
+// internal: also accept reorth = 3 (store the vectors without reorthogonalising; the FP32
+// phase of ed_lanczos_solve_mixed)
+static ed_status check_opts(const ed_opts* o, bool internal = false) {
   ED_CHECK_ARG(o != nullptr, "opts is NULL");
   ED_CHECK_ARG(o->max_steps >= 1 && o->max_steps <= ED_MAX_STEPS,
                "max_steps = %d outside [1, %d]", o->max_steps, ED_MAX_STEPS);
   ED_CHECK_ARG(o->dtype == ED_F64 || o->dtype == ED_F32 || o->dtype == ED_F64_NATIVE ||
                    is_complex(o->dtype),
                "unknown dtype %d", (int)o->dtype);
-  ED_CHECK_ARG(o->reorth >= 0 && o->reorth <= 2, "reorth = %d outside 0 (none), 1 (full), 2 (partial)",
-               o->reorth);
+  ED_CHECK_ARG(o->reorth >= 0 && o->reorth <= (internal ? 3 : 2),
+               "reorth = %d outside 0 (none), 1 (full), 2 (partial)", o->reorth);
   ED_CHECK_ARG(o->reorth == 0 || !is_complex(o->dtype),
                "reorthogonalisation is available for the real dtypes only");
   ED_CHECK_ARG(std::isfinite(o->tol), "tol is not finite");
@@ -406,7 +409,7 @@ constexpr int64_t kAutotuneMinDim = (int64_t)1 << 22;
 static ed_status lz_alloc(const ed_basis* b, const ed_opts* o, cudaStream_t s, ed_lanczos** out) {
   *out = nullptr;
   ED_CHECK_ARG(b != nullptr, "basis is NULL");
-  ed_status r = check_opts(o);
+  ed_status r = check_opts(o, true);
   if (r != ED_OK) return r;
   ED_CHECK_ARG(is_complex(o->dtype) || !b->has_tau(),
                "the lattice has complex amplitudes; use ED_C32 or ED_C64");
@@ -552,6 +555,11 @@ extern "C" ed_status ed_lanczos_init(const ed_basis* b, const ed_opts* o, const 
                                      void* stream, ed_lanczos** out) {
   clear_error();
   ED_CHECK_ARG(out != nullptr, "ed_lanczos_init: out is NULL");
+  *out = nullptr;
+  {
+    const ed_status rc = check_opts(o);
+    if (rc != ED_OK) return rc;
+  }
   ed_status r = lz_init(b, o, f1, (cudaStream_t)stream, ED_MAX_STEPS + 1, true, out);
   if (r == ED_OK)
     r = o->dtype == ED_F64 ? fx_prepare(b)
@@ -652,6 +660,10 @@ extern "C" ed_status ed_lanczos_ground_state(const ed_basis* b, const ed_params*
   clear_error();
   ED_CHECK_ARG(b && p && o && psi && E0, "ed_lanczos_ground_state: NULL argument");
   ED_CHECK_ARG(o->dtype == ED_F64, "ed_lanczos_ground_state: dtype must be ED_F64");
+  {
+    const ed_status rc = check_opts(o);
+    if (rc != ED_OK) return rc;
+  }
   ED_CHECK_ARG(aligned16(psi), "ed_lanczos_ground_state: psi must be 16-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
   ed_lanczos* st = nullptr;
@@ -816,15 +828,11 @@ static ed_status solve_on(ed_lanczos* st, const ed_basis* b, const ed_params* p,
   return ED_OK;
 }
 
-extern "C" ed_status ed_lanczos_solve(const ed_basis* b, const ed_params* p, const ed_opts* o,
-                                      const void* f1, void* stream, double* E0, int32_t* steps,
-                                      double* alpha, double* beta, double* E0_hist) {
-  clear_error();
-  ED_CHECK_ARG(b != nullptr && p != nullptr, "ed_lanczos_solve: basis or params is NULL");
-  ED_CHECK_ARG(E0 != nullptr, "ed_lanczos_solve: E0 is NULL");
-  ed_status r = check_opts(o);
-  if (r != ED_OK) return r;
-  cudaStream_t user = (cudaStream_t)stream;
+// Run fn(st) on the basis's cached state for opts o (allocated on first use), or on a
+// private state when another thread holds the cache; the work is ordered after the work
+// already queued on the caller's stream.
+template <typename Fn>
+static ed_status with_state(const ed_basis* b, const ed_opts* o, cudaStream_t user, Fn fn) {
   SolveCache* C = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_cache_mu);
@@ -843,13 +851,13 @@ extern "C" ed_status ed_lanczos_solve(const ed_basis* b, const ed_params* p, con
   const bool cached = lk.owns_lock();
   cudaStream_t s = C->stream;
   if (!cached) ED_TRY_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-  // the run starts after the work already queued on the caller's stream
   cudaEvent_t ev = nullptr;
   ED_TRY_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   cudaEventRecord(ev, user);
   cudaStreamWaitEvent(s, ev, 0);
   cudaEventDestroy(ev);
   ed_lanczos* st = nullptr;
+  ed_status r;
   if (cached) {
     const int slots = o->reorth ? o->max_steps : 0;
     for (auto& e : C->entries)
@@ -860,14 +868,112 @@ extern "C" ed_status ed_lanczos_solve(const ed_basis* b, const ed_params* p, con
       if ((r = lz_alloc(b, o, s, &st)) != ED_OK) return r;
       C->entries.push_back({(int)o->dtype, o->schedule, o->reorth, slots, st});
     }
-    return solve_on(st, b, p, o, f1, E0, steps, alpha, beta, E0_hist);
+    return fn(st);
   }
   if ((r = lz_alloc(b, o, s, &st)) != ED_OK) {
     cudaStreamDestroy(s);
     return r;
   }
-  r = solve_on(st, b, p, o, f1, E0, steps, alpha, beta, E0_hist);
+  r = fn(st);
   ed_lanczos_destroy(st);
   cudaStreamDestroy(s);
   return r;
+}
+
+extern "C" ed_status ed_lanczos_solve(const ed_basis* b, const ed_params* p, const ed_opts* o,
+                                      const void* f1, void* stream, double* E0, int32_t* steps,
+                                      double* alpha, double* beta, double* E0_hist) {
+  clear_error();
+  ED_CHECK_ARG(b != nullptr && p != nullptr, "ed_lanczos_solve: basis or params is NULL");
+  ED_CHECK_ARG(E0 != nullptr, "ed_lanczos_solve: E0 is NULL");
+  ed_status r = check_opts(o);
+  if (r != ED_OK) return r;
+  return with_state(b, o, (cudaStream_t)stream, [&](ed_lanczos* st) {
+    return solve_on(st, b, p, o, f1, E0, steps, alpha, beta, E0_hist);
+  });
+}
+
+extern "C" ed_status ed_lanczos_solve_mixed(const ed_basis* b, const ed_params* p,
+                                            const ed_opts* o, const void* f1,
+                                            int32_t refine_steps, double refine_tol, void* stream,
+                                            double* E0, int32_t* steps32, double* E0_fp32,
+                                            int32_t* steps64, double* residual) {
+  clear_error();
+  ED_CHECK_ARG(b != nullptr && p != nullptr && o != nullptr && E0 != nullptr,
+               "ed_lanczos_solve_mixed: NULL argument");
+  ed_status r = check_opts(o);
+  if (r != ED_OK) return r;
+  ED_CHECK_ARG(o->dtype == ED_F32, "ed_lanczos_solve_mixed: opts->dtype must be ED_F32");
+  ED_CHECK_ARG(o->reorth == 0, "ed_lanczos_solve_mixed: opts->reorth must be 0");
+  ED_CHECK_ARG(refine_steps >= 1 && refine_steps <= ED_MAX_STEPS,
+               "ed_lanczos_solve_mixed: refine_steps = %d outside [1, %d]", refine_steps,
+               ED_MAX_STEPS);
+  ED_CHECK_ARG(std::isfinite(refine_tol), "ed_lanczos_solve_mixed: refine_tol is not finite");
+  ED_CHECK_ARG(!b->has_tau(), "ed_lanczos_solve_mixed: real lattices only");
+  cudaStream_t user = (cudaStream_t)stream;
+  // ---- FP32 phase: Algorithm 1 with the vectors kept, then the Ritz vector in rank order
+  ed_opts o32 = *o;
+  o32.reorth = 3;
+  {
+    // the FP32 phase keeps at most as many vectors as fit in half the free device memory
+    // and in 96 GB; a shorter FP32 phase leaves more of the convergence to the refinement
+    // steps
+    size_t free_b = 0, total_b = 0;
+    ED_TRY_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const double vbytes = (double)b->up.dim * (double)((b->dn.dim + 31) / 32 * 32) * 4.0;
+    const double budget = std::min((double)free_b / 2.0, 96e9);
+    const int cap = (int)std::min(budget / vbytes - 1.0, (double)ED_MAX_STEPS);
+    ED_CHECK_ARG(cap >= 2, "ed_lanczos_solve_mixed: device memory for FP32 vectors too small");
+    if (o32.max_steps > cap) o32.max_steps = cap;
+    // beyond dim steps the FP32 recurrence only adds rounding noise
+    if ((int64_t)o32.max_steps > b->dim) o32.max_steps = (int)std::max<int64_t>(b->dim, 1);
+  }
+  double* psi = nullptr;
+  double* y = nullptr;
+  int m = 0;
+  double e32 = NAN;
+  r = with_state(b, &o32, user, [&](ed_lanczos* st) -> ed_status {
+    cudaStream_t s = st->stream;
+    ed_status rr = solve_on(st, b, p, &o32, f1, &e32, &m, nullptr, nullptr, nullptr);
+    if (rr < 0 && rr != ED_ERR_NOT_CONVERGED) return rr;
+    if (m < 1) {
+      set_error("ed_lanczos_solve_mixed: the FP32 phase took no step");
+      return ED_ERR_ARG;
+    }
+    if (cudaMallocAsync((void**)&y, (size_t)3 * (m + 2) * sizeof(double), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&psi, (size_t)b->dim * sizeof(double), s) != cudaSuccess) {
+      set_error("ed_lanczos_solve_mixed: out of device memory");
+      return ED_ERR_OOM;
+    }
+    lz_ritz_kernel<<<1, 32, 0, s>>>(st->S, m, e32, y, y + (m + 2));
+    ED_TRY_CUDA(cudaGetLastError());
+    rr = ro_ritz_vector(st->ro, y, m, b->dim, b->dn.dim, st->ld, hv2_colpos(st->plan), psi, s);
+    if (rr != ED_OK) return rr;
+    ED_TRY_CUDA(cudaStreamSynchronize(s));
+    return ED_OK;
+  });
+  auto release = [&](ed_status e) {
+    if (y) cudaFreeAsync(y, user);
+    if (psi) cudaFreeAsync(psi, user);
+    return e;
+  };
+  if (r != ED_OK) return release(r);
+  if (steps32) *steps32 = m;
+  if (E0_fp32) *E0_fp32 = e32;
+  // ---- FP64-accurate phase from psi: a_1 = psi.H psi (the Rayleigh quotient), b_2 = the
+  // residual norm, E0 = lambda_min of the refined T
+  ed_opts o64 = *o;
+  o64.dtype = ED_F64;
+  o64.max_steps = refine_steps;
+  o64.tol = refine_tol;
+  o64.schedule = -1;
+  std::vector<double> a(refine_steps), bt(refine_steps);
+  int32_t k = 0;
+  r = with_state(b, &o64, user, [&](ed_lanczos* st) {
+    return solve_on(st, b, p, &o64, psi, E0, &k, a.data(), bt.data(), nullptr);
+  });
+  if (r == ED_BREAKDOWN) r = ED_OK;
+  if (steps64) *steps64 = k;
+  if ((r == ED_OK || r == ED_ERR_NOT_CONVERGED) && residual) *residual = bt[0];
+  return release(r);
 }

@@ -44,7 +44,7 @@ struct RoFlags {
 };
 
 struct Reorth {
-  int mode = 0;        // 1 full, 2 partial
+  int mode = 0;        // 1 full, 2 partial, 3 store only (the mixed-precision solve)
   int kind = 0;        // 0 FP32, 1 FP64, 2 int64 fixed point
   int64_t n = 0;       // elements per stored vector (padded layout)
   int slots = 0;       // stored vectors (max_steps + 1)
@@ -479,20 +479,18 @@ ed_status ro_prepare(const Reorth* r) {
   const size_t csm = (size_t)r->slots * 8;
   if (csm > 48 * 1024) {
     if (r->kind == 0)
-      ED_TRY_CUDA(cudaFuncSetAttribute(ro_update_kernel<float>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
+      ED_TRY_CUDA(allow_max_smem(ro_update_kernel<float>));
     else if (r->kind == 1)
-      ED_TRY_CUDA(cudaFuncSetAttribute(ro_update_kernel<double>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
+      ED_TRY_CUDA(allow_max_smem(ro_update_kernel<double>));
     else
-      ED_TRY_CUDA(cudaFuncSetAttribute(ro_update_kernel<long long>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
+      ED_TRY_CUDA(allow_max_smem(ro_update_kernel<long long>));
   }
   return ED_OK;
 }
 
 // Between the update pass (q and its partial norms in pb, nb records) and the finish pass.
 ed_status ro_apply(const Reorth* r, const LzScalars* S, void* Q, void* pb, int nb, cudaStream_t s) {
+  if (r->mode == 3) return ED_OK;  // vectors are stored, never reorthogonalised
   ro_decide_kernel<<<1, kRoThreads, 0, s>>>(S, r->F, r->omega, r->mode, r->kind, pb, nb, r->slots,
                                             r->eps, r->psi);
   if (r->kind == 0)
@@ -501,6 +499,41 @@ ed_status ro_apply(const Reorth* r, const LzScalars* S, void* Q, void* pb, int n
     ro_passes_t<double>(r, S, Q, pb, nb, s);
   else
     ro_passes_t<long long>(r, S, Q, pb, nb, s);
+  ED_TRY_CUDA(cudaGetLastError());
+  return ED_OK;
+}
+
+// psi[i] (rank order, FP64) = sum_{k < m} y[k + 1] s_k V_k[r ld + p] for the stored FP32
+// vectors, with row r = i / cols, column c = i % cols at position p = colpos[c] (or c); the
+// coefficients y_k s_k are rounded to FP32 and the sum is accumulated in FP32.
+__global__ void __launch_bounds__(kRoThreads)
+ro_ritz_f32_kernel(const double* __restrict__ y, int m, const float* __restrict__ V,
+                   const double* __restrict__ vscale, int64_t n, int64_t dim, int64_t cols,
+                   int64_t ld, const int32_t* __restrict__ colpos, double* __restrict__ psi) {
+  extern __shared__ __align__(16) unsigned char ro_smem[];
+  float* c = reinterpret_cast<float*>(ro_smem);
+  for (int k = threadIdx.x; k < m; k += blockDim.x) c[k] = (float)(y[k + 1] * vscale[k]);
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < dim;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / cols, cc = i - r * cols;
+    const int64_t e = r * ld + (colpos ? colpos[cc] : cc);
+    float acc = 0.f;
+    for (int k = 0; k < m; ++k) acc = fmaf(c[k], V[(int64_t)k * n + e], acc);
+    psi[i] = (double)acc;
+  }
+}
+
+ed_status ro_ritz_vector(const Reorth* r, const double* y, int m, int64_t dim, int64_t cols,
+                         int64_t ld, const int32_t* colpos, double* psi, cudaStream_t s) {
+  ED_CHECK_ARG(r->kind == 0, "internal: Ritz vectors are assembled from FP32 runs only");
+  ED_CHECK_ARG(m >= 1 && m <= r->slots, "internal: Ritz vector of %d steps", m);
+  int g = (int)((dim + kRoThreads - 1) / kRoThreads);
+  const int cap = 4 * sm_count();
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  ro_ritz_f32_kernel<<<g, kRoThreads, (size_t)m * 4, s>>>(y, m, (const float*)r->V, r->vscale, r->n,
+                                                           dim, cols, ld, colpos, psi);
   ED_TRY_CUDA(cudaGetLastError());
   return ED_OK;
 }

@@ -26,7 +26,9 @@ def _json_lines(text):
     return [json.loads(l) for l in text.splitlines() if l.strip().startswith("{")]
 
 
-REF_ARGS = ["--impl", "reference", "--steps", "2", "--warmup", "1", "--ref-rows", "2000"]
+# the 12-site ring keeps the reference arm's full oracle step short on this host
+REF_ARGS = ["--impl", "reference", "--steps", "2", "--warmup", "1", "--ref-rows", "2000",
+            "--workload", "ring12_3_3"]
 
 
 def test_reference_arm_json_line():
@@ -45,6 +47,18 @@ def test_reference_arm_json_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+    # measured on one full oracle step; the same config dict as the GPU arm's
+    assert d["full_step_s"] > 0 and d["value"] == pytest.approx(1.0 / d["full_step_s"])
+    assert d["config"] == bench._workload_config("ring12_3_3")
+    assert d["config"]["dim"] == 220 * 220
+
+
+def test_reference_values_come_from_stored_oracle_results():
+    E, src = bench.reference_E0("torus4x4_5_5", 4.0)
+    assert E == pytest.approx(-19.5809375254, abs=1e-9) and "oracle" in src
+    E, src = bench.reference_E0("ring16_8_8", 4.0)
+    assert E == pytest.approx(-9.21443097198, abs=1e-9) and "Bethe" in src
+    assert len(bench.golden_batched()) == 256
 
 
 def test_reference_arm_two_ranks_prints_once():
