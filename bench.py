@@ -425,8 +425,18 @@ def batched_study(ed, rel=1e-8):
                     for b, t, U in zip(bases, ts, Us)]
         _mixed()
         mix, t_m = _timed(_mixed)
+        # the batch in FP64 (one persistent launch), and the plain method one instance at a time
+        o64 = ed.make_opts(max_steps=600, tol=1e-12, seed=4, dtype="f64n", schedule=-1)
+        ed.ed_lanczos_solve_batched(bases, ts, Us, o64, raise_not_converged=False)   # autotune
+        res64, t_b64 = _timed(lambda: ed.ed_lanczos_solve_batched(bases, ts, Us, o64, raise_not_converged=False))
+        def _seqn():
+            return [ed.ed_lanczos_solve(b, t, U, ed.make_opts(max_steps=600, tol=1e-12, seed=4, dtype="f64n"),
+                                        raise_not_converged=False)["E0"] for b, t, U in zip(bases, ts, Us)]
+        _seqn()
+        seqn, t_sn = _timed(_seqn)
         rerr = lambda E: np.abs(np.asarray(E) - E_ref) / np.maximum(1.0, np.abs(E_ref))
         eb, es, em = rerr(res["E0"]), rerr(seq), rerr(mix)
+        eb64, esn = rerr(res64["E0"]), rerr(seqn)
         return {"instances": len(insts), "sum_dim": int(sum(ed.ed_basis_dims(b)[2] for b in bases)),
                 "E0_ref_source": "oracle E0 of every instance (tests/golden/batched_E0.txt)", "rel": rel,
                 "batched_f32_s": t_b, "schedule": res["schedule"],
@@ -436,6 +446,14 @@ def batched_study(ed, rel=1e-8):
                 "sequential_f64_s": t_s, "sequential_f64_first_solves_s": t_cold,
                 "sequential_f64_max_rel_err": float(es.max()),
                 "sequential_f32_mixed_s": t_m, "sequential_f32_mixed_max_rel_err": float(em.max()),
+                "batched_f64_native_s": t_b64, "batched_f64_native_max_rel_err": float(eb64.max()),
+                "batched_f64_native_schedule": res64["schedule"],
+                "sequential_f64_native_s": t_sn, "sequential_f64_native_max_rel_err": float(esn.max()),
+                "time_to_rel": {"batched_f64_native_s": t_b64 if eb64.max() <= rel else None,
+                                "batched_f32_s": t_b if eb.max() <= rel else None,
+                                "sequential_f64_fixed_s": t_s if es.max() <= rel else None,
+                                "sequential_f64_native_s": t_sn if esn.max() <= rel else None,
+                                "sequential_f32_mixed_s": t_m if em.max() <= rel else None},
                 "speedup_batched_vs_sequential_f64": t_s / t_b,
                 "repeat_identical": bool(np.array_equal(np.array(seq), np.array(seq2)))}
     finally:

@@ -266,9 +266,10 @@ ed_status ed_lanczos_solve_mixed(const ed_basis* basis, const ed_params* params,
 
 /* ed_lanczos_solve_batched - Algorithm 1 for n independent instances (basis i with
  * params[i], a HOST array of n) in one persistent cooperative kernel launch, captured in a
- * CUDA graph. opts apply to every instance (dtype must be ED_F32: FP32 vectors and H.v,
- * dot products as for ED_F32 (compensated FP32 per thread, FP64 across threads), FP64 a_j,
- * b_j and tridiagonal solve; start vector of opts->seed for every instance; reorth 0). The convergence test of opts is evaluated every 4 steps.
+ * CUDA graph. opts apply to every instance (dtype ED_F32: FP32 vectors and H.v, dot
+ * products as for ED_F32 (compensated FP32 per thread, FP64 across threads); or
+ * ED_F64_NATIVE: FP64 vectors and H.v; FP64 a_j, b_j and tridiagonal solve either way;
+ * start vector of opts->seed for every instance; reorth 0). The convergence test of opts is evaluated every 4 steps.
  * opts->schedule picks how instances are packed onto groups of CTAs (0..5; 5 sizes groups
  * in proportion to each instance's work); -1 lets the
  * library time every schedule on this batch with a short run and keep the fastest (cached

@@ -37,8 +37,8 @@ struct BInst {
   const int32_t* hu;
   const int32_t* hd;
   int dim_up, dim_dn, mhu, mhd;
-  float* B0;
-  float* B1;
+  void* B0;  // two work vectors of the instance (FP32 or FP64 elements)
+  void* B1;
   double t, U;
 };
 
@@ -124,7 +124,8 @@ __device__ bool group_barrier(unsigned* count, unsigned* gen, int g, long long m
 
 // Loads of data that other CTAs of the group wrote during this launch go to L2 (the L1 of
 // this SM is not coherent with their stores).
-__device__ __forceinline__ float ld_shared_f(const float* p, bool multi) { return multi ? __ldcg(p) : *p; }
+template <typename T>
+__device__ __forceinline__ T ld_shared_f(const T* p, bool multi) { return multi ? __ldcg(p) : *p; }
 
 __device__ __forceinline__ double bstart_element(uint64_t seed, uint64_t i) {
   uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
@@ -146,12 +147,16 @@ __device__ __forceinline__ double group_sum(const double* part, int first, int g
   return v;
 }
 
+// T = float (ED_F32) or double (ED_F64_NATIVE): vector elements and H.v arithmetic; the
+// scalars are FP64 either way.
+template <typename T>
 __global__ void __launch_bounds__(kBThreads, 4)
 batched_lanczos_kernel(BArgs a) {
+  constexpr int kRowElems = kBSmemBytes / (int)sizeof(T);  // staged elements of a row block
   __shared__ double red[33];
   __shared__ int stop_s;
   __shared__ __align__(16) unsigned char bsm[kBSmemBytes];
-  float* xsm = reinterpret_cast<float*>(bsm);
+  T* xsm = reinterpret_cast<T*>(bsm);
   const int gi = a.group_of_cta[blockIdx.x];
   const BGroup G = a.groups[gi];
   const int c = blockIdx.x - G.first_cta, g = G.ncta;
@@ -182,8 +187,8 @@ batched_lanczos_kernel(BArgs a) {
       if (!group_barrier(bc, bg, g, a.max_spin, a.error)) return;
       const double inv = 1.0 / sqrt(group_sum(a.part_a, G.first_cta, g, red));
       for (int64_t e = t0; e < dim; e += gt) {
-        I.B0[e] = (float)(bstart_element(a.seed, (uint64_t)e) * inv);
-        I.B1[e] = 0.f;
+        ((T*)I.B0)[e] = (T)(bstart_element(a.seed, (uint64_t)e) * inv);
+        ((T*)I.B1)[e] = T(0);
       }
       if (leader && threadIdx.x == 0) {
         S->j = 0;
@@ -199,48 +204,48 @@ batched_lanczos_kernel(BArgs a) {
     }
     int cur = 0;
     for (int j = 1; j <= a.max_steps; ++j) {
-      float* xc = cur ? I.B1 : I.B0;
-      float* xp = cur ? I.B0 : I.B1;
+      T* xc = (T*)(cur ? I.B1 : I.B0);
+      T* xp = (T*)(cur ? I.B0 : I.B1);
       // ---- phase 1: fused H.v
-      const float sc = (float)__ldcg(&S->scale[cur]);
-      const float bsp = (float)(__ldcg(&be[j]) * __ldcg(&S->scale[1 - cur]));
-      const float tt = (float)I.t, UU = (float)I.U;
-      DotAcc<float> dot;
-      if (I.dim_dn <= kBRowFloats) {
+      const T sc = (T)__ldcg(&S->scale[cur]);
+      const T bsp = (T)(__ldcg(&be[j]) * __ldcg(&S->scale[1 - cur]));
+      const T tt = (T)I.t, UU = (T)I.U;
+      DotAcc<T> dot;
+      if (I.dim_dn <= kRowElems) {
         // blocks of BR consecutive up rows staged in shared memory (coalesced loads; from L2
         // when other CTAs of the group wrote them): down-hop gathers read shared memory,
         // up-hop gathers read whole neighbour rows coalesced
-        const int BR = max(1, min(kBRowFloats, 2048) / I.dim_dn);
+        const int BR = max(1, min(kRowElems, 2048) / I.dim_dn);
         const int nblk = (I.dim_up + BR - 1) / BR;
         for (int blk = c; blk < nblk; blk += g) {
           const int u0 = blk * BR;
           const int nr = min(BR, I.dim_up - u0);
           const int nel = nr * I.dim_dn;
-          const float* xb = xc + (int64_t)u0 * I.dim_dn;
+          const T* xb = xc + (int64_t)u0 * I.dim_dn;
           for (int i = threadIdx.x; i < nel; i += blockDim.x) xsm[i] = ld_shared_f(xb + i, multi);
           __syncthreads();
           for (int i = threadIdx.x; i < nel; i += blockDim.x) {
             const int r = i / I.dim_dn, d = i - r * I.dim_dn, u = u0 + r;
-            const float* xr = xsm + r * I.dim_dn;
-            float acc = 0.f;
+            const T* xr = xsm + r * I.dim_dn;
+            T acc = T(0);
             for (int k = 0; k < I.mhd; ++k) {
               const uint32_t en = (uint32_t)I.hd[(int64_t)k * I.dim_dn + d];
               const uint32_t tg = en & kTargetMask;
               if (tg >= (uint32_t)I.dim_dn) break;
-              const float v = xr[tg];
+              const T v = xr[tg];
               acc += (en & kSignBit) ? -v : v;
             }
             for (int k = 0; k < I.mhu; ++k) {
               const uint32_t en = (uint32_t)I.hu[(int64_t)k * I.dim_up + u];
               const uint32_t tg = en & kTargetMask;
               if (tg >= (uint32_t)I.dim_up) break;
-              const float v = ld_shared_f(xc + (int64_t)tg * I.dim_dn + d, multi);
+              const T v = ld_shared_f(xc + (int64_t)tg * I.dim_dn + d, multi);
               acc += (en & kSignBit) ? -v : v;
             }
-            const float xv = xsm[i];
+            const T xv = xsm[i];
             const int64_t e = (int64_t)u0 * I.dim_dn + i;
-            const float hx = fmaf(-tt, acc, UU * (float)__popc(I.upb[u] & I.dnb[d]) * xv);
-            const float w = fmaf(sc, hx, -bsp * ld_shared_f(xp + e, multi));
+            const T hx = fma(-tt, acc, UU * (T)__popc(I.upb[u] & I.dnb[d]) * xv);
+            const T w = fma(sc, hx, -bsp * ld_shared_f(xp + e, multi));
             xp[e] = w;
             dot.add(w, sc * xv);
           }
@@ -249,25 +254,25 @@ batched_lanczos_kernel(BArgs a) {
       } else {
         for (int64_t e = t0; e < dim; e += gt) {
           const int u = (int)(e / I.dim_dn), d = (int)(e - (int64_t)u * I.dim_dn);
-          const float* xr = xc + (int64_t)u * I.dim_dn;
-          float acc = 0.f;
+          const T* xr = xc + (int64_t)u * I.dim_dn;
+          T acc = T(0);
           for (int k = 0; k < I.mhd; ++k) {
             const uint32_t en = (uint32_t)I.hd[(int64_t)k * I.dim_dn + d];
             const uint32_t tg = en & kTargetMask;
             if (tg >= (uint32_t)I.dim_dn) break;
-            const float v = ld_shared_f(xr + tg, multi);
+            const T v = ld_shared_f(xr + tg, multi);
             acc += (en & kSignBit) ? -v : v;
           }
           for (int k = 0; k < I.mhu; ++k) {
             const uint32_t en = (uint32_t)I.hu[(int64_t)k * I.dim_up + u];
             const uint32_t tg = en & kTargetMask;
             if (tg >= (uint32_t)I.dim_up) break;
-            const float v = ld_shared_f(xc + (int64_t)tg * I.dim_dn + d, multi);
+            const T v = ld_shared_f(xc + (int64_t)tg * I.dim_dn + d, multi);
             acc += (en & kSignBit) ? -v : v;
           }
-          const float xv = ld_shared_f(xr + d, multi);
-          const float hx = fmaf(-tt, acc, UU * (float)__popc(I.upb[u] & I.dnb[d]) * xv);
-          const float w = fmaf(sc, hx, -bsp * ld_shared_f(xp + e, multi));
+          const T xv = ld_shared_f(xr + d, multi);
+          const T hx = fma(-tt, acc, UU * (T)__popc(I.upb[u] & I.dnb[d]) * xv);
+          const T w = fma(sc, hx, -bsp * ld_shared_f(xp + e, multi));
           xp[e] = w;
           dot.add(w, sc * xv);
         }
@@ -280,11 +285,11 @@ batched_lanczos_kernel(BArgs a) {
       // ---- phase 2: a_j, update
       const double alpha = group_sum(a.part_a, G.first_cta, g, red);
       if (leader && threadIdx.x == 0) al[j] = alpha;
-      const float coef = (float)(alpha * __ldcg(&S->scale[cur]));
-      DotAcc<float> q2;
+      const T coef = (T)(alpha * __ldcg(&S->scale[cur]));
+      DotAcc<T> q2;
       // (phase 1 wrote w by row blocks: other CTAs' values are read from L2)
       for (int64_t e = t0; e < dim; e += gt) {
-        const float q = ld_shared_f(xp + e, multi) - coef * ld_shared_f(xc + e, multi);
+        const T q = ld_shared_f(xp + e, multi) - coef * ld_shared_f(xc + e, multi);
         xp[e] = q;
         q2.add(q, q);
       }
@@ -448,7 +453,7 @@ struct BatchRun {
   std::vector<BInst> hinst;
   std::vector<int> dims;
   std::vector<long long> work;
-  float* vec = nullptr;
+  void* vec = nullptr;
   BInst* d_inst = nullptr;
   BState* d_state = nullptr;
   double* d_scal = nullptr;  // alpha | beta | E0
@@ -493,6 +498,8 @@ ed_status upload_plan(const Plan& p, PlanDev& d, cudaStream_t s) {
 // One cooperative launch of the whole batch, captured in a CUDA graph and replayed once.
 ed_status run_plan(BatchRun& R, const Plan& p, const ed_opts* o, int check, cudaStream_t s,
                    float* ms_out) {
+  const void* kernel = o->dtype == ED_F64_NATIVE ? (const void*)batched_lanczos_kernel<double>
+                                                 : (const void*)batched_lanczos_kernel<float>;
   PlanDev d;
   ed_status st = upload_plan(p, d, s);
   if (st != ED_OK) return st;
@@ -521,8 +528,7 @@ ed_status run_plan(BatchRun& R, const Plan& p, const ed_opts* o, int check, cuda
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   ED_TRY_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  cudaError_t le = cudaLaunchCooperativeKernel((const void*)batched_lanczos_kernel, p.grid,
-                                               kBThreads, args, 0, s);
+  cudaError_t le = cudaLaunchCooperativeKernel(kernel, p.grid, kBThreads, args, 0, s);
   cudaError_t ce = cudaStreamEndCapture(s, &graph);
   if (le != cudaSuccess || ce != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
@@ -606,7 +612,8 @@ extern "C" ed_status ed_lanczos_solve_batched(int32_t n, const ed_basis* const* 
                                               int32_t* status, int32_t* schedule_used) {
   clear_error();
   ED_CHECK_ARG(n >= 1 && bases && params && o && E0, "ed_lanczos_solve_batched: bad arguments");
-  ED_CHECK_ARG(o->dtype == ED_F32, "ed_lanczos_solve_batched: dtype must be ED_F32");
+  ED_CHECK_ARG(o->dtype == ED_F32 || o->dtype == ED_F64_NATIVE,
+               "ed_lanczos_solve_batched: dtype must be ED_F32 or ED_F64_NATIVE");
   ED_CHECK_ARG(o->reorth == 0, "ed_lanczos_solve_batched: reorth must be 0 (none)");
   ED_CHECK_ARG(o->max_steps >= 1 && o->max_steps <= ED_MAX_STEPS, "max_steps out of range");
   ED_CHECK_ARG(o->schedule >= -1 && o->schedule < kNumScheds, "schedule %d out of range", o->schedule);
@@ -639,7 +646,8 @@ extern "C" ed_status ed_lanczos_solve_batched(int32_t n, const ed_basis* const* 
     R.work[i] = (long long)b->dim * (b->up.maxhops + b->dn.maxhops + 4);
     total += 2 * (size_t)((b->dim + 3) / 4 * 4);
   }
-  ED_TRY_CUDA(cudaMalloc((void**)&R.vec, total * sizeof(float)));
+  const size_t esize = o->dtype == ED_F64_NATIVE ? 8 : 4;
+  ED_TRY_CUDA(cudaMalloc((void**)&R.vec, total * esize));
   size_t off = 0;
   for (int i = 0; i < n; ++i) {
     const ed_basis* b = bases[i];
@@ -653,8 +661,8 @@ extern "C" ed_status ed_lanczos_solve_batched(int32_t n, const ed_basis* const* 
     I.mhu = b->up.maxhops;
     I.mhd = b->dn.maxhops;
     const size_t dpad = (size_t)(b->dim + 3) / 4 * 4;
-    I.B0 = R.vec + off;
-    I.B1 = R.vec + off + dpad;
+    I.B0 = (char*)R.vec + off * esize;
+    I.B1 = (char*)R.vec + (off + dpad) * esize;
     off += 2 * dpad;
     I.t = params[i].t;
     I.U = params[i].U;
@@ -669,8 +677,12 @@ extern "C" ed_status ed_lanczos_solve_batched(int32_t n, const ed_basis* const* 
 
   int dev = 0, per_sm = 0;
   cudaGetDevice(&dev);
-  ED_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_lanczos_kernel,
-                                                            kBThreads, 0));
+  if (o->dtype == ED_F64_NATIVE)
+    ED_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_lanczos_kernel<double>,
+                                                              kBThreads, 0));
+  else
+    ED_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_lanczos_kernel<float>,
+                                                              kBThreads, 0));
   const int max_ctas = sm_count() * std::min(per_sm, 4);
   const int check = 4;  // E0(j) every 4 steps (and at the stop step)
   int sched = o->schedule;
@@ -678,7 +690,7 @@ extern "C" ed_status ed_lanczos_solve_batched(int32_t n, const ed_basis* const* 
     // autotune: time every candidate schedule on this batch with a short run, keep the best
     std::string key;
     for (int i = 0; i < n; ++i) key += std::to_string(R.work[i]) + ",";
-    key += std::to_string(max_ctas);
+    key += std::to_string(max_ctas) + "/" + std::to_string((int)o->dtype);
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
       auto it = g_tune_cache.find(key);

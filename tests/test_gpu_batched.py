@@ -138,3 +138,27 @@ def test_sequential_solves_of_every_instance_repeat_and_match_oracle(ed):
     E_ref = np.array([ref[i] for i in range(len(insts))])
     err = np.abs(rounds[0] - E_ref) / np.maximum(1.0, np.abs(E_ref))
     assert err.max() <= 1e-10, (int(np.argmax(err)), err.max())
+
+
+def test_batched_native_fp64_matches_oracle(ed):
+    """The batch in FP64 vectors and arithmetic (ED_F64_NATIVE) in one persistent launch:
+    every instance within 1e-10 of the oracle's E0, which the FP32 batch cannot reach."""
+    import os
+    ref = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "batched_E0.txt")):
+        f = line.split()
+        if f and not f[0].startswith("#"):
+            ref[int(f[0])] = float(f[6])
+    insts = ed_inputs.batched_instances()
+    bases = [ed.ed_build_basis(w["n_sites"], w["bonds"], w["n_up"], w["n_dn"]) for w in insts]
+    try:
+        res = ed.ed_lanczos_solve_batched(bases, [w["t"] for w in insts], [w["U"] for w in insts],
+                                          ed.make_opts(max_steps=600, tol=1e-13, seed=4, dtype="f64n",
+                                                       schedule=5),
+                                          raise_not_converged=False)
+    finally:
+        for b in bases:
+            ed.ed_basis_destroy(b)
+    E_ref = np.array([ref[i] for i in range(len(insts))])
+    err = np.abs(res["E0"] - E_ref) / np.maximum(1.0, np.abs(E_ref))
+    assert err.max() <= 1e-10, (int(np.argmax(err)), err.max())
