@@ -221,6 +221,18 @@ ed_status ed_lanczos_run(ed_lanczos* st, const ed_params* params, int32_t nsteps
 /* ed_lanczos_schedule - the fused H.v variant the state uses (0: the general kernels). */
 ed_status ed_lanczos_schedule(const ed_lanczos* st, int32_t* schedule);
 
+/* ed_lanczos_buffers - read-only DEVICE views of the state's two work vectors, for
+ * inspection and tests (no counterpart in the paper; Algorithm 1 keeps exactly these two
+ * vectors, Sec. 2.2). After step j, *f_next is the buffer of f_{j+1} and *f_cur that of
+ * f_j, each an unnormalised vector B with f = scale * B (*scale_next, *scale_cur; for
+ * ED_F64 the buffers hold int64 fixed point). Layout: dim_up rows of *ld elements (complex
+ * dtypes: pairs), the down rank d at column (*colpos)[d] (*colpos NULL: column d); columns
+ * past dim_dn hold 0. Valid until the next call on the state. Any output may be NULL.
+ * Synchronises the state's stream. */
+ed_status ed_lanczos_buffers(const ed_lanczos* st, const void** f_next, const void** f_cur,
+                             double* scale_next, double* scale_cur, int64_t* ld,
+                             const int32_t** colpos);
+
 /* ed_lanczos_energy - E0(j) = lowest eigenvalue of T_j (Sec. 2.2), computed on the device
  * by Sturm-sequence bisection in FP64, and the number of steps j taken. Synchronises. */
 ed_status ed_lanczos_energy(ed_lanczos* st, double* E0, int32_t* steps);

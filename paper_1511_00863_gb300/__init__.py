@@ -64,6 +64,8 @@ _SIGS = {
     "ed_lanczos_run": (c_int, [c_void_p, POINTER(ed_params), c_int32, POINTER(ctypes.c_float)]),
     "ed_lanczos_energy": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int32)]),
     "ed_lanczos_schedule": (c_int, [c_void_p, POINTER(c_int32)]),
+    "ed_lanczos_buffers": (c_int, [c_void_p, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_double),
+                                   POINTER(c_double), POINTER(c_int64), POINTER(c_void_p)]),
     "ed_lanczos_destroy": (None, [c_void_p]),
     "ed_lanczos_solve": (c_int, [c_void_p, POINTER(ed_params), POINTER(ed_opts), c_void_p, c_void_p,
                                  POINTER(c_double), POINTER(c_int32), POINTER(c_double),
@@ -306,6 +308,16 @@ def ed_lanczos_solve(basis, t: float, U: float, opts: ed_opts, f1=None, stream=N
     n = steps.value
     return dict(status=s, E0=E0.value, steps=n, alpha=np.array(alpha[:n]), beta=np.array(beta[:n]),
                 E0_hist=np.array(hist[:n]) if history else None)
+
+
+def ed_lanczos_buffers(st) -> dict:
+    """Device pointers and scales of the state's two work vectors (see include/ed.h)."""
+    fn, fc, cp = c_void_p(), c_void_p(), c_void_p()
+    sn, sc = c_double(), c_double()
+    ld = c_int64()
+    _check(_lib.ed_lanczos_buffers(st, byref(fn), byref(fc), byref(sn), byref(sc), byref(ld), byref(cp)))
+    return dict(f_next=fn.value, f_cur=fc.value, scale_next=sn.value, scale_cur=sc.value, ld=ld.value,
+                colpos=cp.value)
 
 
 def ed_lanczos_solve_mixed(basis, t: float, U: float, opts: ed_opts, f1=None, refine_steps: int = 64,

@@ -632,6 +632,24 @@ extern "C" ed_status ed_lanczos_run(ed_lanczos* st, const ed_params* p, int32_t 
   return r;
 }
 
+extern "C" ed_status ed_lanczos_buffers(const ed_lanczos* st, const void** f_next,
+                                       const void** f_cur, double* scale_next,
+                                       double* scale_cur, int64_t* ld, const int32_t** colpos) {
+  clear_error();
+  ED_CHECK_ARG(st != nullptr, "ed_lanczos_buffers: state is NULL");
+  // after step j the buffer `cur` holds f_{j+1} (scale S->scale[cur]) and the other f_j
+  double sc[2] = {0.0, 0.0};
+  ED_TRY_CUDA(cudaMemcpyAsync(sc, st->S->scale, sizeof(sc), cudaMemcpyDeviceToHost, st->stream));
+  ED_TRY_CUDA(cudaStreamSynchronize(st->stream));
+  if (f_next) *f_next = st->B[st->cur];
+  if (f_cur) *f_cur = st->B[1 - st->cur];
+  if (scale_next) *scale_next = sc[st->cur];
+  if (scale_cur) *scale_cur = sc[1 - st->cur];
+  if (ld) *ld = st->ld;
+  if (colpos) *colpos = hv2_colpos(st->plan);
+  return ED_OK;
+}
+
 extern "C" ed_status ed_lanczos_schedule(const ed_lanczos* st, int32_t* schedule) {
   clear_error();
   ED_CHECK_ARG(st != nullptr && schedule != nullptr, "ed_lanczos_schedule: NULL argument");

@@ -520,3 +520,36 @@ def test_single_species_ring26_closed_form(ed, fill):
     finally:
         ed.ed_basis_destroy(b)
     assert abs(res["E0"] - ref) <= 1e-11 * abs(ref), (res["E0"], ref, res["steps"])
+
+
+@pytest.mark.parametrize("name", ["variant_lattice", "ring14_7_7"])
+def test_fp32_norm_accumulation_matches_fp64_norm(ed, name):
+    """The FP32 path accumulates dot products per thread as compensated FP32 pairs (Dot2),
+    summed in FP64: b_{j+1} returned by a step equals the FP64 norm of the very FP32 vector
+    q the step wrote (read back through ed_lanczos_buffers) to 1e-12 relative over several
+    steps (the lattice with padded rows of the variant tests, and the 11.8 M-state 14-site
+    ring). FP32 products summed in FP64 would be off by ~1e-11 relative at this size, a
+    plain FP32 running sum by ~1e-7; Dot2 measures ~2e-14 here (its bound, gamma_n^2 for n
+    terms per thread, is far looser)."""
+    if name == "ring14_7_7":
+        w = ed_inputs.workload(name)
+        L, bonds, nu, nd, t, U = w["n_sites"], w["bonds"], w["n_up"], w["n_dn"], w["t"], w["U"]
+    else:
+        L, bonds, nu, nd, t, U = VARIANT_LATTICE
+    b = ed.ed_build_basis(L, bonds, nu, nd)
+    try:
+        du, dd, dim = ed.ed_basis_dims(b)
+        st = ed.ed_lanczos_init(b, ed.make_opts(max_steps=20, tol=0.0, seed=3, dtype="f32"))
+        try:
+            for _ in range(5):
+                s, a_j, b_j1 = ed.ed_lanczos_step(st, t, U)
+                bufs = ed.ed_lanczos_buffers(st)
+                n = du * bufs["ld"]
+                q = dev_to_numpy(bufs["f_next"], n, "<f4").astype(np.float64)
+                norm = float(np.sqrt(q @ q))          # FP64 norm of the FP32 values
+                assert abs(b_j1 - norm) <= 1e-12 * norm, (b_j1, norm)
+                assert bufs["scale_next"] == pytest.approx(1.0 / b_j1, rel=1e-15)
+        finally:
+            ed.ed_lanczos_destroy(st)
+    finally:
+        ed.ed_basis_destroy(b)
