@@ -500,8 +500,10 @@ def _hv_roofline(dim, du, dd, tabs, esize, hv_ms, workload, dtype, variant, t_bo
         traffic = rec["bytes"]
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic,
-            "kernel": (f"hv2_kernel variant {variant} (fused Lanczos H.v)" if variant > 0 else
-                       "general H.v kernels (rows too few or too long for the fused kernel)"),
+            "kernel": (f"hv2s_kernel variant {variant} (fused Lanczos H.v, rows staged as two slices)"
+                       if variant >= 30 else
+                       f"hv2_kernel variant {variant} (fused Lanczos H.v)" if variant > 0 else
+                       "general H.v kernels (rows too few for the fused kernel)"),
             "bytes_per_launch": hv_bytes, "launch_ms": hv_ms,
             "peak_source": f"{peak_kind} HBM copy bandwidth"}
 

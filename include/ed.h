@@ -120,7 +120,10 @@ typedef struct {
  *             takes element i = (r_2i, r_2i+1) from the real sequence of ed_start_vector
  *             over 2 dim entries, scaled to unit norm.
  *  schedule   fused H.v kernel variant (1..7 and 14 for ED_F32, 8..13 for ED_F64, 20..23
- *             for ED_C32; a variant of another precision or one that does not fit falls
+ *             for ED_C32; 30 (ED_F64) and 31 (ED_F32) are the split-row variants, which
+ *             stage a row as two slices of the down states (cut by the occupation of site
+ *             0) and run by themselves when a row is longer than any other variant's shared
+ *             memory; a variant of another precision or one that does not fit falls
  *             back to the default one,
  *             see ed_lanczos_schedule); -1 = for bases of at least 2^22 states, the fastest
  *             variant for this basis and dtype, found by timing every variant that fits on
@@ -382,6 +385,24 @@ ed_status ed_hv_down_tables(const int32_t* hop, const int32_t* hop_amp, const ui
                             int64_t dim, int32_t maxhops, int32_t ld, int32_t V, int32_t G,
                             int32_t complex_entries, uint32_t* table, int32_t rows_cap,
                             int32_t* rows, uint8_t* kpn, uint8_t* slot_lo, int32_t* colpos);
+
+/* ed_hv_split_tables - HOST ONLY (no GPU, no CUDA call): the down-hop tables of the split-row
+ * fused H.v (schedule 30 / 31) for one species, by the code its plan uses, for inspection and
+ * tests. hop [maxhops][dim] and bits [dim] as in ed_hv_down_tables; V columns per thread
+ * (1..8); site: the site whose occupation cuts the states into slice 0 (occupied) and slice
+ * 1 (empty). Outputs (caller-owned HOST arrays): table [rows_cap][cols_cap] (row stride *ld)
+ * uint16 entries of hop step k of column p at table[k * ld + p]: a target in p's own slice
+ * is its slot (column - cstart[s]), a target in the other slice 32768 + (column -
+ * cstart[other]), padding the zero slot *zslot; per chunk of 32 V columns the +1 hops occupy
+ * the first kpn[2c] rows and the -1 hops the next kpn[2c + 1]; cstart[3] the slice starts
+ * (each slice padded to a multiple of 32 V; *ld = cstart[2]); colpos[dim] the column of each
+ * down rank (slice, then hop count and +1-hop count descending, then rank). ED_ERR_ARG when a
+ * capacity is too small, a slice does not fit 15 bits, or a column has more than 255 hops
+ * of one sign. */
+ed_status ed_hv_split_tables(const int32_t* hop, const uint32_t* bits, int64_t dim,
+                             int32_t maxhops, int32_t V, int32_t site, uint16_t* table,
+                             int32_t rows_cap, int32_t cols_cap, int32_t* rows, int32_t* ld,
+                             int32_t* cstart, int32_t* zslot, uint8_t* kpn, int32_t* colpos);
 
 /* ed_selftest_barrier_timeout - failure-detection self-test of the bounded group barrier
  * used by ed_lanczos_solve_batched: a cooperative launch of `ctas` CTAs (2..64) in which

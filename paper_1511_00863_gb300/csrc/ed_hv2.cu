@@ -9,6 +9,7 @@
 
 #include "ed_hv2_kernel.cuh"
 #include "ed_hv2c_kernel.cuh"
+#include "ed_hv2s_kernel.cuh"
 #include "ed_tables.h"
 
 namespace ed {
@@ -24,7 +25,14 @@ struct Hv2Plan {
   uint8_t* slot_lo = nullptr;  // per column: slot within its group of G
   uint32_t* dn_pad = nullptr;  // down bits by column
   int32_t* colpos = nullptr;  // column of each down rank
+  int cst[3] = {0, 0, 0};     // split-row plans: slice starts
+  int zslot = 0;              // split-row plans: zero slot
 };
+
+// Split-row variants (hv2s_kernel): id, element, V, T, MB.
+#define HV2S_KINDS(X)              \
+  X(30, long long, 2, 512, 1)      \
+  X(31, float, 4, 512, 2)
 
 static int optin_smem() {
   int dev = 0, v = 0;
@@ -185,10 +193,116 @@ static ed_status down_tables(const ed_basis* b, int ld, const KindInfo& ki, cuda
   return ED_OK;
 }
 
+void hv2_split_free(const ed_basis* b);
 void hv2_tables_free(const ed_basis* b) {
+  hv2_split_free(b);
   std::lock_guard<std::mutex> lock(g_tables_mu);
   delete static_cast<std::deque<DownTables>*>(b->hv2_tables);
   b->hv2_tables = nullptr;
+}
+
+// ------------------------------------------------------------------ split rows
+static std::mutex g_split_mu;
+struct SplitCache {
+  bool tried = false;
+  SplitTables t;
+  bool ok = false;
+};
+
+static size_t split_smem(const SplitTables& t, const ed_basis* b, size_t esize) {
+  const int MH = b->up.maxhops > 0 ? b->up.maxhops : 1;
+  return ((size_t)(t.zslot + 1) * esize + 15) / 16 * 16 + (size_t)MH * 12;
+}
+
+// The split tables of this basis for V = 2 (int64 kernel) or V = 4 (FP32 kernel), built on
+// first use from the device basis tables and cached on the basis.
+static const SplitTables* split_tables(const ed_basis* b, int V, cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(g_split_mu);
+  auto* cache = static_cast<SplitCache*>(b->hv2_split);
+  if (!cache) b->hv2_split = cache = new SplitCache[2];
+  SplitCache& c = cache[V == 2 ? 0 : 1];
+  if (!c.tried) {
+    c.tried = true;
+    const int64_t n = b->dn.dim;
+    const int mh = b->dn.maxhops;
+    std::vector<int32_t> hop((size_t)mh * n);
+    std::vector<uint32_t> bits((size_t)n);
+    if ((mh > 0 && cudaMemcpyAsync(hop.data(), b->dn.hop, hop.size() * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
+        cudaMemcpyAsync(bits.data(), b->dn.bits, bits.size() * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return nullptr;
+    c.ok = build_split_tables(hop.data(), bits.data(), n, mh, V, 0, c.t) == ED_OK;
+  }
+  return c.ok ? &c.t : nullptr;
+}
+
+// forced: the caller asked for the split-row variant (schedule 30 / 31) whether or not the
+// plain variants fit
+static bool split_usable(const ed_basis* b, int mode, int ld_plain, bool forced = false) {
+  if (mode != kHv2F32 && mode != kHv2Fx) return false;
+  if (b->dn.maxhops > 255 || b->swapped || b->up.dim < 1) return false;
+  if (forced) return true;
+  if (b->up.dim < kMinRowsStaged) return false;
+  static const int pref_f32[] = {1, 4, 2, 6}, pref_fx[] = {8, 9, 12, 11};
+  KindInfo ki;
+  for (int i = 0; i < 4; ++i)
+    if (kind_usable(mode == kHv2Fx ? pref_fx[i] : pref_f32[i], b, mode, ld_plain, &ki)) return false;
+  return true;
+}
+
+int hv2_split_ld(const ed_basis* b, int mode, int schedule, cudaStream_t s) {
+  const int ld_plain = (int)((b->dn.dim + 31) / 32 * 32);
+  const bool forced = schedule == (mode == kHv2Fx ? 30 : 31);
+  if (!split_usable(b, mode, ld_plain, forced)) return 0;
+  const SplitTables* t = split_tables(b, mode == kHv2Fx ? 2 : 4, s);
+  if (!t) return 0;
+  if (split_smem(*t, b, mode == kHv2Fx ? 8 : 4) > (size_t)optin_smem() - 64) return 0;
+  return t->ld;
+}
+
+void hv2_split_free(const ed_basis* b) {
+  std::lock_guard<std::mutex> lock(g_split_mu);
+  delete[] static_cast<SplitCache*>(b->hv2_split);
+  b->hv2_split = nullptr;
+}
+
+static ed_status hv2_build_split(const ed_basis* b, int mode, int ld, cudaStream_t s, Hv2Plan** out) {
+  const int V = mode == kHv2Fx ? 2 : 4;
+  const SplitTables* t = split_tables(b, V, s);
+  if (!t || t->ld != ld) return ED_OK;  // caller falls back to the general kernels
+  Hv2Plan* p = new Hv2Plan();
+  p->kind = mode == kHv2Fx ? 30 : 31;
+  p->smem = split_smem(*t, b, mode == kHv2Fx ? 8 : 4);
+  p->ld = ld;
+  p->grid = (int)b->up.dim;
+  p->zslot = t->zslot;
+  for (int i = 0; i < 3; ++i) p->cst[i] = t->cstart[i];
+  const int64_t n = b->dn.dim;
+  if (cudaMalloc(&p->dtab, t->tab.size() * 2) != cudaSuccess ||
+      cudaMalloc((void**)&p->kpn, t->kpn.size()) != cudaSuccess ||
+      cudaMalloc((void**)&p->dn_pad, (size_t)ld * 4) != cudaSuccess ||
+      cudaMalloc((void**)&p->colpos, (size_t)(n > 0 ? n : 1) * 4) != cudaSuccess) {
+    cudaGetLastError();
+    hv2_free(p);
+    set_error("H.v split tables: out of device memory");
+    return ED_ERR_OOM;
+  }
+  cudaError_t e = cudaMemcpyAsync(p->dtab, t->tab.data(), t->tab.size() * 2, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p->kpn, t->kpn.data(), t->kpn.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p->dn_pad, t->pad.data(), (size_t)ld * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p->colpos, t->pos.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+#define HV2S_ATTR(K, E, V_, T, MB) \
+  if (e == cudaSuccess && p->kind == K) e = allow_max_smem(hv2s_kernel<E, V_, T, MB>);
+  HV2S_KINDS(HV2S_ATTR)
+#undef HV2S_ATTR
+  if (e != cudaSuccess) {
+    hv2_free(p);
+    set_error("H.v split tables: %s", cudaGetErrorString(e));
+    return ED_ERR_CUDA;
+  }
+  *out = p;
+  return ED_OK;
 }
 
 // Choose the kernel variant for this basis and element type, build the per-plan tables.
@@ -197,6 +311,9 @@ ed_status hv2_build(const ed_basis* b, int mode, int ld, int schedule, cudaStrea
   *out = nullptr;
   // down-loop lengths are stored in 8 bits
   if (b->dn.maxhops > 255) return ED_OK;  // caller falls back to the general kernels
+  if (schedule == (mode == kHv2Fx ? 30 : 31) && mode != kHv2C32 &&
+      split_usable(b, mode, (int)((b->dn.dim + 31) / 32 * 32), true))
+    return hv2_build_split(b, mode, ld, s, out);
   static const int pref_f32[] = {1, 4, 2, 6}, pref_fx[] = {8, 9, 12, 11}, pref_c32[] = {20, 21, 22, 23};
   const int* pref = mode == kHv2Fx ? pref_fx : mode == kHv2C32 ? pref_c32 : pref_f32;
   const int npref = 4;
@@ -207,7 +324,12 @@ ed_status hv2_build(const ed_basis* b, int mode, int ld, int schedule, cudaStrea
     if (i >= 0 && b->up.dim < kMinRowsStaged) break;  // few rows: the general kernels
     if (kind_usable(k, b, mode, ld, &ki)) kind = k;
   }
-  if (!kind) return ED_OK;  // caller falls back to the general kernels
+  if (!kind) {
+    // rows too long for every variant: the split-row kernel, when the stride is its own
+    if (split_usable(b, mode, (int)((b->dn.dim + 31) / 32 * 32)))
+      return hv2_build_split(b, mode, ld, s, out);
+    return ED_OK;  // caller falls back to the general kernels
+  }
   Hv2Plan* p = new Hv2Plan();
   p->kind = kind;
   p->smem = ki.smem;
@@ -314,7 +436,30 @@ ed_status hv2_launch(const Hv2Plan* p, const ed_basis* b, double t, double U, co
                                                              partial);
   HV2_KINDS(HV2_LAUNCH)
 #undef HV2_LAUNCH
-  if (p->kind >= 20) {
+  if (p->kind >= 30) {
+    Hv2sArgs c;
+    c.up_bits = b->up.bits;
+    c.dn_bits = p->dn_pad;
+    c.dtab = (const uint16_t*)p->dtab;
+    c.kpn = p->kpn;
+    c.hop_up = b->up.hop;
+    c.order = b->up_order;
+    c.dim_up = b->up.dim;
+    c.ld = p->ld;
+    c.maxhops_up = b->up.maxhops;
+    c.zslot = p->zslot;
+    c.cstart0 = p->cst[0];
+    c.cstart1 = p->cst[1];
+    c.cstart2 = p->cst[2];
+    c.t = (float)t;
+    c.U = (float)U;
+#define HV2S_LAUNCH(K, E, V_, T, MB)                                                          \
+    if (p->kind == K)                                                                          \
+      hv2s_kernel<E, V_, T, MB><<<p->grid, T, p->smem, s>>>(c, (const E*)x, (E*)y, S, cur, partial);
+    HV2S_KINDS(HV2S_LAUNCH)
+#undef HV2S_LAUNCH
+  }
+  if (p->kind >= 20 && p->kind <= 23) {
     Hv2cArgs c;
     c.up_bits = b->up.bits;
     c.dn_bits = p->dn_pad;

@@ -68,6 +68,8 @@ struct ed_basis {
   // Host-built down tables of the fused H.v per (V, G) geometry (ed_hv2.cu); freed with the
   // basis.
   mutable void* hv2_tables = nullptr;
+  // Host-built split-row down tables (ed_hv2.cu), for rows longer than shared memory.
+  mutable void* hv2_split = nullptr;
   // True when the caller's down species has a single state (N_dn = 0 or N_dn = n_sites) and
   // the up species more: the kernels then see the occupied species as the row (`dn`)
   // species, so a state vector is one row of C(L, N_up) elements instead of C(L, N_up) rows
@@ -225,6 +227,11 @@ ed_status hv2_build(const ed_basis* b, int mode, int ld, int schedule, cudaStrea
                     Hv2Plan** out);
 void hv2_free(Hv2Plan* p);
 int hv2_grid(const Hv2Plan* p);
+// Row stride the fused H.v needs for this basis and precision when its rows only fit in
+// shared memory as two slices (the split-row kernel), else 0 (the stride is then dim_dn
+// rounded up to 32). Builds and caches the split tables on the basis.
+// schedule 30 (int64) / 31 (FP32) asks for the split-row kernel whether or not rows fit.
+int hv2_split_ld(const ed_basis* b, int mode, int schedule, cudaStream_t s);
 // Column of each down rank in the plan's row layout (device, dim_dn entries).
 const int32_t* hv2_colpos(const Hv2Plan* p);
 int hv2_kind(const Hv2Plan* p);

@@ -423,6 +423,12 @@ static ed_status lz_alloc(const ed_basis* b, const ed_opts* o, cudaStream_t s, e
   st->fx = o->dtype == ED_F64;
   if (st->fx) st->fxr = fx_make(b);
   st->ld = (b->dn.dim + 31) / 32 * 32;
+  if (o->dtype == ED_F32 || o->dtype == ED_F64) {
+    // rows longer than shared memory: the split-row fused H.v lays each row out as two
+    // padded slices
+    const int lds = hv2_split_ld(b, o->dtype == ED_F64 ? kHv2Fx : kHv2F32, o->schedule, s);
+    if (lds > 0) st->ld = lds;
+  }
   st->n = b->up.dim * st->ld;
   // partial sums: one double per CTA, or four int64 words per CTA on the fixed-point path
   st->npa = hv_max_grid(b) * (st->fx ? 4 : 1);

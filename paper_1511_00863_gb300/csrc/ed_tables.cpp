@@ -384,3 +384,131 @@ extern "C" ed_status ed_hv_down_tables(const int32_t* hop, const int32_t* hop_am
   std::copy(t.pos.begin(), t.pos.end(), colpos);
   return ED_OK;
 }
+
+namespace ed {
+
+// Split-row tables: the down states are cut in two slices by the occupation of one site
+// (slice 0: occupied, slice 1: empty); a slice is staged in shared memory at a time, so a
+// row twice as long as shared memory can still be processed row-staged. Columns of slice s
+// are [cstart[s], cstart[s+1]), each slice padded to a multiple of 32 V and its states
+// ordered like the plain tables (hop count, then +1-hop count, descending, then rank). An
+// entry of hop step k of column p: a target in p's own slice is its slot inside the slice
+// (column - cstart[s], < 32768); a target in the other slice is 32768 + (column -
+// cstart[other]) and is read from global memory; padding is the zero slot zslot.
+ed_status build_split_tables(const int32_t* hop, const uint32_t* bits, int64_t n, int mh, int V,
+                             int site, SplitTables& out) {
+  if (n < 1 || mh < 0 || V < 1 || V > 8 || site < 0 || site > 31) {
+    set_error("split tables: invalid geometry");
+    return ED_ERR_ARG;
+  }
+  const int CW = 32 * V;
+  std::vector<int> npos(n, 0), nneg(n, 0);
+  for (int64_t d = 0; d < n; ++d)
+    for (int k = 0; k < mh; ++k) {
+      const uint32_t e = (uint32_t)hop[(size_t)k * n + d];
+      if ((int64_t)(e & kTargetMask) >= n) continue;
+      ((e & kSignBit) ? nneg : npos)[d]++;
+    }
+  std::vector<int64_t> members[2];
+  for (int64_t d = 0; d < n; ++d) members[((bits[d] >> site) & 1u) ? 0 : 1].push_back(d);
+  for (auto& m : members)
+    std::stable_sort(m.begin(), m.end(), [&](int64_t a, int64_t b) {
+      const int ha = npos[a] + nneg[a], hb = npos[b] + nneg[b];
+      if (ha != hb) return ha > hb;
+      if (npos[a] != npos[b]) return npos[a] > npos[b];
+      return a < b;
+    });
+  const int64_t len0 = (int64_t)members[0].size(), len1 = (int64_t)members[1].size();
+  const int64_t p0 = (len0 + CW - 1) / CW * CW, p1 = (len1 + CW - 1) / CW * CW;
+  if (p0 >= 32768 || p1 >= 32768) {
+    set_error("split tables: a slice of %lld columns does not fit the 15-bit slot field",
+              (long long)std::max(p0, p1));
+    return ED_ERR_ARG;
+  }
+  out = SplitTables();
+  out.V = V;
+  out.site = site;
+  out.cstart[0] = 0;
+  out.cstart[1] = (int)p0;
+  out.cstart[2] = (int)(p0 + p1);
+  out.ld = out.cstart[2];
+  out.zslot = (int)std::max(p0, p1);
+  out.pos.assign(n, -1);
+  out.pad.assign(out.ld, 0u);
+  std::vector<int64_t> rank_of_col(out.ld, -1);
+  for (int s = 0; s < 2; ++s)
+    for (size_t i = 0; i < members[s].size(); ++i) {
+      const int64_t d = members[s][i];
+      const int col = out.cstart[s] + (int)i;
+      out.pos[d] = col;
+      out.pad[col] = bits[d];
+      rank_of_col[col] = d;
+    }
+  const int nch = out.ld / CW;
+  std::vector<int> kp(nch, 0), kn(nch, 0);
+  for (int p = 0; p < out.ld; ++p) {
+    const int64_t d = rank_of_col[p];
+    if (d < 0) continue;
+    kp[p / CW] = std::max(kp[p / CW], npos[d]);
+    kn[p / CW] = std::max(kn[p / CW], nneg[d]);
+  }
+  out.rows = 0;
+  out.kpn.assign(2 * (size_t)nch, 0);
+  for (int c = 0; c < nch; ++c) {
+    if (kp[c] > 255 || kn[c] > 255) {
+      set_error("split tables: more than 255 hops of one sign");
+      return ED_ERR_ARG;
+    }
+    out.kpn[2 * c] = (uint8_t)kp[c];
+    out.kpn[2 * c + 1] = (uint8_t)kn[c];
+    out.rows = std::max(out.rows, kp[c] + kn[c]);
+  }
+  out.tab.assign((size_t)out.rows * out.ld, (uint16_t)out.zslot);
+  for (int p = 0; p < out.ld; ++p) {
+    const int64_t d = rank_of_col[p];
+    if (d < 0) continue;
+    const int s = p < out.cstart[1] ? 0 : 1, c = p / CW;
+    int ip = 0, in = 0;
+    for (int k = 0; k < mh; ++k) {
+      const uint32_t e = (uint32_t)hop[(size_t)k * n + d];
+      const int64_t t = (int64_t)(e & kTargetMask);
+      if (t >= n) continue;
+      const int tc = out.pos[t];
+      const int ts = tc < out.cstart[1] ? 0 : 1;
+      const uint16_t ent = ts == s ? (uint16_t)(tc - out.cstart[s])
+                                   : (uint16_t)(32768 + (tc - out.cstart[ts]));
+      const int row = (e & kSignBit) ? kp[c] + in++ : ip++;
+      out.tab[(size_t)row * out.ld + p] = ent;
+    }
+  }
+  return ED_OK;
+}
+
+}  // namespace ed
+
+extern "C" ed_status ed_hv_split_tables(const int32_t* hop, const uint32_t* bits, int64_t dim,
+                                        int32_t maxhops, int32_t V, int32_t site,
+                                        uint16_t* table, int32_t rows_cap, int32_t cols_cap,
+                                        int32_t* rows, int32_t* ld, int32_t* cstart,
+                                        int32_t* zslot, uint8_t* kpn, int32_t* colpos) {
+  if (!table || !rows || !ld || !cstart || !zslot || !kpn || !colpos) {
+    ed::set_error("ed_hv_split_tables: null output");
+    return ED_ERR_ARG;
+  }
+  ed::SplitTables t;
+  const ed_status r = ed::build_split_tables(hop, bits, dim, maxhops, V, site, t);
+  if (r != ED_OK) return r;
+  *rows = t.rows;
+  *ld = t.ld;
+  if (t.rows > rows_cap || t.ld > cols_cap) {
+    ed::set_error("ed_hv_split_tables: %d x %d table, capacity %d x %d", t.rows, t.ld, rows_cap,
+                  cols_cap);
+    return ED_ERR_ARG;
+  }
+  std::copy(t.tab.begin(), t.tab.end(), table);
+  for (int i = 0; i < 3; ++i) cstart[i] = t.cstart[i];
+  *zslot = t.zslot;
+  std::copy(t.kpn.begin(), t.kpn.end(), kpn);
+  std::copy(t.pos.begin(), t.pos.end(), colpos);
+  return ED_OK;
+}

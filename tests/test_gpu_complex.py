@@ -178,11 +178,12 @@ def test_every_complex_variant_follows_oracle(ed, variant):
 
 def test_checkerboard_c32_matches_c64(ed):
     """The checkerboard-type 4x4 workload (dim 19,079,424): the fused complex FP32 path and
-    the FP64 complex path reach the same ground-state energy within FP32 accuracy."""
+    the FP64 complex path reach the same ground-state energy within 1e-6 relative (the FP32
+    tolerance of the benchmark spec), the FP32 run converged to |dE0| <= 1e-9."""
     w = ed_inputs.workload("checker4x4_5_5")
     b = ed.ed_build_basis(w["n_sites"], w["bonds"], w["n_up"], w["n_dn"], t_bond=w["t_bond"])
     try:
-        o32 = ed.make_opts(max_steps=300, tol=1e-7, seed=w["seed"], dtype="c32")
+        o32 = ed.make_opts(max_steps=300, tol=1e-9, seed=w["seed"], dtype="c32")
         st = ed.ed_lanczos_init(b, o32)
         try:
             assert ed.ed_lanczos_schedule(st) >= 20
@@ -193,4 +194,4 @@ def test_checkerboard_c32_matches_c64(ed):
                                                                   dtype="c64"))["E0"]
     finally:
         ed.ed_basis_destroy(b)
-    assert abs(e32 - e64) <= 2e-5 * abs(e64), (e32, e64)
+    assert abs(e32 - e64) <= 1e-6 * abs(e64), (e32, e64)

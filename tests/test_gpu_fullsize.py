@@ -89,3 +89,24 @@ def test_ring18_U4_fp32_E0_vs_bethe_ansatz(ed):
     E_ref = bethe_golden("ring18_9_9", 4.0)
     res = _solve(ed, "ring18_9_9", "f32", U=4.0, tol=1e-9, max_steps=300)
     assert abs(res["E0"] - E_ref) <= 1e-6 * abs(E_ref), (res["E0"], E_ref, res["steps"])
+
+
+@pytest.mark.slow
+def test_ring18_U4_fp64_accurate_split_rows_vs_bethe_ansatz(ed):
+    """The FP64-accurate form of the 18-site 9/9 basis: its 389 KB int64 rows exceed shared
+    memory, so the split-row fused kernel (schedule 30, two slices of the down states) runs
+    by itself; E0 at U = 4 within 1e-10 of the Bethe-ansatz energy."""
+    E_ref = bethe_golden("ring18_9_9", 4.0)
+    w = ed_inputs.workload("ring18_9_9")
+    b = ed.ed_build_basis(w["n_sites"], w["bonds"], w["n_up"], w["n_dn"])
+    try:
+        opts = ed.make_opts(max_steps=400, tol=1e-12, seed=w["seed"], dtype="f64")
+        st = ed.ed_lanczos_init(b, opts)
+        try:
+            assert ed.ed_lanczos_schedule(st) == 30
+        finally:
+            ed.ed_lanczos_destroy(st)
+        res = ed.ed_lanczos_solve(b, w["t"], 4.0, opts, raise_not_converged=False)
+    finally:
+        ed.ed_basis_destroy(b)
+    assert abs(res["E0"] - E_ref) <= 1e-10 * abs(E_ref), (res["E0"], E_ref, res["steps"])

@@ -363,8 +363,8 @@ def test_cached_solves_repeat_exactly(ed, dtype):
 # signs and uneven hop counts: a_j, b_{j+1} of the first steps follow the oracle.
 VARIANT_LATTICE = (11, np.array([[i, (i + 1) % 11] for i in range(11)] +
                                 [[0, 5], [2, 9], [3, 7], [1, 8], [4, 10], [6, 0]]), 3, 5, 1.0, 3.5)
-F32_VARIANTS = [1, 2, 3, 4, 5, 6, 7, 14]
-F64_VARIANTS = [8, 9, 10, 11, 12, 13]
+F32_VARIANTS = [1, 2, 3, 4, 5, 6, 7, 14, 31]   # 31: split-row kernel, forced
+F64_VARIANTS = [8, 9, 10, 11, 12, 13, 30]      # 30: split-row kernel, forced
 
 
 @pytest.fixture(scope="module")

@@ -165,3 +165,59 @@ def test_bad_geometry():
     with pytest.raises(ed.EdError) as e:
         ed.ed_hv_down_tables(hop, bits, 2, 16, hop_amp=bad, complex_entries=True)
     assert e.value.status == ed.ED_ERR_ARG
+
+
+SPLIT_CASES = [
+    (12, ed_inputs.ring_bonds(12), 6, 2),     # half filling: equal slices
+    (10, ed_inputs.ring_bonds(10), 3, 4),     # unequal slices (site 0 occupied in 36 of 120)
+    (8, ed_inputs.torus_bonds(2, 4), 4, 1),   # doubled bonds
+    (9, np.array([[0, 5], [3, 8], [1, 2], [7, 0], [6, 4], [2, 8], [5, 1]]), 4, 2),
+]
+
+
+@pytest.mark.parametrize("L,bonds,N,V", SPLIT_CASES)
+def test_split_tables_keep_every_hop(L, bonds, N, V):
+    """Split-row tables (rows longer than shared memory, staged as two slices cut by the
+    occupation of site 0): each column decodes to exactly its state's hops, by sign, with
+    in-slice targets as slots and cross-slice targets as columns of the other slice; slices
+    hold exactly the states with site 0 occupied / empty; padding points at the zero slot."""
+    hop, _, bits = hop_table(L, N, bonds)
+    n = bits.size
+    out = ed.ed_hv_split_tables(hop, bits, V, site=0)
+    T, kpn, cs, z, pos, ld = out["table"], out["kpn"], out["cstart"], out["zslot"], out["colpos"], out["ld"]
+    CW = 32 * V
+    assert cs[0] == 0 and cs[1] % CW == 0 and cs[2] == ld and ld % CW == 0
+    occ = (bits & 1) == 1
+    assert cs[1] == (occ.sum() + CW - 1) // CW * CW
+    assert z == max(cs[1] - cs[0], cs[2] - cs[1])
+    # every rank has a distinct column inside its slice
+    assert len(set(pos.tolist())) == n
+    assert np.all((pos < cs[1]) == occ)
+    col2rank = {int(p): d for d, p in enumerate(pos)}
+    h = hop.view(np.uint32).astype(np.int64)
+    for p in range(ld):
+        s = 0 if p < cs[1] else 1
+        c = p // CW
+        kp, kn = int(kpn[c, 0]), int(kpn[c, 1])
+        assert T.shape[0] >= kp + kn
+        d = col2rank.get(p)
+        got = {+1: [], -1: []}
+        for k in range(kp + kn):
+            e = int(T[k, p])
+            if e == z:
+                continue
+            if e < 32768:
+                tcol = cs[s] + e
+                assert tcol < cs[s + 1]
+            else:
+                tcol = cs[1 - s] + (e - 32768)
+                assert cs[1 - s] <= tcol < cs[2 - s]
+            got[+1 if k < kp else -1].append(col2rank[tcol])
+        if d is None:
+            assert not got[+1] and not got[-1]    # padding column: only zero slots
+            continue
+        want = {+1: [], -1: []}
+        for k in range(h.shape[0]):
+            if (h[k, d] & 0x3FFFFFFF) < n:
+                want[-1 if (h[k, d] >> 31) & 1 else +1].append(int(h[k, d] & 0x3FFFFFFF))
+        assert sorted(got[+1]) == sorted(want[+1]) and sorted(got[-1]) == sorted(want[-1]), p
