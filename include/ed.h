@@ -122,8 +122,9 @@ typedef struct {
  *  schedule   fused H.v kernel variant (1..7 and 14 for ED_F32, 8..13 for ED_F64, 20..23
  *             for ED_C32; 30 (ED_F64) and 31 (ED_F32) are the split-row variants, which
  *             stage a row as two slices of the down states (cut by the occupation of site
- *             0) and run by themselves when a row is longer than any other variant's shared
- *             memory; a variant of another precision or one that does not fit falls
+ *             0) and run by themselves when the other variants do not fit two rows per SM
+ *             in shared memory (or not at all); a variant of another precision or one that
+ *             does not fit falls
  *             back to the default one,
  *             see ed_lanczos_schedule); -1 = for bases of at least 2^22 states, the fastest
  *             variant for this basis and dtype, found by timing every variant that fits on

@@ -243,10 +243,14 @@ static bool split_usable(const ed_basis* b, int mode, int ld_plain, bool forced 
   if (b->dn.maxhops > 255 || b->swapped || b->up.dim < 1) return false;
   if (forced) return true;
   if (b->up.dim < kMinRowsStaged) return false;
+  // chosen by itself when no plain variant fits, or when the plain ones fit only one CTA per
+  // SM (half-rows then run two per SM: 23 ms against 40 ms per H.v on the 18-site FP32 basis)
   static const int pref_f32[] = {1, 4, 2, 6}, pref_fx[] = {8, 9, 12, 11};
   KindInfo ki;
   for (int i = 0; i < 4; ++i)
-    if (kind_usable(mode == kHv2Fx ? pref_fx[i] : pref_f32[i], b, mode, ld_plain, &ki)) return false;
+    if (kind_usable(mode == kHv2Fx ? pref_fx[i] : pref_f32[i], b, mode, ld_plain, &ki) &&
+        2 * ki.smem <= (size_t)optin_smem())
+      return false;
   return true;
 }
 
@@ -311,8 +315,10 @@ ed_status hv2_build(const ed_basis* b, int mode, int ld, int schedule, cudaStrea
   *out = nullptr;
   // down-loop lengths are stored in 8 bits
   if (b->dn.maxhops > 255) return ED_OK;  // caller falls back to the general kernels
-  if (schedule == (mode == kHv2Fx ? 30 : 31) && mode != kHv2C32 &&
-      split_usable(b, mode, (int)((b->dn.dim + 31) / 32 * 32), true))
+  if (mode != kHv2C32 &&
+      ((schedule == (mode == kHv2Fx ? 30 : 31) &&
+        split_usable(b, mode, (int)((b->dn.dim + 31) / 32 * 32), true)) ||
+       (schedule < 0 && split_usable(b, mode, (int)((b->dn.dim + 31) / 32 * 32)))))
     return hv2_build_split(b, mode, ld, s, out);
   static const int pref_f32[] = {1, 4, 2, 6}, pref_fx[] = {8, 9, 12, 11}, pref_c32[] = {20, 21, 22, 23};
   const int* pref = mode == kHv2Fx ? pref_fx : mode == kHv2C32 ? pref_c32 : pref_f32;

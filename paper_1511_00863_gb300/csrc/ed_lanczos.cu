@@ -423,11 +423,15 @@ static ed_status lz_alloc(const ed_basis* b, const ed_opts* o, cudaStream_t s, e
   st->fx = o->dtype == ED_F64;
   if (st->fx) st->fxr = fx_make(b);
   st->ld = (b->dn.dim + 31) / 32 * 32;
+  bool split = false;  // the split-row kernel (its own row stride; no timing of variants)
   if (o->dtype == ED_F32 || o->dtype == ED_F64) {
     // rows longer than shared memory: the split-row fused H.v lays each row out as two
     // padded slices
     const int lds = hv2_split_ld(b, o->dtype == ED_F64 ? kHv2Fx : kHv2F32, o->schedule, s);
-    if (lds > 0) st->ld = lds;
+    if (lds > 0) {
+      st->ld = lds;
+      split = true;
+    }
   }
   st->n = b->up.dim * st->ld;
   // partial sums: one double per CTA, or four int64 words per CTA on the fixed-point path
@@ -458,6 +462,7 @@ static ed_status lz_alloc(const ed_basis* b, const ed_opts* o, cudaStream_t s, e
   if (o->dtype == ED_F32 || o->dtype == ED_F64 || o->dtype == ED_C32) {
     const int mode = st->fx ? kHv2Fx : o->dtype == ED_C32 ? kHv2C32 : kHv2F32;
     int sched = o->schedule;
+    if (split) sched = st->fx ? 30 : 31;
     if (sched < 0) {
       // autotune once per basis and dtype: time every variant on this run's zeroed buffers
       int& tuned = b->tuned_kind[(int)o->dtype];

@@ -470,7 +470,7 @@ def test_ring18_half_filling_U0_closed_form(ed):
         opts = ed.make_opts(max_steps=400, tol=1e-9, seed=w["seed"], dtype="f32")
         st = ed.ed_lanczos_init(b, opts)
         try:
-            assert ed.ed_lanczos_schedule(st) > 0   # the fused FP32 path (R = 1 rows per CTA)
+            assert ed.ed_lanczos_schedule(st) == 31   # the split-row fused kernel (two 97 KB slices)
         finally:
             ed.ed_lanczos_destroy(st)
         res = ed.ed_lanczos_solve(b, 1.0, 0.0, opts, raise_not_converged=False)
