@@ -38,7 +38,7 @@ FALLBACK_HBM_GBS = 6800.0
 # the kernel's sources are unchanged since that capture.
 KERNEL_SOURCES = ["paper_1511_00863_gb300/csrc/ed_hv2_kernel.cuh", "paper_1511_00863_gb300/csrc/ed_fixed.cuh",
                   "paper_1511_00863_gb300/csrc/ed_internal.cuh", "paper_1511_00863_gb300/csrc/ed_tables.h"]
-TRAFFIC_SOURCES_SHA256 = "c6bae5256eb92ac066e40f34f2bfba8da6959a41e4cae6186f9a0111cafb23d2"
+TRAFFIC_SOURCES_SHA256 = "d5cddba73f3a3d16aa105a94ec04438c502f7512267e7f10f94116b3c2604841"
 MEASURED_TRAFFIC = {
     ("torus4x4_5_5", "f64", 8): {"bytes": 474670848 + 136560640,
                                  "profile": "profiles/hv2_kernel_torus4x4_5_5_int64.md"},
@@ -54,14 +54,17 @@ MEASURED_TRAFFIC = {
 
 
 def _sources_sha256():
-    """Digest of the fused H.v kernel's sources: its own headers and the reduction helpers
-    it uses from ed_internal.cuh (the part of that header after its reductions marker)."""
+    """Digest of the fused H.v kernel's sources: its own headers, the reduction helpers it
+    uses from ed_internal.cuh (the part of that header after its reductions marker) and the
+    hop-entry constants of ed_tables.h."""
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
         txt = open(os.path.join(ROOT, f), "rb").read()
         if f.endswith("ed_internal.cuh"):
             txt = txt[txt.index(b"// ---------------------------------------------------------------- reductions"):]
+        elif f.endswith("ed_tables.h"):   # the kernel uses the hop-entry layout constants only
+            txt = b"".join(l for l in txt.splitlines(True) if b"constexpr uint32_t k" in l)
         h.update(txt)
     return h.hexdigest()
 

@@ -123,6 +123,9 @@ def workload(name: str) -> dict:
         bonds, amp = checkerboard_lattice(4, 4)
         return dict(n_sites=16, bonds=bonds, t_bond=amp, n_up=5, n_dn=5, t=1.0, U=4.0,
                     dtype="c64", seed=8)
+    if name == "ring18_3_9":      # L=18 ring, 3 up, 9 down: the 18-site rows at 39.7 M states
+        return dict(n_sites=18, bonds=ring_bonds(18), n_up=3, n_dn=9, t=1.0, U=4.0,
+                    dtype="f32", seed=6)
     if name == "ring18_9_9":      # L=18 ring, half filling, dim 48620^2 = 2.36e9, FP32
         return dict(n_sites=18, bonds=ring_bonds(18), n_up=9, n_dn=9, t=1.0, U=4.0,
                     dtype="f32", seed=6)
