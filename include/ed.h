@@ -367,7 +367,8 @@ void ed_mlp_destroy(ed_mlp* mlp);
  *  hop_amp  NULL, or [maxhops][dim] amplitude numbers a, 0 <= 2 a + 1 < 65536 (complex
  *           entries only; NULL = 0).
  *  bits     [dim] uint32 (HOST): bit strings in rank order.
- *  ld       row length of the library's vectors: dim rounded up to a multiple of 32.
+ *  ld       row length: a multiple of 32, at least dim (the library's vectors use dim
+ *           rounded up to 32; the split-row tables use longer slices).
  *  V, G     columns per thread (1..8) and shared-memory slots per bank group (8, 16, 32).
  *  complex_entries  0: entries are slots (16-bit in the kernel); 1: slot | signed amplitude
  *           index << 16, index 2 a + s for amplitude number a and sign bit s.
@@ -390,20 +391,29 @@ ed_status ed_hv_down_tables(const int32_t* hop, const int32_t* hop_amp, const ui
 /* ed_hv_split_tables - HOST ONLY (no GPU, no CUDA call): the down-hop tables of the split-row
  * fused H.v (schedule 30 / 31) for one species, by the code its plan uses, for inspection and
  * tests. hop [maxhops][dim] and bits [dim] as in ed_hv_down_tables; V columns per thread
- * (1..8); site: the site whose occupation cuts the states into slice 0 (occupied) and slice
- * 1 (empty). Outputs (caller-owned HOST arrays): table [rows_cap][cols_cap] (row stride *ld)
- * uint16 entries of hop step k of column p at table[k * ld + p]: a target in p's own slice
- * is its slot (column - cstart[s]), a target in the other slice 32768 + (column -
- * cstart[other]), padding the zero slot *zslot; per chunk of 32 V columns the +1 hops occupy
- * the first kpn[2c] rows and the -1 hops the next kpn[2c + 1]; cstart[3] the slice starts
- * (each slice padded to a multiple of 32 V; *ld = cstart[2]); colpos[dim] the column of each
- * down rank (slice, then hop count and +1-hop count descending, then rank). ED_ERR_ARG when a
- * capacity is too small, a slice does not fit 15 bits, or a column has more than 255 hops
- * of one sign. */
+ * (1..8); G slots per bank group (8, 16 or 32; the kernels use 16 with V = 2 and 32 with
+ * V = 4); site: the site whose occupation cuts the states into slice 0 (occupied) and slice
+ * 1 (empty). Slice s holds the columns [cstart[s], cstart[s+1]); its length ld_s is a
+ * multiple of 32 V with at least one padding column, and its columns, slot map and in-slice
+ * hop rows are those ed_hv_down_tables gives for the slice's own states and in-slice hops
+ * (zero slots ld_s .. ld_s + G - 1). Outputs (caller-owned HOST arrays):
+ *  table   [rows_cap][cols_cap], row stride *ld: in-slice hop step k of column p at
+ *          table[k * ld + p], the slot of the target inside p's slice;
+ *  xtable  [rows_cap][cols_cap], row stride *ld: cross-slice hop step k of column p at
+ *          xtable[k * ld + p], the target's column inside the other slice (padding: the
+ *          other slice's last column, a padding column);
+ *  kpn     [4 * (*ld / (32 V))]: per chunk, the in-slice +1 rows, in-slice -1 rows (both in
+ *          table), cross +1 rows, cross -1 rows (both in xtable), +1 rows first;
+ *  slot_lo [*ld]: slot of column p within its aligned group of G (columns counted from the
+ *          slice start); cstart[3] the slice starts (*ld = cstart[2]); colpos [dim] the
+ *          column of each down rank; *rows, *xrows the row counts of table and xtable.
+ * ED_ERR_ARG when a capacity is too small, a slice does not fit 15 bits, or a column has
+ * more than 255 hops of one sign. */
 ed_status ed_hv_split_tables(const int32_t* hop, const uint32_t* bits, int64_t dim,
-                             int32_t maxhops, int32_t V, int32_t site, uint16_t* table,
-                             int32_t rows_cap, int32_t cols_cap, int32_t* rows, int32_t* ld,
-                             int32_t* cstart, int32_t* zslot, uint8_t* kpn, int32_t* colpos);
+                             int32_t maxhops, int32_t V, int32_t G, int32_t site,
+                             uint16_t* table, uint16_t* xtable, int32_t rows_cap,
+                             int32_t cols_cap, int32_t* rows, int32_t* xrows, int32_t* ld,
+                             int32_t* cstart, uint8_t* kpn, uint8_t* slot_lo, int32_t* colpos);
 
 /* ed_selftest_barrier_timeout - failure-detection self-test of the bounded group barrier
  * used by ed_lanczos_solve_batched: a cooperative launch of `ctas` CTAs (2..64) in which

@@ -91,9 +91,10 @@ _SIGS = {
     "ed_hv_down_tables": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32, c_int32,
                                   c_int32, c_int32, c_void_p, c_int32, POINTER(c_int32), c_void_p,
                                   c_void_p, c_void_p]),
-    "ed_hv_split_tables": (c_int, [c_void_p, c_void_p, c_int64, c_int32, c_int32, c_int32, c_void_p, c_int32,
-                                   c_int32, POINTER(c_int32), POINTER(c_int32), c_void_p, POINTER(c_int32),
-                                   c_void_p, c_void_p]),
+    "ed_hv_split_tables": (c_int, [c_void_p, c_void_p, c_int64, c_int32, c_int32, c_int32, c_int32,
+                                   c_void_p, c_void_p, c_int32, c_int32, POINTER(c_int32),
+                                   POINTER(c_int32), POINTER(c_int32), c_void_p, c_void_p, c_void_p,
+                                   c_void_p]),
     "ed_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -207,28 +208,33 @@ def ed_hv_down_tables(hop, bits, V: int, G: int, hop_amp=None, complex_entries: 
             "colpos": colpos, "ld": ld}
 
 
-def ed_hv_split_tables(hop, bits, V: int, site: int = 0):
+def ed_hv_split_tables(hop, bits, V: int, G: int, site: int = 0):
     """Host-only: the split-row fused H.v's down tables of one species (no GPU needed).
 
-    Returns dict(table [rows][ld] uint16, kpn [chunks][2] uint8, cstart [3], zslot,
-    colpos [dim] int32, ld)."""
+    Returns dict(table [rows][ld] uint16 in-slice slots, xtable [xrows][ld] uint16 columns in
+    the other slice, kpn [chunks][4] uint8, slot_lo [ld] uint8, cstart [3], colpos [dim]
+    int32, ld)."""
     hop = np.ascontiguousarray(hop, dtype=np.int32)
     bits = np.ascontiguousarray(bits, dtype=np.uint32)
     mh, dim = (hop.shape if hop.ndim == 2 else (0, bits.size))
-    cols = 2 * ((dim + 32 * V - 1) // (32 * V) + 1) * 32 * V
+    cols = 2 * ((dim + 32 * V) // (32 * V) + 1) * 32 * V
     cap = max(1, 2 * mh)
     table = np.zeros(cap * cols, dtype=np.uint16)
-    kpn = np.zeros(2 * (cols // (32 * V)), dtype=np.uint8)
+    xtable = np.zeros(cap * cols, dtype=np.uint16)
+    kpn = np.zeros(4 * (cols // (32 * V)), dtype=np.uint8)
+    lo = np.zeros(cols, dtype=np.uint8)
     cstart = np.zeros(3, dtype=np.int32)
     colpos = np.zeros(dim, dtype=np.int32)
-    rows, ld, zslot = c_int32(0), c_int32(0), c_int32(0)
-    _check(_lib.ed_hv_split_tables(hop.ctypes.data if mh else None, bits.ctypes.data, dim, mh, V, site,
-                                   table.ctypes.data, cap, cols, byref(rows), byref(ld),
-                                   cstart.ctypes.data, byref(zslot), kpn.ctypes.data, colpos.ctypes.data))
-    n = rows.value * ld.value
-    return {"table": table[:n].reshape(rows.value, ld.value).copy(),
-            "kpn": kpn[:2 * (ld.value // (32 * V))].reshape(-1, 2), "cstart": cstart.copy(),
-            "zslot": zslot.value, "colpos": colpos, "ld": ld.value}
+    rows, xrows, ld = c_int32(0), c_int32(0), c_int32(0)
+    _check(_lib.ed_hv_split_tables(hop.ctypes.data if mh else None, bits.ctypes.data, dim, mh, V, G,
+                                   site, table.ctypes.data, xtable.ctypes.data, cap, cols,
+                                   byref(rows), byref(xrows), byref(ld), cstart.ctypes.data,
+                                   kpn.ctypes.data, lo.ctypes.data, colpos.ctypes.data))
+    n, nx, w = rows.value * ld.value, xrows.value * ld.value, ld.value
+    return {"table": table[:n].reshape(rows.value, w).copy(),
+            "xtable": xtable[:nx].reshape(xrows.value, w).copy(),
+            "kpn": kpn[:4 * (w // (32 * V))].reshape(-1, 4).copy(), "slot_lo": lo[:w].copy(),
+            "cstart": cstart.copy(), "colpos": colpos, "ld": w}
 
 
 def ed_basis_filling(basis):

@@ -26,7 +26,8 @@ struct Hv2Plan {
   uint32_t* dn_pad = nullptr;  // down bits by column
   int32_t* colpos = nullptr;  // column of each down rank
   int cst[3] = {0, 0, 0};     // split-row plans: slice starts
-  int zslot = 0;              // split-row plans: zero slot
+  int nslots = 0;             // split-row plans: shared-memory slots (longest slice + G)
+  uint16_t* xtab = nullptr;   // split-row plans: cross-slice rows
 };
 
 // Split-row variants (hv2s_kernel): id, element, V, T, MB.
@@ -117,6 +118,7 @@ static bool kind_usable(int kind, const ed_basis* b, int mode, int ld, KindInfo*
 void hv2_free(Hv2Plan* p) {
   if (!p) return;
   if (p->dtab) cudaFree(p->dtab);
+  if (p->xtab) cudaFree(p->xtab);
   if (p->kpn) cudaFree(p->kpn);
   if (p->slot_lo) cudaFree(p->slot_lo);
   if (p->dn_pad) cudaFree(p->dn_pad);
@@ -209,13 +211,17 @@ struct SplitCache {
   bool ok = false;
 };
 
-static size_t split_smem(const SplitTables& t, const ed_basis* b, size_t esize) {
-  const int MH = b->up.maxhops > 0 ? b->up.maxhops : 1;
-  return ((size_t)(t.zslot + 1) * esize + 15) / 16 * 16 + (size_t)MH * 12;
+static int split_slots(const SplitTables& t) {
+  return std::max(t.cstart[1] - t.cstart[0], t.cstart[2] - t.cstart[1]) + t.G;
 }
 
-// The split tables of this basis for V = 2 (int64 kernel) or V = 4 (FP32 kernel), built on
-// first use from the device basis tables and cached on the basis.
+static size_t split_smem(const SplitTables& t, const ed_basis* b, size_t esize) {
+  const int MH = b->up.maxhops > 0 ? b->up.maxhops : 1;
+  return ((size_t)split_slots(t) * esize + 15) / 16 * 16 + (size_t)MH * 12;
+}
+
+// The split tables of this basis for V = 2, G = 16 (int64 kernel) or V = 4, G = 32 (FP32
+// kernel), built on first use from the device basis tables and cached on the basis.
 static const SplitTables* split_tables(const ed_basis* b, int V, cudaStream_t s) {
   std::lock_guard<std::mutex> lock(g_split_mu);
   auto* cache = static_cast<SplitCache*>(b->hv2_split);
@@ -231,7 +237,7 @@ static const SplitTables* split_tables(const ed_basis* b, int V, cudaStream_t s)
         cudaMemcpyAsync(bits.data(), b->dn.bits, bits.size() * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
       return nullptr;
-    c.ok = build_split_tables(hop.data(), bits.data(), n, mh, V, 0, c.t) == ED_OK;
+    c.ok = build_split_tables(hop.data(), bits.data(), n, mh, V, V == 2 ? 16 : 32, 0, c.t) == ED_OK;
   }
   return c.ok ? &c.t : nullptr;
 }
@@ -279,11 +285,13 @@ static ed_status hv2_build_split(const ed_basis* b, int mode, int ld, cudaStream
   p->smem = split_smem(*t, b, mode == kHv2Fx ? 8 : 4);
   p->ld = ld;
   p->grid = (int)b->up.dim;
-  p->zslot = t->zslot;
+  p->nslots = split_slots(*t);
   for (int i = 0; i < 3; ++i) p->cst[i] = t->cstart[i];
   const int64_t n = b->dn.dim;
   if (cudaMalloc(&p->dtab, t->tab.size() * 2) != cudaSuccess ||
+      cudaMalloc((void**)&p->xtab, t->xtab.size() * 2) != cudaSuccess ||
       cudaMalloc((void**)&p->kpn, t->kpn.size()) != cudaSuccess ||
+      cudaMalloc((void**)&p->slot_lo, (size_t)ld) != cudaSuccess ||
       cudaMalloc((void**)&p->dn_pad, (size_t)ld * 4) != cudaSuccess ||
       cudaMalloc((void**)&p->colpos, (size_t)(n > 0 ? n : 1) * 4) != cudaSuccess) {
     cudaGetLastError();
@@ -292,7 +300,9 @@ static ed_status hv2_build_split(const ed_basis* b, int mode, int ld, cudaStream
     return ED_ERR_OOM;
   }
   cudaError_t e = cudaMemcpyAsync(p->dtab, t->tab.data(), t->tab.size() * 2, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p->xtab, t->xtab.data(), t->xtab.size() * 2, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p->kpn, t->kpn.data(), t->kpn.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p->slot_lo, t->lo.data(), (size_t)ld, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p->dn_pad, t->pad.data(), (size_t)ld * 4, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p->colpos, t->pos.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -447,13 +457,15 @@ ed_status hv2_launch(const Hv2Plan* p, const ed_basis* b, double t, double U, co
     c.up_bits = b->up.bits;
     c.dn_bits = p->dn_pad;
     c.dtab = (const uint16_t*)p->dtab;
-    c.kpn = p->kpn;
+    c.xtab = p->xtab;
+    c.kpn = reinterpret_cast<const uchar4*>(p->kpn);
+    c.slot_lo = p->slot_lo;
     c.hop_up = b->up.hop;
     c.order = b->up_order;
     c.dim_up = b->up.dim;
     c.ld = p->ld;
     c.maxhops_up = b->up.maxhops;
-    c.zslot = p->zslot;
+    c.nslots = p->nslots;
     c.cstart0 = p->cst[0];
     c.cstart1 = p->cst[1];
     c.cstart2 = p->cst[2];

@@ -7,11 +7,13 @@
 //
 // The down states are cut in two slices by the occupation of one site (SplitTables): a hop
 // changes that occupation only when it moves a particle onto or off the site, so most down
-// hops stay inside their slice. One CTA owns one up row and processes it slice by slice: the
-// slice is staged in shared memory (slot = column - slice start, a zero slot after the
-// longer slice), the in-slice down hops gather there, the few cross-slice ones read the row
-// in global memory (it is L2-resident while the CTA works on it), the up part streams the
-// neighbour rows' columns of the slice, and the epilogue is hv2_kernel's.
+// hops stay inside their slice. One CTA owns one up row and processes it slice by slice. A
+// slice is laid out and staged exactly like a whole row of hv2_kernel (R = 1): column order
+// by hop count, slot map (p & ~(G-1)) | lo[p] against bank conflicts, zero slots ld_s ..
+// ld_s + G - 1, per-lane hop order chosen by the host. The in-slice down hops gather from
+// shared memory; the few cross-slice ones have table rows of their own and read the row in
+// global memory (it is L2-resident while the CTA works on it); the up part streams the
+// neighbour rows' columns of the slice; the epilogue is hv2_kernel's.
 #include "ed_hv2_kernel.cuh"
 
 namespace ed {
@@ -19,12 +21,14 @@ namespace ed {
 struct Hv2sArgs {
   const uint32_t* __restrict__ up_bits;
   const uint32_t* __restrict__ dn_bits;  // by column, padded (pads 0)
-  const uint16_t* __restrict__ dtab;     // [rows][ld]: slot | 32768 + column in other slice
-  const uchar2* __restrict__ kpn;        // per chunk of 32 V columns: positive, negative rows
+  const uint16_t* __restrict__ dtab;     // [rows][ld]: slot of the target inside the slice
+  const uint16_t* __restrict__ xtab;     // [xrows][ld]: target column inside the other slice
+  const uchar4* __restrict__ kpn;        // per chunk of 32 V columns: in +, in -, cross +, cross -
+  const uint8_t* __restrict__ slot_lo;   // [ld] slot of column p within its group of G
   const int32_t* __restrict__ hop_up;    // basis table [maxhops_up][dim_up]
   const int32_t* __restrict__ order;     // up-row visit order (NULL = rank order)
   int64_t dim_up;
-  int ld, maxhops_up, zslot;
+  int ld, maxhops_up, nslots;            // nslots: longest slice + G
   int cstart0, cstart1, cstart2;         // slices [cstart0, cstart1), [cstart1, cstart2)
   float t, U;                            // FP32 variant
 };
@@ -39,8 +43,9 @@ hv2s_kernel(Hv2sArgs a, const E* __restrict__ x, E* __restrict__ y,
   if (S->status != 0) return;
   const int ld = a.ld;
   const int MH = a.maxhops_up > 0 ? a.maxhops_up : 1;
+  constexpr int G = hv2_group<E, 1>();
   E* xs = reinterpret_cast<E*>(smem);
-  int64_t* upoff = reinterpret_cast<int64_t*>(smem + ((size_t)(a.zslot + 1) * sizeof(E) + 15) / 16 * 16);
+  int64_t* upoff = reinterpret_cast<int64_t*>(smem + ((size_t)a.nslots * sizeof(E) + 15) / 16 * 16);
   uint32_t* upraw = reinterpret_cast<uint32_t*>(upoff + MH);
   const int64_t g = blockIdx.x;
   const int64_t u = a.order ? (int64_t)a.order[g] : g;
@@ -87,30 +92,42 @@ hv2s_kernel(Hv2sArgs a, const E* __restrict__ x, E* __restrict__ y,
   for (int s = 0; s < 2; ++s) {
     const int c0 = s ? a.cstart1 : a.cstart0, c1 = s ? a.cstart2 : a.cstart1;
     const int oth = s ? a.cstart0 : a.cstart1;  // start of the other slice
-    // ---- stage the slice (the previous slice's gathers are done)
+    const int lds = c1 - c0;
+    // ---- stage the slice through its slot map (the previous slice's gathers are done);
+    // slots lds .. lds + G - 1 are zero, one in each bank group
     __syncthreads();
-    for (int i = threadIdx.x; i < c1 - c0; i += T) xs[i] = xrow[c0 + i];
-    if (threadIdx.x == 0) xs[a.zslot] = E(0);
+    for (int i = threadIdx.x; i < lds + G; i += T)
+      xs[i < lds ? (i & ~(G - 1)) | a.slot_lo[c0 + i] : i] = i < lds ? xrow[c0 + i] : E(0);
     __syncthreads();
     for (int d0 = c0 + threadIdx.x * V; d0 < c1; d0 += T * V) {
       E acc[V];
 #pragma unroll
       for (int v = 0; v < V; ++v) acc[v] = E(0);
-      // ---- down part: in-slice hops from shared memory, cross-slice hops from the row
-      const uchar2 kpn = a.kpn[d0 / (32 * V)];
+      // ---- down part: in-slice hops from shared memory, +1 rows first
+      const uchar4 kpn = a.kpn[d0 / (32 * V)];
       const uint16_t* tp = a.dtab + d0;
-      const int kend = kpn.x + kpn.y;
-      for (int k = 0; k < kend; ++k) {
+      for (int k = 0; k < kpn.x; ++k) {
         const Pack<uint16_t, V> e = *reinterpret_cast<const Pack<uint16_t, V>*>(tp + (size_t)k * ld);
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-          const uint32_t en = e.v[v];
-          const E q = en < 32768u ? xs[en] : xrow[oth + (int)(en - 32768u)];
-          if (k < kpn.x)
-            acc[v] += q;
-          else
-            acc[v] -= q;
-        }
+        for (int v = 0; v < V; ++v) acc[v] += xs[e.v[v]];
+      }
+      for (int k = kpn.x; k < kpn.x + kpn.y; ++k) {
+        const Pack<uint16_t, V> e = *reinterpret_cast<const Pack<uint16_t, V>*>(tp + (size_t)k * ld);
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] -= xs[e.v[v]];
+      }
+      // ---- cross-slice hops from the row in global memory
+      const E* xo = xrow + oth;
+      const uint16_t* xp = a.xtab + d0;
+      for (int k = 0; k < kpn.z; ++k) {
+        const Pack<uint16_t, V> e = *reinterpret_cast<const Pack<uint16_t, V>*>(xp + (size_t)k * ld);
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] += xo[e.v[v]];
+      }
+      for (int k = kpn.z; k < kpn.z + kpn.w; ++k) {
+        const Pack<uint16_t, V> e = *reinterpret_cast<const Pack<uint16_t, V>*>(xp + (size_t)k * ld);
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] -= xo[e.v[v]];
       }
       // ---- up part: the slice's columns of the neighbour rows
       const E* xb = x + d0;
@@ -130,10 +147,11 @@ hv2s_kernel(Hv2sArgs a, const E* __restrict__ x, E* __restrict__ y,
       const Pack<uint32_t, V> db = *reinterpret_cast<const Pack<uint32_t, V>*>(a.dn_bits + d0);
       E* yp = y + u * ld + d0;
       const Pack<E, V> P = ldcs_pack(reinterpret_cast<const Pack<E, V>*>(yp));
+      const Pack<uint8_t, V> lo = *reinterpret_cast<const Pack<uint8_t, V>*>(a.slot_lo + d0);
       Pack<E, V> W;
 #pragma unroll
       for (int v = 0; v < V; ++v) {
-        const E xc = xs[d0 + v - c0];
+        const E xc = xs[((d0 + v - c0) & ~(G - 1)) | lo.v[v]];
         const int n = __popc(ub & db.v[v]);
         if constexpr (sizeof(E) == 4) {
           const float hx = fmaf(-a.t, (float)acc[v], a.U * (float)n * (float)xc);

@@ -263,7 +263,7 @@ static void schedule_gathers(std::vector<int32_t>& tcol, std::vector<uint32_t>& 
 
 ed_status build_down_tables(const int32_t* hop, const int32_t* hopa, const uint32_t* bits,
                             int64_t n, int mh, int ld, int V, int G, bool cplx, DownTables& out) {
-  if (n < 1 || mh < 0 || ld != (int)((n + 31) / 32 * 32) || ld + G - 1 > 0xFFFF ||
+  if (n < 1 || mh < 0 || ld < (int)((n + 31) / 32 * 32) || ld % 32 != 0 || ld + G - 1 > 0xFFFF ||
       !(G == 8 || G == 16 || G == 32) || V < 1 || V > 8 || (mh > 0 && !hop) || !bits) {
     set_error("H.v tables: invalid geometry (n %lld, maxhops %d, ld %d, V %d, G %d)",
               (long long)n, mh, ld, V, G);
@@ -389,96 +389,145 @@ namespace ed {
 
 // Split-row tables: the down states are cut in two slices by the occupation of one site
 // (slice 0: occupied, slice 1: empty); a slice is staged in shared memory at a time, so a
-// row twice as long as shared memory can still be processed row-staged. Columns of slice s
-// are [cstart[s], cstart[s+1]), each slice padded to a multiple of 32 V and its states
-// ordered like the plain tables (hop count, then +1-hop count, descending, then rank). An
-// entry of hop step k of column p: a target in p's own slice is its slot inside the slice
-// (column - cstart[s], < 32768); a target in the other slice is 32768 + (column -
-// cstart[other]) and is read from global memory; padding is the zero slot zslot.
+// row twice as long as shared memory can still be processed row-staged. Each slice gets the
+// plain tables of its own states (build_down_tables on the slice's sub-basis with the hops
+// that stay inside it: column order, slot map, per-lane hop order against bank conflicts,
+// zero slots ld_s .. ld_s + G - 1); slice s occupies the columns [cstart[s], cstart[s+1]),
+// ld_s = cstart[s+1] - cstart[s] a multiple of 32 V with at least one padding column. The
+// hops into the other slice go to rows of their own (xtab: the target's column inside the
+// other slice, read from global memory; padding points at the other slice's last column,
+// a padding column that holds 0). Per chunk of 32 V columns kpn holds four counts: in-slice
+// +1 rows, in-slice -1 rows, cross +1 rows, cross -1 rows.
 ed_status build_split_tables(const int32_t* hop, const uint32_t* bits, int64_t n, int mh, int V,
-                             int site, SplitTables& out) {
-  if (n < 1 || mh < 0 || V < 1 || V > 8 || site < 0 || site > 31) {
+                             int G, int site, SplitTables& out) {
+  if (n < 1 || mh < 0 || V < 1 || V > 8 || site < 0 || site > 31 || !(G == 8 || G == 16 || G == 32)) {
     set_error("split tables: invalid geometry");
     return ED_ERR_ARG;
   }
   const int CW = 32 * V;
-  std::vector<int> npos(n, 0), nneg(n, 0);
-  for (int64_t d = 0; d < n; ++d)
-    for (int k = 0; k < mh; ++k) {
-      const uint32_t e = (uint32_t)hop[(size_t)k * n + d];
-      if ((int64_t)(e & kTargetMask) >= n) continue;
-      ((e & kSignBit) ? nneg : npos)[d]++;
-    }
   std::vector<int64_t> members[2];
-  for (int64_t d = 0; d < n; ++d) members[((bits[d] >> site) & 1u) ? 0 : 1].push_back(d);
-  for (auto& m : members)
-    std::stable_sort(m.begin(), m.end(), [&](int64_t a, int64_t b) {
-      const int ha = npos[a] + nneg[a], hb = npos[b] + nneg[b];
-      if (ha != hb) return ha > hb;
-      if (npos[a] != npos[b]) return npos[a] > npos[b];
-      return a < b;
-    });
-  const int64_t len0 = (int64_t)members[0].size(), len1 = (int64_t)members[1].size();
-  const int64_t p0 = (len0 + CW - 1) / CW * CW, p1 = (len1 + CW - 1) / CW * CW;
-  if (p0 >= 32768 || p1 >= 32768) {
-    set_error("split tables: a slice of %lld columns does not fit the 15-bit slot field",
-              (long long)std::max(p0, p1));
-    return ED_ERR_ARG;
+  std::vector<int> slice((size_t)n), local((size_t)n);
+  for (int64_t d = 0; d < n; ++d) {
+    const int sl = ((bits[d] >> site) & 1u) ? 0 : 1;
+    slice[d] = sl;
+    local[d] = (int)members[sl].size();
+    members[sl].push_back(d);
   }
   out = SplitTables();
   out.V = V;
+  out.G = G;
   out.site = site;
+  int lds[2];
+  for (int sl = 0; sl < 2; ++sl) {
+    const int64_t ns = (int64_t)members[sl].size();
+    lds[sl] = (int)((ns + 1 + CW - 1) / CW * CW);  // at least one padding column
+  }
+  if (lds[0] + G > 32768 || lds[1] + G > 32768) {
+    set_error("split tables: a slice of %d columns does not fit the 15-bit slot field",
+              std::max(lds[0], lds[1]));
+    return ED_ERR_ARG;
+  }
   out.cstart[0] = 0;
-  out.cstart[1] = (int)p0;
-  out.cstart[2] = (int)(p0 + p1);
+  out.cstart[1] = lds[0];
+  out.cstart[2] = lds[0] + lds[1];
   out.ld = out.cstart[2];
-  out.zslot = (int)std::max(p0, p1);
-  out.pos.assign(n, -1);
-  out.pad.assign(out.ld, 0u);
-  std::vector<int64_t> rank_of_col(out.ld, -1);
-  for (int s = 0; s < 2; ++s)
-    for (size_t i = 0; i < members[s].size(); ++i) {
-      const int64_t d = members[s][i];
-      const int col = out.cstart[s] + (int)i;
+  DownTables T[2];
+  std::vector<int32_t> shop;
+  std::vector<uint32_t> sbits;
+  for (int sl = 0; sl < 2; ++sl) {
+    const int64_t ns = (int64_t)members[sl].size();
+    if (ns == 0) {
+      T[sl].ld = lds[sl];
+      T[sl].rows = 0;
+      T[sl].lo.resize((size_t)lds[sl]);
+      for (int p = 0; p < lds[sl]; ++p) T[sl].lo[p] = (uint8_t)(p % G);
+      continue;
+    }
+    // the slice's sub-basis: in-slice hops only, targets as local ranks
+    shop.assign((size_t)mh * ns, (int32_t)ns);
+    sbits.resize((size_t)ns);
+    for (int64_t i = 0; i < ns; ++i) {
+      const int64_t d = members[sl][i];
+      sbits[i] = bits[d];
+      int kk = 0;
+      for (int k = 0; k < mh; ++k) {
+        const uint32_t e = (uint32_t)hop[(size_t)k * n + d];
+        const int64_t t = (int64_t)(e & kTargetMask);
+        if (t >= n || slice[t] != sl) continue;
+        shop[(size_t)kk++ * ns + i] = (int32_t)(((uint32_t)local[t]) | (e & kSignBit));
+      }
+    }
+    const ed_status r = build_down_tables(shop.data(), nullptr, sbits.data(), ns, mh, lds[sl], V, G,
+                                          false, T[sl]);
+    if (r != ED_OK) return r;
+  }
+  // columns, bits, slot map
+  out.pos.assign((size_t)n, -1);
+  out.pad.assign((size_t)out.ld, 0u);
+  out.lo.assign((size_t)out.ld, 0);
+  std::vector<int64_t> rank_of_col((size_t)out.ld, -1);
+  for (int sl = 0; sl < 2; ++sl) {
+    for (size_t i = 0; i < members[sl].size(); ++i) {
+      const int64_t d = members[sl][i];
+      const int col = out.cstart[sl] + T[sl].pos[i];
       out.pos[d] = col;
       out.pad[col] = bits[d];
       rank_of_col[col] = d;
     }
+    for (int p = 0; p < lds[sl]; ++p) out.lo[out.cstart[sl] + p] = T[sl].lo[p];
+  }
   const int nch = out.ld / CW;
-  std::vector<int> kp(nch, 0), kn(nch, 0);
+  std::vector<int> xp((size_t)nch, 0), xn((size_t)nch, 0), xpc((size_t)out.ld, 0), xnc((size_t)out.ld, 0);
   for (int p = 0; p < out.ld; ++p) {
     const int64_t d = rank_of_col[p];
     if (d < 0) continue;
-    kp[p / CW] = std::max(kp[p / CW], npos[d]);
-    kn[p / CW] = std::max(kn[p / CW], nneg[d]);
+    for (int k = 0; k < mh; ++k) {
+      const uint32_t e = (uint32_t)hop[(size_t)k * n + d];
+      const int64_t t = (int64_t)(e & kTargetMask);
+      if (t >= n || slice[t] == slice[d]) continue;
+      ++((e & kSignBit) ? xnc : xpc)[p];
+    }
+    xp[p / CW] = std::max(xp[p / CW], xpc[p]);
+    xn[p / CW] = std::max(xn[p / CW], xnc[p]);
   }
-  out.rows = 0;
-  out.kpn.assign(2 * (size_t)nch, 0);
+  out.rows = std::max(T[0].rows, T[1].rows);
+  out.xrows = 0;
+  out.kpn.assign(4 * (size_t)nch, 0);
   for (int c = 0; c < nch; ++c) {
-    if (kp[c] > 255 || kn[c] > 255) {
-      set_error("split tables: more than 255 hops of one sign");
+    const int sl = c * CW < out.cstart[1] ? 0 : 1;
+    const int lc = (c * CW - out.cstart[sl]) / CW;
+    if (xp[c] > 255 || xn[c] > 255) {
+      set_error("split tables: more than 255 cross-slice hops of one sign");
       return ED_ERR_ARG;
     }
-    out.kpn[2 * c] = (uint8_t)kp[c];
-    out.kpn[2 * c + 1] = (uint8_t)kn[c];
-    out.rows = std::max(out.rows, kp[c] + kn[c]);
+    out.kpn[4 * c] = T[sl].kpn.empty() ? 0 : T[sl].kpn[2 * lc];
+    out.kpn[4 * c + 1] = T[sl].kpn.empty() ? 0 : T[sl].kpn[2 * lc + 1];
+    out.kpn[4 * c + 2] = (uint8_t)xp[c];
+    out.kpn[4 * c + 3] = (uint8_t)xn[c];
+    out.xrows = std::max(out.xrows, xp[c] + xn[c]);
   }
-  out.tab.assign((size_t)out.rows * out.ld, (uint16_t)out.zslot);
+  // in-slice entries: the slice's own slots (zero slots ld_s .. ld_s + G - 1)
+  out.tab.assign((size_t)std::max(out.rows, 1) * out.ld, 0);
+  for (int sl = 0; sl < 2; ++sl)
+    for (int k = 0; k < out.rows; ++k)
+      for (int p = 0; p < lds[sl]; ++p)
+        out.tab[(size_t)k * out.ld + out.cstart[sl] + p] =
+            k < T[sl].rows ? T[sl].tab[(size_t)k * lds[sl] + p] : (uint16_t)lds[sl];
+  // cross-slice entries: the target's column inside the other slice
+  out.xtab.assign((size_t)std::max(out.xrows, 1) * out.ld, 0);
   for (int p = 0; p < out.ld; ++p) {
+    const int sl = p < out.cstart[1] ? 0 : 1, o = 1 - sl, c = p / CW;
+    const uint16_t zero = (uint16_t)(lds[o] - 1);  // a padding column of the other slice
+    for (int k = 0; k < out.xrows; ++k) out.xtab[(size_t)k * out.ld + p] = zero;
     const int64_t d = rank_of_col[p];
     if (d < 0) continue;
-    const int s = p < out.cstart[1] ? 0 : 1, c = p / CW;
     int ip = 0, in = 0;
     for (int k = 0; k < mh; ++k) {
       const uint32_t e = (uint32_t)hop[(size_t)k * n + d];
       const int64_t t = (int64_t)(e & kTargetMask);
-      if (t >= n) continue;
-      const int tc = out.pos[t];
-      const int ts = tc < out.cstart[1] ? 0 : 1;
-      const uint16_t ent = ts == s ? (uint16_t)(tc - out.cstart[s])
-                                   : (uint16_t)(32768 + (tc - out.cstart[ts]));
-      const int row = (e & kSignBit) ? kp[c] + in++ : ip++;
-      out.tab[(size_t)row * out.ld + p] = ent;
+      if (t >= n || slice[t] == sl) continue;
+      const int row = (e & kSignBit) ? xp[c] + in++ : ip++;
+      out.xtab[(size_t)row * out.ld + p] = (uint16_t)(out.pos[t] - out.cstart[o]);
     }
   }
   return ED_OK;
@@ -487,28 +536,31 @@ ed_status build_split_tables(const int32_t* hop, const uint32_t* bits, int64_t n
 }  // namespace ed
 
 extern "C" ed_status ed_hv_split_tables(const int32_t* hop, const uint32_t* bits, int64_t dim,
-                                        int32_t maxhops, int32_t V, int32_t site,
-                                        uint16_t* table, int32_t rows_cap, int32_t cols_cap,
-                                        int32_t* rows, int32_t* ld, int32_t* cstart,
-                                        int32_t* zslot, uint8_t* kpn, int32_t* colpos) {
-  if (!table || !rows || !ld || !cstart || !zslot || !kpn || !colpos) {
+                                        int32_t maxhops, int32_t V, int32_t G, int32_t site,
+                                        uint16_t* table, uint16_t* xtable, int32_t rows_cap,
+                                        int32_t cols_cap, int32_t* rows, int32_t* xrows,
+                                        int32_t* ld, int32_t* cstart, uint8_t* kpn,
+                                        uint8_t* slot_lo, int32_t* colpos) {
+  if (!table || !xtable || !rows || !xrows || !ld || !cstart || !kpn || !slot_lo || !colpos) {
     ed::set_error("ed_hv_split_tables: null output");
     return ED_ERR_ARG;
   }
   ed::SplitTables t;
-  const ed_status r = ed::build_split_tables(hop, bits, dim, maxhops, V, site, t);
+  const ed_status r = ed::build_split_tables(hop, bits, dim, maxhops, V, G, site, t);
   if (r != ED_OK) return r;
   *rows = t.rows;
+  *xrows = t.xrows;
   *ld = t.ld;
-  if (t.rows > rows_cap || t.ld > cols_cap) {
-    ed::set_error("ed_hv_split_tables: %d x %d table, capacity %d x %d", t.rows, t.ld, rows_cap,
-                  cols_cap);
+  if (t.rows > rows_cap || t.xrows > rows_cap || t.ld > cols_cap) {
+    ed::set_error("ed_hv_split_tables: %d + %d rows x %d columns, capacity %d x %d", t.rows,
+                  t.xrows, t.ld, rows_cap, cols_cap);
     return ED_ERR_ARG;
   }
-  std::copy(t.tab.begin(), t.tab.end(), table);
+  std::copy(t.tab.begin(), t.tab.begin() + (size_t)t.rows * t.ld, table);
+  std::copy(t.xtab.begin(), t.xtab.begin() + (size_t)t.xrows * t.ld, xtable);
   for (int i = 0; i < 3; ++i) cstart[i] = t.cstart[i];
-  *zslot = t.zslot;
   std::copy(t.kpn.begin(), t.kpn.end(), kpn);
+  std::copy(t.lo.begin(), t.lo.end(), slot_lo);
   std::copy(t.pos.begin(), t.pos.end(), colpos);
   return ED_OK;
 }

@@ -44,15 +44,17 @@ ed_status build_down_tables(const int32_t* hop, const int32_t* hopa, const uint3
 // Split-row tables (two slices of the down states by the occupation of one site, for rows
 // longer than shared memory): see build_split_tables.
 struct SplitTables {
-  int V = 0, site = 0, ld = 0, rows = 0, zslot = 0;
+  int V = 0, G = 0, site = 0, ld = 0, rows = 0, xrows = 0;
   int cstart[3] = {0, 0, 0};     // slice s: columns [cstart[s], cstart[s+1])
-  std::vector<uint16_t> tab;     // [rows][ld]
-  std::vector<uint8_t> kpn;      // [2 * chunks]: +1 rows, -1 rows
+  std::vector<uint16_t> tab;     // [rows][ld] in-slice slots (zero slots ld_s .. ld_s + G - 1)
+  std::vector<uint16_t> xtab;    // [xrows][ld] target column inside the other slice
+  std::vector<uint8_t> kpn;      // [4 * chunks]: in-slice +1, -1 rows; cross +1, -1 rows
+  std::vector<uint8_t> lo;       // [ld] slot of column p within its aligned group of G
   std::vector<uint32_t> pad;     // [ld] down bit string by column (0 on pads)
   std::vector<int32_t> pos;      // [n] column of each down rank
 };
 
 ed_status build_split_tables(const int32_t* hop, const uint32_t* bits, int64_t n, int mh, int V,
-                             int site, SplitTables& out);
+                             int G, int site, SplitTables& out);
 
 }  // namespace ed

@@ -168,56 +168,90 @@ def test_bad_geometry():
 
 
 SPLIT_CASES = [
-    (12, ed_inputs.ring_bonds(12), 6, 2),     # half filling: equal slices
-    (10, ed_inputs.ring_bonds(10), 3, 4),     # unequal slices (site 0 occupied in 36 of 120)
-    (8, ed_inputs.torus_bonds(2, 4), 4, 1),   # doubled bonds
-    (9, np.array([[0, 5], [3, 8], [1, 2], [7, 0], [6, 4], [2, 8], [5, 1]]), 4, 2),
+    (12, ed_inputs.ring_bonds(12), 6, 2, 16),     # half filling: equal slices
+    (10, ed_inputs.ring_bonds(10), 3, 4, 32),     # unequal slices (site 0 occupied in 36 of 120)
+    (8, ed_inputs.torus_bonds(2, 4), 4, 1, 16),   # doubled bonds
+    (9, np.array([[0, 5], [3, 8], [1, 2], [7, 0], [6, 4], [2, 8], [5, 1]]), 4, 2, 8),
+    (14, ed_inputs.ring_bonds(14), 7, 4, 32),     # the FP32 geometry on a longer row
 ]
 
 
-@pytest.mark.parametrize("L,bonds,N,V", SPLIT_CASES)
-def test_split_tables_keep_every_hop(L, bonds, N, V):
+@pytest.mark.parametrize("L,bonds,N,V,G", SPLIT_CASES)
+def test_split_tables_keep_every_hop(L, bonds, N, V, G):
     """Split-row tables (rows longer than shared memory, staged as two slices cut by the
-    occupation of site 0): each column decodes to exactly its state's hops, by sign, with
-    in-slice targets as slots and cross-slice targets as columns of the other slice; slices
-    hold exactly the states with site 0 occupied / empty; padding points at the zero slot."""
+    occupation of site 0): each slice holds exactly the states with site 0 occupied / empty
+    and at least one padding column; its slot map is a permutation inside aligned groups of
+    G; each column decodes to exactly its state's hops, by sign, the in-slice ones as slots
+    (padding on the slice's zero slots) and the cross-slice ones as columns of the other
+    slice (padding on one of its padding columns); the in-slice gathers keep the modelled
+    bank conflicts of the plain tables."""
     hop, _, bits = hop_table(L, N, bonds)
     n = bits.size
-    out = ed.ed_hv_split_tables(hop, bits, V, site=0)
-    T, kpn, cs, z, pos, ld = out["table"], out["kpn"], out["cstart"], out["zslot"], out["colpos"], out["ld"]
+    out = ed.ed_hv_split_tables(hop, bits, V, G, site=0)
+    T, X, kpn, lo, cs, pos, ld = (out[k] for k in ("table", "xtable", "kpn", "slot_lo", "cstart",
+                                                   "colpos", "ld"))
     CW = 32 * V
-    assert cs[0] == 0 and cs[1] % CW == 0 and cs[2] == ld and ld % CW == 0
     occ = (bits & 1) == 1
-    assert cs[1] == (occ.sum() + CW - 1) // CW * CW
-    assert z == max(cs[1] - cs[0], cs[2] - cs[1])
+    nsl = [int(occ.sum()), int(n - occ.sum())]
+    assert cs[0] == 0 and cs[2] == ld
+    for s_ in range(2):
+        assert cs[s_ + 1] - cs[s_] == (nsl[s_] + 1 + CW - 1) // CW * CW
     # every rank has a distinct column inside its slice
     assert len(set(pos.tolist())) == n
     assert np.all((pos < cs[1]) == occ)
     col2rank = {int(p): d for d, p in enumerate(pos)}
+    assert (np.sort(lo.reshape(-1, G), axis=1) == np.arange(G)).all()
     h = hop.view(np.uint32).astype(np.int64)
-    for p in range(ld):
-        s = 0 if p < cs[1] else 1
-        c = p // CW
-        kp, kn = int(kpn[c, 0]), int(kpn[c, 1])
-        assert T.shape[0] >= kp + kn
-        d = col2rank.get(p)
-        got = {+1: [], -1: []}
-        for k in range(kp + kn):
-            e = int(T[k, p])
-            if e == z:
-                continue
-            if e < 32768:
-                tcol = cs[s] + e
-                assert tcol < cs[s + 1]
-            else:
-                tcol = cs[1 - s] + (e - 32768)
-                assert cs[1 - s] <= tcol < cs[2 - s]
-            got[+1 if k < kp else -1].append(col2rank[tcol])
-        if d is None:
-            assert not got[+1] and not got[-1]    # padding column: only zero slots
-            continue
-        want = {+1: [], -1: []}
-        for k in range(h.shape[0]):
-            if (h[k, d] & 0x3FFFFFFF) < n:
-                want[-1 if (h[k, d] >> 31) & 1 else +1].append(int(h[k, d] & 0x3FFFFFFF))
-        assert sorted(got[+1]) == sorted(want[+1]) and sorted(got[-1]) == sorted(want[-1]), p
+    tgt, neg = h & 0x3FFFFFFF, (h >> 31) & 1
+    for s_ in range(2):
+        c0, c1, o = int(cs[s_]), int(cs[s_ + 1]), 1 - s_
+        lds, ldo = c1 - c0, int(cs[o + 1] - cs[o])
+        slot_of = (np.arange(lds) & ~(G - 1)) | lo[c0:c1]
+        col_of_slot = np.empty(lds, dtype=np.int64)
+        col_of_slot[slot_of] = np.arange(c0, c1)
+        assert (c1 - 1) not in col2rank and (int(cs[o + 1]) - 1) not in col2rank
+        for p in range(c0, c1):
+            c = p // CW
+            ip, im, xp, xm = (int(v) for v in kpn[c])
+            assert T.shape[0] >= ip + im and X.shape[0] >= xp + xm
+            got = {(+1, 0): [], (-1, 0): [], (+1, 1): [], (-1, 1): []}
+            for k in range(ip + im):
+                e = int(T[k, p])
+                assert e < lds + G
+                if e >= lds:
+                    continue
+                got[(+1 if k < ip else -1, 0)].append(int(col_of_slot[e]))
+            for k in range(xp + xm):
+                e = int(X[k, p])
+                assert e < ldo
+                if cs[o] + e in col2rank:
+                    got[(+1 if k < xp else -1, 1)].append(int(cs[o] + e))
+                else:
+                    assert e == ldo - 1
+            d = col2rank.get(p)
+            want = {key: [] for key in got}
+            if d is not None:
+                for k in range(h.shape[0]):
+                    if tgt[k, d] < n:
+                        t = int(tgt[k, d])
+                        want[(-1 if neg[k, d] else +1, int(occ[t] != occ[d]))].append(int(pos[t]))
+            for key in got:
+                assert sorted(got[key]) == sorted(want[key]), (p, key)
+        # per chunk: the rows are the largest counts of the chunk's columns
+        for c in range(c0 // CW, c1 // CW):
+            cols = [col2rank[p] for p in range(c * CW, (c + 1) * CW) if p in col2rank]
+            cnt = np.zeros((4, max(len(cols), 1)), dtype=np.int64)
+            for j, d in enumerate(cols):
+                for k in range(h.shape[0]):
+                    if tgt[k, d] < n:
+                        cnt[2 * int(occ[tgt[k, d]] != occ[d]) + int(neg[k, d]), j] += 1
+            assert list(kpn[c]) == list(cnt.max(axis=1)), c
+        sub = {"table": T[:, c0:c1], "kpn": kpn[c0 // CW:c1 // CW, :2], "ld": lds}
+        assert modelled_wavefronts(sub, V, G, False) < 2.0
+
+
+def test_split_tables_bad_geometry():
+    hop, _, bits = hop_table(8, 4, ed_inputs.ring_bonds(8))
+    with pytest.raises(ed.EdError) as e:
+        ed.ed_hv_split_tables(hop, bits, 2, 12)
+    assert e.value.status == ed.ED_ERR_ARG
