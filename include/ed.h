@@ -246,7 +246,9 @@ void ed_lanczos_destroy(ed_lanczos* st);
 /* ed_lanczos_solve - run Algorithm 1 from f1 (as in ed_lanczos_init) until the convergence
  * test of opts passes, b_{j+1} vanishes, or max_steps; returns E0 (HOST) and the steps
  * taken. alpha, beta, E0_hist (HOST, optional, max_steps entries) receive a_1..a_m,
- * b_2..b_{m+1} and E0(1)..E0(m) (the lowest eigenvalue of T_j after every step). Returns
+ * b_2..b_{m+1} and E0(1)..E0(m) (the lowest eigenvalue of T_j after every step; without a
+ * convergence test (tol = 0) the steps compute E0 only at the stop and the history is
+ * computed after the run, all steps in one launch). Returns
  * ED_OK, ED_BREAKDOWN or ED_ERR_NOT_CONVERGED (E0 still set) or an error. Synchronises.
  * The basis keeps the work vectors and the captured CUDA graph of its last solve per
  * (dtype, schedule) for later solves (released by ed_basis_destroy); concurrent solves on one

@@ -164,6 +164,19 @@ lz_energy_kernel(const LzScalars* S, double* out) {
   if (threadIdx.x == 0) *out = E;
 }
 
+// E0(i) = lambda_min(T_i) for i = 1 .. m - 1, block i - 1 for step i: the history of a run
+// whose steps computed E0 only at the stop step (no convergence test). The steps' scalars are
+// final, so the m - 1 bisections run side by side on as many SMs instead of one after each
+// step on one SM (FP64 multisection: 4-9 rounds of ~9 us each on GB300).
+__global__ void __launch_bounds__(kRedThreads)
+lz_history_kernel(LzScalars* S, int m) {
+  const int i = (int)blockIdx.x + 1;
+  if (i >= m) return;
+  __shared__ double sturm_work[kSturmWork];
+  const double E = sturm_lowest(S->alpha, S->beta, i, NAN, sturm_work);
+  if (threadIdx.x == 0) S->E0[i] = E;
+}
+
 // Eigenvector y of T_m for its lowest eigenvalue lam by inverse iteration (two solves of
 // (T - sigma I) z = r with sigma just below lam, where T - sigma I is positive definite, so
 // the tridiagonal LU without pivoting is stable); one thread. y normalised, y[1..m].
@@ -784,8 +797,9 @@ static ed_status solve_on(ed_lanczos* st, const ed_basis* b, const ed_params* p,
                           const void* f1, double* E0, int32_t* steps, double* alpha, double* beta,
                           double* E0_hist) {
   cudaStream_t s = st->stream;
-  // E0(j) every step when the convergence test or the history needs it, else at the stop
-  const int check = (o->tol > 0.0 || E0_hist) ? 1 : ED_MAX_STEPS + 1;
+  // E0(j) every step when the convergence test needs it, else at the stop step (a history
+  // is then computed after the run, all steps at once)
+  const int check = o->tol > 0.0 ? 1 : ED_MAX_STEPS + 1;
   ed_status r = lz_reset(st, o, f1, check, false);
   if (r != ED_OK) return r;
   if ((r = (o->dtype == ED_F64 ? fx_prepare(b)
@@ -833,6 +847,10 @@ static ed_status solve_on(ed_lanczos* st, const ed_basis* b, const ed_params* p,
     if (hdr[1] != 0 || launched >= o->max_steps) break;
   }
   const int j = hdr[0];
+  if (E0_hist && check > 1 && j > 1) {
+    lz_history_kernel<<<j - 1, kRedThreads, 0, s>>>(st->S, j);
+    ED_TRY_CUDA(cudaGetLastError());
+  }
   std::vector<double> hv(3 * (size_t)(j + 2));
   double* h_alpha = hv.data();
   double* h_beta = h_alpha + (j + 2);

@@ -430,12 +430,14 @@ def test_down_dimension_above_2_15(ed, dtype):
     assert np.allclose(res["beta"], ref.beta, rtol=tol, atol=tol), (res["beta"], ref.beta)
 
 
+@pytest.mark.parametrize("tol", [1e-14, 0.0])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("lattice", ["torus2x4", "ring10"])
-def test_per_step_lowest_ritz_value_matches_lapack(ed, dtype, lattice):
-    """E0(j) reported for every step (device Sturm multisection, warm-started from E0(j-1))
-    equals lambda_min of T_j assembled from the returned a_j, b_j, by LAPACK, to a few ulps
-    of ||T_j||."""
+def test_per_step_lowest_ritz_value_matches_lapack(ed, dtype, lattice, tol):
+    """E0(j) reported for every step equals lambda_min of T_j assembled from the returned a_j,
+    b_j, by LAPACK, to a few ulps of ||T_j||: with a convergence test (tol > 0) each step's
+    device Sturm multisection, warm-started from E0(j-1); without one (tol = 0) the history
+    computed after the run, one multisection per step side by side."""
     import scipy.linalg
     if lattice == "torus2x4":
         L, bonds, nu, nd, U = 8, ed_inputs.torus_bonds(2, 4), 3, 4, 6.0
@@ -443,7 +445,7 @@ def test_per_step_lowest_ritz_value_matches_lapack(ed, dtype, lattice):
         L, bonds, nu, nd, U = 10, ed_inputs.ring_bonds(10), 5, 4, 2.5
     b = ed.ed_build_basis(L, bonds, nu, nd)
     try:
-        res = ed.ed_lanczos_solve(b, 1.0, U, ed.make_opts(max_steps=120, tol=1e-14, seed=3,
+        res = ed.ed_lanczos_solve(b, 1.0, U, ed.make_opts(max_steps=120, tol=tol, seed=3,
                                                           dtype=dtype), raise_not_converged=False)
     finally:
         ed.ed_basis_destroy(b)
@@ -454,6 +456,7 @@ def test_per_step_lowest_ritz_value_matches_lapack(ed, dtype, lattice):
         w = scipy.linalg.eigvalsh_tridiagonal(a[:j], bt[:j - 1], select="i", select_range=(0, 0))
         scale = np.max(np.abs(a[:j])) + (np.max(np.abs(bt[:j - 1])) if j > 1 else 0.0)
         assert abs(hist[j - 1] - w[0]) <= 8 * EPS64 * max(scale, 1.0), (j, hist[j - 1], w[0])
+    assert res["E0"] == hist[n - 1]
 
 
 @pytest.mark.slow
