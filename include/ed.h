@@ -355,7 +355,10 @@ ed_status ed_mlp_train_step(ed_mlp* mlp, const ed_basis* basis, double U, const 
                             int64_t batch, double lr, uint64_t seed, double* loss);
 
 /* ed_mlp_infer - out[i] = predicted amplitude of basis state i at interaction U, for every
- * state of `basis` (DEVICE array of dim, FP32 for ED_F32 else FP64; not normalised). */
+ * state of `basis` (DEVICE array of dim, FP32 for ED_F32 else FP64; not normalised). The
+ * products run on the tensor cores (bfloat16 operands, FP32 accumulation) and tanh on the
+ * special-function unit (relative error about 2^-11); training evaluates tanh exactly to
+ * FP32. */
 ed_status ed_mlp_infer(ed_mlp* mlp, const ed_basis* basis, double U, ed_dtype dtype, void* out);
 
 void ed_mlp_destroy(ed_mlp* mlp);

@@ -9,6 +9,11 @@
 // for every forward pass; FP32 accumulation. The U feature and the first layer's output
 // enter the next product rounded to bfloat16 (the operands of the tensor-core products of
 // the inference kernel); the backward pass treats these roundings as the identity.
+// Inference evaluates tanh with the special-function unit's approximation (PTX
+// tanh.approx.f32, maximum relative error about 2^-11: one instruction instead of the ~19 of
+// an accurate tanhf, which made the inference issue-bound); training uses tanhf. The
+// predicted vector only starts Algorithm 1, so an error of that size in the activations
+// changes nothing the method relies on.
 // Training: samples drawn uniformly from the basis with weight dim * psi^2; loss per sample
 // (a - log|psi|)^2 + log(1 + exp(-sign(psi) z)); deterministic per-CTA gradient partials
 // reduced in a fixed order.
@@ -49,6 +54,13 @@ __host__ __device__ inline MlpDims mlp_dims(int L) {
 
 __device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
+// tanh on the special-function unit (PTX tanh.approx.f32, sm_75 and later)
+__device__ __forceinline__ float tanh_sfu(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Rounded weights into shared memory (sw has P floats).
 __device__ __forceinline__ void load_weights(const float* __restrict__ params, int P, float* sw) {
   for (int i = threadIdx.x; i < P; i += blockDim.x) sw[i] = bf16r(params[i]);
@@ -62,7 +74,8 @@ __device__ __forceinline__ void load_weights(const float* __restrict__ params, i
 // K-major core-matrix layout; one thread issues tcgen05.mma (BF16 x BF16 -> FP32 in TMEM:
 // D1 = X W1 in columns 0..63, D2 = bf16(h1) W2 in columns 64..127) and commits to an
 // mbarrier; every thread then reads its row of the accumulator with tcgen05.ld and applies
-// bias and tanh on the CUDA cores; the 64 -> 2 output layer stays on the CUDA cores.
+// bias (CUDA cores) and tanh (special-function unit); the 64 -> 2 output layer stays on the
+// CUDA cores.
 // Waits on the mbarrier are bounded (1 s of the global timer); on expiry the kernel sets
 // *err, frees its TMEM and returns.
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
@@ -72,7 +85,10 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 
 constexpr int kTcRows = 128;      // states per tile = threads per CTA = TMEM lanes used
 constexpr uint32_t kTcCols = 128;  // TMEM columns: D1 [0, 64), D2 [64, 128)
-constexpr int kTcSmemMin = 61440;  // at most 3 CTAs (384 TMEM columns) per SM
+// At most 4 CTAs per SM (4 x 128 = all 512 TMEM columns, so no allocation ever waits): with
+// 1 KB reserved per CTA, 5 x (46 KB + 1 KB) exceeds the SM's 228 KB.
+constexpr int kTcSmemMin = 47104;
+constexpr int kTcCtasPerSm = 4;
 
 struct TcLayout {
   int K1;
@@ -191,7 +207,8 @@ mlp_infer_tc_kernel(const float* __restrict__ params, int L, float U, const uint
       uint32_t w[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        w[q] = pack_bf16(tanhf(h[j + 2 * q] + sb1[j + 2 * q]), tanhf(h[j + 2 * q + 1] + sb1[j + 2 * q + 1]));
+        w[q] = pack_bf16(tanh_sfu(h[j + 2 * q] + sb1[j + 2 * q]),
+                         tanh_sfu(h[j + 2 * q + 1] + sb1[j + 2 * q + 1]));
       *reinterpret_cast<uint4*>(A2 + cm_offset(tid, j, kH)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
     // ---- layer 2 on the tensor cores
@@ -215,7 +232,7 @@ mlp_infer_tc_kernel(const float* __restrict__ params, int L, float U, const uint
     float a = sb3[0], z = sb3[1];
 #pragma unroll
     for (int n = 0; n < kH; ++n) {
-      const float t = tanhf(h[n] + sb2[n]);
+      const float t = tanh_sfu(h[n] + sb2[n]);
       a = fmaf(t, sW3[2 * n], a);
       z = fmaf(t, sW3[2 * n + 1], z);
     }
@@ -630,7 +647,7 @@ extern "C" ed_status ed_mlp_infer(ed_mlp* M, const ed_basis* b, double U, ed_dty
   const TcLayout ly = tc_layout(M->d.nin);
   const int sm = (int)std::max<uint32_t>(ly.total, (uint32_t)kTcSmemMin);
   const int64_t ntiles = (b->dim + kTcRows - 1) / kTcRows;
-  const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sm_count() * 3);
+  const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sm_count() * kTcCtasPerSm);
   ED_TRY_CUDA(cudaMemsetAsync(M->err, 0, sizeof(int), M->stream));
   if (dtype == ED_F32) {
     ED_TRY_CUDA(allow_max_smem(mlp_infer_tc_kernel<float>));

@@ -90,49 +90,22 @@ def test_mlp_gradient_vs_oracle(ed):
         ed.ed_basis_destroy(b)
 
 
+# The inference evaluates tanh on the special-function unit (PTX tanh.approx.f32); the PTX ISA
+# states a maximum relative error of about 2^-11 for it. Taken with a factor-2 margin:
+EPS_TANH = 2.0 ** -10
+
+
 @pytest.mark.parametrize("fill", [(3, 4), (3, 0)])
-def test_mlp_inference_vs_oracle(ed, fill):
+def test_mlp_inference_vs_unrounded_forward(ed, fill):
+    """The network evaluated in FP64 with bfloat16 weights, exact tanh and without rounding the
+    first layer's output or the U input (the plain definition of the network on rounded
+    parameters) against the GPU's tensor-core inference, which feeds the second layer
+    bfloat16 activations and bfloat16(U/8) and evaluates tanh with the approximation above:
+    the difference must stay inside the bound those roundings (bfloat16: relative 2^-8 at
+    most, taken twice as a margin; tanh: EPS_TANH) propagate through the layers (tanh is
+    1-Lipschitz), plus FP32 accumulation at every layer. Fill (3, 0) has an empty species."""
     L, U = 8, 2.5
     nu, nd = fill
-    b = ed.ed_build_basis(L, ed_inputs.ring_bonds(L), nu, nd)
-    net = ed.ed_mlp_create(L, 11)
-    try:
-        dim = ed.ed_basis_dims(b)[2]
-        P = omlp.param_count(L)
-        params = (np.random.default_rng(5).normal(size=P) * 0.3).astype(np.float32)
-        _set_params(ed, net, params)
-        out = torch.empty(dim, dtype=torch.float64, device="cuda")
-        ed.ed_mlp_infer(net, b, U, out)
-        got = out.cpu().numpy()
-        up = obasis.species_states(L, nu)
-        dn = obasis.species_states(L, nd)
-        g = np.arange(dim)
-        x = omlp.features(up[g // len(dn)], dn[g % len(dn)], L, U)
-        a, z, (_, h1, _) = omlp.forward(params.astype(np.float64), x, L)
-        ref = np.where(z >= 0, 1.0, -1.0) * np.exp(a)
-        # compare where FP32 and FP64 take the same discrete decisions: the sign of z, and the
-        # bfloat16 rounding of every first-layer output (skip states with an h1 value within
-        # 1e-4 bfloat16 ulp of a rounding midpoint; FP32 errors are about 3e-5 ulp)
-        ulp = 2.0 ** (np.floor(np.log2(np.maximum(np.abs(h1), 1e-30))) - 7)
-        frac = np.abs(h1) / ulp
-        margin = np.min(np.abs(frac - np.floor(frac) - 0.5), axis=1)
-        decided = (np.abs(z) > 1e-4) & (margin > 1e-4)
-        assert decided.mean() > 0.95
-        assert np.all(np.abs(got[decided] - ref[decided]) <= 2e-5 * np.abs(ref[decided]))
-    finally:
-        ed.ed_mlp_destroy(net)
-        ed.ed_basis_destroy(b)
-
-
-def test_mlp_inference_vs_unrounded_forward(ed):
-    """The network evaluated with bfloat16 weights but without rounding the first layer's
-    output or the U input (the plain definition of the network on rounded parameters)
-    against the GPU's tensor-core inference, which feeds the second layer bfloat16
-    activations and bfloat16(U/8): the difference must stay inside the bound those two
-    roundings (relative 2^-8 at most, taken twice as a margin) propagate through the
-    layers (tanh is 1-Lipschitz), plus FP32 accumulation at every layer."""
-    L, U = 8, 2.5
-    nu, nd = 3, 4
     b = ed.ed_build_basis(L, ed_inputs.ring_bonds(L), nu, nd)
     net = ed.ed_mlp_create(L, 13)
     try:
@@ -154,22 +127,23 @@ def test_mlp_inference_vs_unrounded_forward(ed):
     a, z, (_, h1, h2) = omlp.forward(pr, x, L, round_weights=False)
     W1, b1, W2, b2, W3, b3 = omlp.unpack(pr, L)
     u = 2.0 ** -8
-    f32 = 1e-5                                                     # FP32 sums and tanhf
+    f32 = 1e-5                                                     # FP32 sums
     dh1 = np.abs(W1[2 * L]) * abs(U / 8.0) * u                  # bf16(U/8)
     dh1 = dh1[None, :] + f32 * (np.abs(x) @ np.abs(W1) + np.abs(b1)[None, :])
+    dh1 = dh1 + EPS_TANH * (np.abs(h1) + dh1)                    # approximate tanh
     dh1 = dh1 + (np.abs(h1) + dh1) * u                           # bf16(h1)
     dh2 = dh1 @ np.abs(W2) + f32 * (np.abs(h1) @ np.abs(W2) + np.abs(b2)[None, :])
+    dh2 = dh2 + EPS_TANH * (np.abs(h2) + dh2)                    # approximate tanh
     acc = f32 * (np.abs(h2) @ np.abs(W3) + np.abs(b3)[None, :])
     da = dh2 @ np.abs(W3[:, 0]) + acc[:, 0]
     dz = dh2 @ np.abs(W3[:, 1]) + acc[:, 1]
     sure = np.abs(z) > dz
-    assert sure.mean() > 0.5
+    assert sure.mean() > 0.3   # the sign check is not vacuous
     assert np.all(np.sign(got[sure]) == np.where(z[sure] >= 0, 1.0, -1.0))
     err = np.abs(np.log(np.abs(got)) - a)
     assert np.all(err <= da), float(np.max(err / da))
-    # the bound adds every rounding with the worst sign; actual roundings are of random sign
-    # (on the CPU, the oracle's rounded forward pass sits at a median of 0.3% of the bound)
-    assert np.median(err / da) < 0.05
+    # the bound adds every rounding with the worst sign; actual roundings are of mixed sign
+    assert np.median(err / da) < 0.25
     assert np.median(err) > 0.0   # the roundings are really there: not a tautology
 
 
