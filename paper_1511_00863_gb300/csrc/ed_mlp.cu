@@ -71,9 +71,10 @@ __device__ __forceinline__ void load_weights(const float* __restrict__ params, i
 // 5th-generation tensor cores: a CTA of 4 warps evaluates tiles of 128 basis states, one
 // state per thread (TMEM lane). The features of the tile (bits as 0/1, bf16(U/8), zero
 // padding to K1 = 16 ceil(nin/16)) and later bf16(h1) are written to shared memory in the
-// K-major core-matrix layout; one thread issues tcgen05.mma (BF16 x BF16 -> FP32 in TMEM:
-// D1 = X W1 in columns 0..63, D2 = bf16(h1) W2 in columns 64..127) and commits to an
-// mbarrier; every thread then reads its row of the accumulator with tcgen05.ld and applies
+// K-major core-matrix layout; one thread issues tcgen05.mma (BF16 x BF16 -> FP32 in TMEM
+// columns 0..63: D1 = X W1, then D2 = bf16(h1) W2 over it, once every thread has read D1)
+// and commits to an mbarrier; every thread then reads its row of the accumulator with
+// tcgen05.ld and applies
 // bias (CUDA cores) and tanh (special-function unit); the 64 -> 2 output layer stays on the
 // CUDA cores.
 // Waits on the mbarrier are bounded (1 s of the global timer); on expiry the kernel sets
@@ -84,11 +85,12 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 }
 
 constexpr int kTcRows = 128;      // states per tile = threads per CTA = TMEM lanes used
-constexpr uint32_t kTcCols = 128;  // TMEM columns: D1 [0, 64), D2 [64, 128)
-// At most 4 CTAs per SM (4 x 128 = all 512 TMEM columns, so no allocation ever waits): with
-// 1 KB reserved per CTA, 5 x (46 KB + 1 KB) exceeds the SM's 228 KB.
-constexpr int kTcSmemMin = 47104;
-constexpr int kTcCtasPerSm = 4;
+constexpr uint32_t kTcCols = 64;   // TMEM columns of D1, then of D2
+// At most 8 CTAs per SM (8 x 64 = all 512 TMEM columns, so no allocation ever waits): with
+// 1 KB reserved per CTA, 9 x (25 KB + 1 KB) exceeds the SM's 228 KB. The register bound
+// (launch bounds) makes 5 resident; the grid is one wave of them.
+constexpr int kTcSmemMin = 25600;
+constexpr int kTcCtasPerSm = 5;
 
 struct TcLayout {
   int K1;
@@ -111,7 +113,7 @@ __host__ __device__ inline TcLayout tc_layout(int nin) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kTcRows)
+__global__ void __launch_bounds__(kTcRows, kTcCtasPerSm)
 mlp_infer_tc_kernel(const float* __restrict__ params, int L, float U, const uint32_t* __restrict__ upb,
                     const uint32_t* __restrict__ dnb, int64_t dim_dn, int64_t dim, T* __restrict__ out,
                     int* __restrict__ err) {
@@ -218,7 +220,7 @@ mlp_infer_tc_kernel(const float* __restrict__ params, int L, float U, const uint
     if (tid == 0) {
       tc_fence_after_sync();
       for (int s = 0; s < kH / 16; ++s)
-        tc_mma_f16(tmem + kH, tc_smem_desc(a2s + s * 256, 128, sbo2), tc_smem_desc(b2s + s * 256, 128, sbo2),
+        tc_mma_f16(tmem, tc_smem_desc(a2s + s * 256, 128, sbo2), tc_smem_desc(b2s + s * 256, 128, sbo2),
                    idesc, s > 0);
       tc_commit(mbar);
     }
@@ -226,8 +228,8 @@ mlp_infer_tc_kernel(const float* __restrict__ params, int L, float U, const uint
     phase ^= 1u;
     if (!ok) break;
     tc_fence_after_sync();
-    tc_ld32(tmem + lanes + kH, h);
-    tc_ld32(tmem + lanes + kH + 32, h + 32);
+    tc_ld32(tmem + lanes, h);
+    tc_ld32(tmem + lanes + 32, h + 32);
     // ---- output layer on the CUDA cores
     float a = sb3[0], z = sb3[1];
 #pragma unroll
@@ -647,15 +649,21 @@ extern "C" ed_status ed_mlp_infer(ed_mlp* M, const ed_basis* b, double U, ed_dty
   const TcLayout ly = tc_layout(M->d.nin);
   const int sm = (int)std::max<uint32_t>(ly.total, (uint32_t)kTcSmemMin);
   const int64_t ntiles = (b->dim + kTcRows - 1) / kTcRows;
-  const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sm_count() * kTcCtasPerSm);
+  ED_TRY_CUDA(allow_max_smem(mlp_infer_tc_kernel<float>));
+  ED_TRY_CUDA(allow_max_smem(mlp_infer_tc_kernel<double>));
+  // one wave of resident CTAs: kTcCtasPerSm while the shared memory allows them, else fewer
+  int dev = 0, sm_bytes = 0, reserved = 0;
+  ED_TRY_CUDA(cudaGetDevice(&dev));
+  ED_TRY_CUDA(cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  ED_TRY_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+  const int per_sm = std::max(1, std::min(kTcCtasPerSm, sm_bytes / (sm + reserved)));
+  const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sm_count() * per_sm);
   ED_TRY_CUDA(cudaMemsetAsync(M->err, 0, sizeof(int), M->stream));
   if (dtype == ED_F32) {
-    ED_TRY_CUDA(allow_max_smem(mlp_infer_tc_kernel<float>));
     mlp_infer_tc_kernel<float><<<grid, kTcRows, sm, M->stream>>>(
         M->params, M->L, (float)U, b->user_up().bits, b->user_dn().bits, b->user_dn().dim, b->dim,
         (float*)out, M->err);
   } else {
-    ED_TRY_CUDA(allow_max_smem(mlp_infer_tc_kernel<double>));
     mlp_infer_tc_kernel<double><<<grid, kTcRows, sm, M->stream>>>(
         M->params, M->L, (float)U, b->user_up().bits, b->user_dn().bits, b->user_dn().dim, b->dim,
         (double*)out, M->err);
