@@ -300,6 +300,27 @@ ed_status ed_lanczos_solve_batched(int32_t n, const ed_basis* const* bases,
                                    double* E0, int32_t* steps, int32_t* status,
                                    int32_t* schedule_used);
 
+/* ed_lanczos_solve_batched_mixed - E0 of n independent instances to FP64 accuracy with most
+ * steps in FP32, in one persistent cooperative kernel launch (the batched form of
+ * ed_lanczos_solve_mixed). Per instance: Algorithm 1 (Sec. 2.2) in FP32 as in
+ * ed_lanczos_solve_batched (opts: dtype ED_F32, max_steps, tol checked every 4 steps, seed,
+ * schedule), keeping its Lanczos vectors on the device (Sum_i dim_i x max_steps x 4 bytes,
+ * drawn from a memory pool of the library that keeps the memory reserved in the process for
+ * later batched mixed solves; ED_ERR_OOM if it is not available); the eigenvector y of T_m
+ * for its lowest eigenvalue by
+ * inverse iteration; the Ritz vector psi = sum_j y_j f_j assembled in FP64; then Algorithm 1
+ * in FP64 (ED_F64_NATIVE arithmetic) from psi for at most refine_steps (1..ED_MAX_STEPS)
+ * steps, with E0 checked every step against refine_tol. Outputs (HOST arrays of n, all but
+ * E0 optional): E0[i] of the FP64 phase, steps32[i] and steps64[i] of the two phases,
+ * status[i] of the FP64 phase (as in ed_lanczos_solve_batched), *schedule_used. Returns
+ * ED_ERR_NOT_CONVERGED if some refinement hit refine_steps with refine_tol > 0,
+ * ED_ERR_TIMEOUT if a group barrier's bounded wait ran out. Synchronises `stream`. */
+ed_status ed_lanczos_solve_batched_mixed(int32_t n, const ed_basis* const* bases,
+                                         const ed_params* params, const ed_opts* opts,
+                                         int32_t refine_steps, double refine_tol, void* stream,
+                                         double* E0, int32_t* steps32, int32_t* steps64,
+                                         int32_t* status, int32_t* schedule_used);
+
 /* ed_lanczos_ground_state - the ground-state vector: Algorithm 1 to convergence (ED_F64
  * only), the eigenvector y of T_m for its lowest eigenvalue (inverse iteration on the
  * device), then the same Lanczos vectors regenerated from f1 and summed, psi = sum_j y_j

@@ -76,6 +76,10 @@ _SIGS = {
     "ed_lanczos_solve_batched": (c_int, [c_int32, POINTER(c_void_p), POINTER(ed_params),
                                          POINTER(ed_opts), c_void_p, POINTER(c_double),
                                          POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)]),
+    "ed_lanczos_solve_batched_mixed": (c_int, [c_int32, POINTER(c_void_p), POINTER(ed_params),
+                                               POINTER(ed_opts), c_int32, c_double, c_void_p,
+                                               POINTER(c_double), POINTER(c_int32), POINTER(c_int32),
+                                               POINTER(c_int32), POINTER(c_int32)]),
     "ed_selftest_barrier_timeout": (c_int, [c_int32, c_int32, c_void_p]),
     "ed_lanczos_ground_state": (c_int, [c_void_p, POINTER(ed_params), POINTER(ed_opts), c_void_p,
                                         c_void_p, c_void_p, POINTER(c_double), POINTER(c_int32)]),
@@ -385,6 +389,27 @@ def ed_lanczos_solve_batched(bases, ts, Us, opts: ed_opts, stream=None,
     if s < 0 and not (s == ED_ERR_NOT_CONVERGED and not raise_not_converged):
         _check(s)
     return dict(status=s, E0=np.array(E0[:]), steps=np.array(steps[:]),
+                inst_status=np.array(status[:]), schedule=used.value)
+
+
+def ed_lanczos_solve_batched_mixed(bases, ts, Us, opts: ed_opts, refine_steps: int = 32,
+                                   refine_tol: float = 1e-12, stream=None,
+                                   raise_not_converged: bool = True) -> dict:
+    """All instances in one persistent launch: FP32 Lanczos (opts), Ritz vector, FP64
+    refinement (see include/ed.h)."""
+    n = len(bases)
+    arr = (c_void_p * n)(*[b.value if isinstance(b, c_void_p) else b for b in bases])
+    params = (ed_params * n)(*[ed_params(float(t), float(u)) for t, u in zip(ts, Us)])
+    E0 = (c_double * n)()
+    s32 = (c_int32 * n)()
+    s64 = (c_int32 * n)()
+    status = (c_int32 * n)()
+    used = c_int32()
+    s = _lib.ed_lanczos_solve_batched_mixed(n, arr, params, byref(opts), refine_steps, refine_tol,
+                                            _stream(stream), E0, s32, s64, status, byref(used))
+    if s < 0 and not (s == ED_ERR_NOT_CONVERGED and not raise_not_converged):
+        _check(s)
+    return dict(status=s, E0=np.array(E0[:]), steps32=np.array(s32[:]), steps64=np.array(s64[:]),
                 inst_status=np.array(status[:]), schedule=used.value)
 
 

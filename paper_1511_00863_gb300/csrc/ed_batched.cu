@@ -40,6 +40,12 @@ struct BInst {
   void* B0;  // two work vectors of the instance (FP32 or FP64 elements)
   void* B1;
   double t, U;
+  // mixed solves only: the FP32 phase's Lanczos vectors (raw, [max_steps][dpad]) and the
+  // FP64 refinement's two work vectors
+  float* V;
+  double* D0;
+  double* D1;
+  int dpad;
 };
 
 // Per-instance results and Lanczos scalars (1-based a_j, b_j like LzScalars).
@@ -75,6 +81,34 @@ struct BArgs {
   double tol;
   uint64_t seed;
   long long max_spin;
+  // mixed solves only (batched_ritz_kernel and the refinement): per instance the FP32
+  // vectors' scales, y and the inverse iteration's workspace ([n_inst][4 (max_steps + 2)]:
+  // vscale | y | 2 (max_steps + 2) of work), the refinement's state and scalars
+  BState* st2;
+  double* rwork;
+  double* alpha2;  // [n_inst][refine_steps + 2]
+  double* beta2;
+  double* E02;
+  int refine_steps;
+  double refine_tol;
+  int refine;  // batched_lanczos_kernel<double>: run the refinement of a mixed solve
+  int store;   // batched_lanczos_kernel<float>: keep the Lanczos vectors (mixed solves)
+};
+
+// One instance's run of Algorithm 1, for the CTAs of its group.
+struct RunSpec {
+  BState* S;
+  double* al;
+  double* be;
+  double* e0;
+  void* B0;
+  void* B1;
+  const double* f1;   // FP64 start vector (unnormalised) or NULL for the seeded one
+  float* V;           // store the raw FP32 vector of every step here ([max_steps][dpad]), or NULL
+  double* vscale;     // with V: the scale of the stored vector of step j at vscale[j]
+  int dpad;
+  int max_steps, check;
+  double tol;
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -149,118 +183,85 @@ __device__ __forceinline__ double group_sum(const double* part, int first, int g
 
 // T = float (ED_F32) or double (ED_F64_NATIVE): vector elements and H.v arithmetic; the
 // scalars are FP64 either way.
+// Algorithm 1 for instance I on its group (CTA c of g, leader = c == 0), FP32 or FP64
+// vectors T, as specified by R. Returns false when a group barrier's bounded wait ran out.
 template <typename T>
-__global__ void __launch_bounds__(kBThreads, 4)
-batched_lanczos_kernel(BArgs a) {
+__device__ bool run_instance(const BArgs& a, const BInst& I, const RunSpec& R, int c, int g,
+                             int first_cta, unsigned* bc, unsigned* bg, double* red, int* stop_s,
+                             unsigned char* bsm) {
   constexpr int kRowElems = kBSmemBytes / (int)sizeof(T);  // staged elements of a row block
-  __shared__ double red[33];
-  __shared__ int stop_s;
-  __shared__ __align__(16) unsigned char bsm[kBSmemBytes];
   T* xsm = reinterpret_cast<T*>(bsm);
-  const int gi = a.group_of_cta[blockIdx.x];
-  const BGroup G = a.groups[gi];
-  const int c = blockIdx.x - G.first_cta, g = G.ncta;
   const bool leader = c == 0;
   const bool multi = g > 1;
-  const int stride = a.max_steps + 2;
-  unsigned* bc = a.bar_count + gi;
-  unsigned* bg = a.bar_gen + gi;
-  for (int oi = G.inst_begin; oi < G.inst_end; ++oi) {
-    const int id = a.order[oi];
-    const BInst I = a.inst[id];
-    BState* S = a.st + id;
-    double* al = a.alpha + (size_t)id * stride;
-    double* be = a.beta + (size_t)id * stride;
-    double* e0 = a.E0 + (size_t)id * stride;
-    const int dim = I.dim_up * I.dim_dn;
-    const int64_t gt = (int64_t)g * blockDim.x;
-    const int64_t t0 = (int64_t)c * blockDim.x + threadIdx.x;
-    // ---- start vector: raw SplitMix64 values, FP64 norm, normalised then rounded
-    {
-      double v = 0.0;
-      for (int64_t e = t0; e < dim; e += gt) {
-        const double x = bstart_element(a.seed, (uint64_t)e);
-        v = fma(x, x, v);
-      }
-      v = block_sum(v, red);
-      if (threadIdx.x == 0) a.part_a[blockIdx.x] = v;
-      if (!group_barrier(bc, bg, g, a.max_spin, a.error)) return;
-      const double inv = 1.0 / sqrt(group_sum(a.part_a, G.first_cta, g, red));
-      for (int64_t e = t0; e < dim; e += gt) {
-        ((T*)I.B0)[e] = (T)(bstart_element(a.seed, (uint64_t)e) * inv);
-        ((T*)I.B1)[e] = T(0);
-      }
-      if (leader && threadIdx.x == 0) {
-        S->j = 0;
-        S->status = 0;
-        S->scale[0] = 1.0;
-        S->scale[1] = 0.0;
-        S->tscale = 0.0;
-        S->last_E0_step = 0;
-        S->last_E0 = 0.0;
-        be[1] = 0.0;
-      }
-      if (!group_barrier(bc, bg, g, a.max_spin, a.error)) return;
+  BState* S = R.S;
+  double* al = R.al;
+  double* be = R.be;
+  double* e0 = R.e0;
+  const int dim = I.dim_up * I.dim_dn;
+  const int64_t gt = (int64_t)g * blockDim.x;
+  const int64_t t0 = (int64_t)c * blockDim.x + threadIdx.x;
+  // ---- start vector: raw values (SplitMix64 or the given FP64 vector), FP64 norm,
+  // normalised then rounded
+  {
+    double v = 0.0;
+    for (int64_t e = t0; e < dim; e += gt) {
+      const double x = R.f1 ? ld_shared_f(R.f1 + e, multi) : bstart_element(a.seed, (uint64_t)e);
+      v = fma(x, x, v);
     }
-    int cur = 0;
-    for (int j = 1; j <= a.max_steps; ++j) {
-      T* xc = (T*)(cur ? I.B1 : I.B0);
-      T* xp = (T*)(cur ? I.B0 : I.B1);
-      // ---- phase 1: fused H.v
-      const T sc = (T)__ldcg(&S->scale[cur]);
-      const T bsp = (T)(__ldcg(&be[j]) * __ldcg(&S->scale[1 - cur]));
-      const T tt = (T)I.t, UU = (T)I.U;
-      DotAcc<T> dot;
-      if (I.dim_dn <= kRowElems) {
-        // blocks of BR consecutive up rows staged in shared memory (coalesced loads; from L2
-        // when other CTAs of the group wrote them): down-hop gathers read shared memory,
-        // up-hop gathers read whole neighbour rows coalesced
-        const int BR = max(1, min(kRowElems, 2048) / I.dim_dn);
-        const int nblk = (I.dim_up + BR - 1) / BR;
-        for (int blk = c; blk < nblk; blk += g) {
-          const int u0 = blk * BR;
-          const int nr = min(BR, I.dim_up - u0);
-          const int nel = nr * I.dim_dn;
-          const T* xb = xc + (int64_t)u0 * I.dim_dn;
-          for (int i = threadIdx.x; i < nel; i += blockDim.x) xsm[i] = ld_shared_f(xb + i, multi);
-          __syncthreads();
-          for (int i = threadIdx.x; i < nel; i += blockDim.x) {
-            const int r = i / I.dim_dn, d = i - r * I.dim_dn, u = u0 + r;
-            const T* xr = xsm + r * I.dim_dn;
-            T acc = T(0);
-            for (int k = 0; k < I.mhd; ++k) {
-              const uint32_t en = (uint32_t)I.hd[(int64_t)k * I.dim_dn + d];
-              const uint32_t tg = en & kTargetMask;
-              if (tg >= (uint32_t)I.dim_dn) break;
-              const T v = xr[tg];
-              acc += (en & kSignBit) ? -v : v;
-            }
-            for (int k = 0; k < I.mhu; ++k) {
-              const uint32_t en = (uint32_t)I.hu[(int64_t)k * I.dim_up + u];
-              const uint32_t tg = en & kTargetMask;
-              if (tg >= (uint32_t)I.dim_up) break;
-              const T v = ld_shared_f(xc + (int64_t)tg * I.dim_dn + d, multi);
-              acc += (en & kSignBit) ? -v : v;
-            }
-            const T xv = xsm[i];
-            const int64_t e = (int64_t)u0 * I.dim_dn + i;
-            const T hx = fma(-tt, acc, UU * (T)__popc(I.upb[u] & I.dnb[d]) * xv);
-            const T w = fma(sc, hx, -bsp * ld_shared_f(xp + e, multi));
-            xp[e] = w;
-            dot.add(w, sc * xv);
-          }
-          __syncthreads();
-        }
-      } else {
-        for (int64_t e = t0; e < dim; e += gt) {
-          const int u = (int)(e / I.dim_dn), d = (int)(e - (int64_t)u * I.dim_dn);
-          const T* xr = xc + (int64_t)u * I.dim_dn;
+    v = block_sum(v, red);
+    if (threadIdx.x == 0) a.part_a[blockIdx.x] = v;
+    if (!group_barrier(bc, bg, g, a.max_spin, a.error)) return false;
+    const double inv = 1.0 / sqrt(group_sum(a.part_a, first_cta, g, red));
+    for (int64_t e = t0; e < dim; e += gt) {
+      const double x = R.f1 ? ld_shared_f(R.f1 + e, multi) : bstart_element(a.seed, (uint64_t)e);
+      ((T*)R.B0)[e] = (T)(x * inv);
+      ((T*)R.B1)[e] = T(0);
+    }
+    if (leader && threadIdx.x == 0) {
+      S->j = 0;
+      S->status = 0;
+      S->scale[0] = 1.0;
+      S->scale[1] = 0.0;
+      S->tscale = 0.0;
+      S->last_E0_step = 0;
+      S->last_E0 = 0.0;
+      be[1] = 0.0;
+    }
+    if (!group_barrier(bc, bg, g, a.max_spin, a.error)) return false;
+  }
+  int cur = 0;
+  for (int j = 1; j <= R.max_steps; ++j) {
+    T* xc = (T*)(cur ? R.B1 : R.B0);
+    T* xp = (T*)(cur ? R.B0 : R.B1);
+    float* vj = R.V ? R.V + (size_t)(j - 1) * R.dpad : nullptr;
+    if (vj && leader && threadIdx.x == 0) R.vscale[j] = __ldcg(&S->scale[cur]);
+    // ---- phase 1: fused H.v
+    const T sc = (T)__ldcg(&S->scale[cur]);
+    const T bsp = (T)(__ldcg(&be[j]) * __ldcg(&S->scale[1 - cur]));
+    const T tt = (T)I.t, UU = (T)I.U;
+    DotAcc<T> dot;
+    if (I.dim_dn <= kRowElems) {
+      // blocks of BR consecutive up rows staged in shared memory (coalesced loads; from L2
+      // when other CTAs of the group wrote them): down-hop gathers read shared memory,
+      // up-hop gathers read whole neighbour rows coalesced
+      const int BR = max(1, min(kRowElems, 2048) / I.dim_dn);
+      const int nblk = (I.dim_up + BR - 1) / BR;
+      for (int blk = c; blk < nblk; blk += g) {
+        const int u0 = blk * BR;
+        const int nr = min(BR, I.dim_up - u0);
+        const int nel = nr * I.dim_dn;
+        const T* xb = xc + (int64_t)u0 * I.dim_dn;
+        for (int i = threadIdx.x; i < nel; i += blockDim.x) xsm[i] = ld_shared_f(xb + i, multi);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nel; i += blockDim.x) {
+          const int r = i / I.dim_dn, d = i - r * I.dim_dn, u = u0 + r;
+          const T* xr = xsm + r * I.dim_dn;
           T acc = T(0);
           for (int k = 0; k < I.mhd; ++k) {
             const uint32_t en = (uint32_t)I.hd[(int64_t)k * I.dim_dn + d];
             const uint32_t tg = en & kTargetMask;
             if (tg >= (uint32_t)I.dim_dn) break;
-            const T v = ld_shared_f(xr + tg, multi);
+            const T v = xr[tg];
             acc += (en & kSignBit) ? -v : v;
           }
           for (int k = 0; k < I.mhu; ++k) {
@@ -270,71 +271,194 @@ batched_lanczos_kernel(BArgs a) {
             const T v = ld_shared_f(xc + (int64_t)tg * I.dim_dn + d, multi);
             acc += (en & kSignBit) ? -v : v;
           }
-          const T xv = ld_shared_f(xr + d, multi);
+          const T xv = xsm[i];
+          const int64_t e = (int64_t)u0 * I.dim_dn + i;
           const T hx = fma(-tt, acc, UU * (T)__popc(I.upb[u] & I.dnb[d]) * xv);
           const T w = fma(sc, hx, -bsp * ld_shared_f(xp + e, multi));
           xp[e] = w;
+          if (vj) vj[e] = (float)xv;
           dot.add(w, sc * xv);
         }
-      }
-      {
-        const double v = block_sum(dot.get(), red);
-        if (threadIdx.x == 0) a.part_a[blockIdx.x] = v;
-      }
-      if (!group_barrier(bc, bg, g, a.max_spin, a.error)) return;
-      // ---- phase 2: a_j, update
-      const double alpha = group_sum(a.part_a, G.first_cta, g, red);
-      if (leader && threadIdx.x == 0) al[j] = alpha;
-      const T coef = (T)(alpha * __ldcg(&S->scale[cur]));
-      DotAcc<T> q2;
-      // (phase 1 wrote w by row blocks: other CTAs' values are read from L2)
-      for (int64_t e = t0; e < dim; e += gt) {
-        const T q = ld_shared_f(xp + e, multi) - coef * ld_shared_f(xc + e, multi);
-        xp[e] = q;
-        q2.add(q, q);
-      }
-      {
-        const double v = block_sum(q2.get(), red);
-        if (threadIdx.x == 0) a.part_b[blockIdx.x] = v;
-      }
-      if (!group_barrier(bc, bg, g, a.max_spin, a.error)) return;
-      // ---- phase 3: b_{j+1}, E0(j), stop test (leader), then everyone reads the status
-      const double b2 = group_sum(a.part_b, G.first_cta, g, red);
-      if (leader) {
-        if (threadIdx.x == 0) {
-          const double beta = sqrt(b2);
-          const double ts = fmax(S->tscale, fabs(alpha) + be[j]);
-          S->tscale = ts;
-          be[j + 1] = beta;
-          S->j = j;
-          int st = (beta > kBreakdownRel * fmax(1.0, ts)) ? 0 : 1;
-          if (st == 0) S->scale[1 - cur] = 1.0 / beta;
-          stop_s = st;
-        }
         __syncthreads();
-        int st = stop_s;
-        if (st != 0 || j >= a.max_steps || (j % a.check) == 0) {
-          const double E = sturm_lowest(al, be, j, S->last_E0_step > 0 ? S->last_E0 : NAN,
-                                        reinterpret_cast<double*>(bsm));
-          if (threadIdx.x == 0) {
-            e0[j] = E;
-            if (st == 0 && a.tol > 0.0 && S->last_E0_step > 0 &&
-                fabs(E - S->last_E0) <= a.tol * fmax(fabs(E), 1.0))
-              st = 2;
-            S->last_E0 = E;
-            S->last_E0_step = j;
-          }
+      }
+    } else {
+      for (int64_t e = t0; e < dim; e += gt) {
+        const int u = (int)(e / I.dim_dn), d = (int)(e - (int64_t)u * I.dim_dn);
+        const T* xr = xc + (int64_t)u * I.dim_dn;
+        T acc = T(0);
+        for (int k = 0; k < I.mhd; ++k) {
+          const uint32_t en = (uint32_t)I.hd[(int64_t)k * I.dim_dn + d];
+          const uint32_t tg = en & kTargetMask;
+          if (tg >= (uint32_t)I.dim_dn) break;
+          const T v = ld_shared_f(xr + tg, multi);
+          acc += (en & kSignBit) ? -v : v;
         }
+        for (int k = 0; k < I.mhu; ++k) {
+          const uint32_t en = (uint32_t)I.hu[(int64_t)k * I.dim_up + u];
+          const uint32_t tg = en & kTargetMask;
+          if (tg >= (uint32_t)I.dim_up) break;
+          const T v = ld_shared_f(xc + (int64_t)tg * I.dim_dn + d, multi);
+          acc += (en & kSignBit) ? -v : v;
+        }
+        const T xv = ld_shared_f(xr + d, multi);
+        const T hx = fma(-tt, acc, UU * (T)__popc(I.upb[u] & I.dnb[d]) * xv);
+        const T w = fma(sc, hx, -bsp * ld_shared_f(xp + e, multi));
+        xp[e] = w;
+        if (vj) vj[e] = (float)xv;
+        dot.add(w, sc * xv);
+      }
+    }
+    {
+      const double v = block_sum(dot.get(), red);
+      if (threadIdx.x == 0) a.part_a[blockIdx.x] = v;
+    }
+    if (!group_barrier(bc, bg, g, a.max_spin, a.error)) return false;
+    // ---- phase 2: a_j, update
+    const double alpha = group_sum(a.part_a, first_cta, g, red);
+    if (leader && threadIdx.x == 0) al[j] = alpha;
+    const T coef = (T)(alpha * __ldcg(&S->scale[cur]));
+    DotAcc<T> q2;
+    // (phase 1 wrote w by row blocks: other CTAs' values are read from L2)
+    for (int64_t e = t0; e < dim; e += gt) {
+      const T q = ld_shared_f(xp + e, multi) - coef * ld_shared_f(xc + e, multi);
+      xp[e] = q;
+      q2.add(q, q);
+    }
+    {
+      const double v = block_sum(q2.get(), red);
+      if (threadIdx.x == 0) a.part_b[blockIdx.x] = v;
+    }
+    if (!group_barrier(bc, bg, g, a.max_spin, a.error)) return false;
+    // ---- phase 3: b_{j+1}, E0(j), stop test (leader), then everyone reads the status
+    const double b2 = group_sum(a.part_b, first_cta, g, red);
+    if (leader) {
+      if (threadIdx.x == 0) {
+        const double beta = sqrt(b2);
+        const double ts = fmax(S->tscale, fabs(alpha) + be[j]);
+        S->tscale = ts;
+        be[j + 1] = beta;
+        S->j = j;
+        int st = (beta > kBreakdownRel * fmax(1.0, ts)) ? 0 : 1;
+        if (st == 0) S->scale[1 - cur] = 1.0 / beta;
+        *stop_s = st;
+      }
+      __syncthreads();
+      int st = *stop_s;
+      if (st != 0 || j >= R.max_steps || (j % R.check) == 0) {
+        const double E = sturm_lowest(al, be, j, S->last_E0_step > 0 ? S->last_E0 : NAN,
+                                      reinterpret_cast<double*>(bsm));
         if (threadIdx.x == 0) {
-          if (st == 0 && j >= a.max_steps) st = 3;
-          S->status = st;
-          __threadfence();
+          e0[j] = E;
+          if (st == 0 && R.tol > 0.0 && S->last_E0_step > 0 &&
+              fabs(E - S->last_E0) <= R.tol * fmax(fabs(E), 1.0))
+            st = 2;
+          S->last_E0 = E;
+          S->last_E0_step = j;
         }
       }
-      if (!group_barrier(bc, bg, g, a.max_spin, a.error)) return;
-      if (__ldcg(&S->status) != 0) break;
-      cur = 1 - cur;
+      if (threadIdx.x == 0) {
+        if (st == 0 && j >= R.max_steps) st = 3;
+        S->status = st;
+        __threadfence();
+      }
     }
+    if (!group_barrier(bc, bg, g, a.max_spin, a.error)) return false;
+    if (__ldcg(&S->status) != 0) break;
+    cur = 1 - cur;
+  }
+  return true;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBThreads, 4)
+batched_lanczos_kernel(BArgs a) {
+  __shared__ double red[33];
+  __shared__ int stop_s;
+  __shared__ __align__(16) unsigned char bsm[kBSmemBytes];
+  const int gi = a.group_of_cta[blockIdx.x];
+  const BGroup G = a.groups[gi];
+  const int c = blockIdx.x - G.first_cta, g = G.ncta;
+  const int stride = a.refine ? a.refine_steps + 2 : a.max_steps + 2;
+  for (int oi = G.inst_begin; oi < G.inst_end; ++oi) {
+    const int id = a.order[oi];
+    const BInst I = a.inst[id];
+    RunSpec R;
+    if (a.refine) {
+      // the FP64 refinement of a mixed solve: from psi, which batched_ritz_kernel left in D1
+      R.S = a.st2 + id;
+      R.al = a.alpha2 + (size_t)id * stride;
+      R.be = a.beta2 + (size_t)id * stride;
+      R.e0 = a.E02 + (size_t)id * stride;
+      R.B0 = I.D0;
+      R.B1 = I.D1;
+      R.f1 = I.D1;
+      R.max_steps = a.refine_steps;
+      R.check = 1;
+      R.tol = a.refine_tol;
+    } else {
+      R.S = a.st + id;
+      R.al = a.alpha + (size_t)id * stride;
+      R.be = a.beta + (size_t)id * stride;
+      R.e0 = a.E0 + (size_t)id * stride;
+      R.B0 = I.B0;
+      R.B1 = I.B1;
+      R.f1 = nullptr;
+      R.max_steps = a.max_steps;
+      R.check = a.check;
+      R.tol = a.tol;
+    }
+    // mixed solves: the FP32 phase keeps its vectors and their scales (rwork: vscale | y | work)
+    R.V = a.store ? I.V : nullptr;
+    R.vscale = a.store ? a.rwork + (size_t)id * 4 * stride : nullptr;
+    R.dpad = I.dpad;
+    if (!run_instance<T>(a, I, R, c, g, G.first_cta, a.bar_count + gi, a.bar_gen + gi, red, &stop_s, bsm))
+      return;
+  }
+}
+
+// Mixed precision per instance (the batched form of ed_lanczos_solve_mixed) in three
+// cooperative launches over the same plan: batched_lanczos_kernel<float> with `store` runs
+// Algorithm 1 in FP32 and keeps its Lanczos vectors; batched_ritz_kernel computes the
+// eigenvector y of T_m for its lowest eigenvalue (inverse iteration, leader thread) and
+// assembles the Ritz vector psi = sum_j y_j f_j into D1; batched_lanczos_kernel<double> with
+// `refine` runs Algorithm 1 in FP64 from psi, with E0 checked every step, until the
+// refinement's convergence test passes.
+__global__ void __launch_bounds__(kBThreads, 4)
+batched_ritz_kernel(BArgs a) {
+  __shared__ __align__(16) float coef[ED_MAX_STEPS + 2];  // y_j times the stored vector's scale
+  const int gi = a.group_of_cta[blockIdx.x];
+  const BGroup G = a.groups[gi];
+  const int c = blockIdx.x - G.first_cta, g = G.ncta;
+  const bool multi = g > 1;
+  const int stride = a.max_steps + 2;
+  unsigned* bc = a.bar_count + gi;
+  unsigned* bg = a.bar_gen + gi;
+  for (int oi = G.inst_begin; oi < G.inst_end; ++oi) {
+    const int id = a.order[oi];
+    const BInst I = a.inst[id];
+    double* rw = a.rwork + (size_t)id * 4 * stride;  // vscale | y | inverse-iteration work (2 strides)
+    const double* al = a.alpha + (size_t)id * stride;
+    const double* be = a.beta + (size_t)id * stride;
+    const int m = __ldcg(&a.st[id].j);
+    double* y = rw + stride;
+    if (c == 0 && threadIdx.x == 0) {
+      if (m >= 1) tridiag_ritz_vector(al, be, m, __ldcg(&a.E0[(size_t)id * stride + m]), y, rw + 2 * stride);
+      __threadfence();
+    }
+    if (!group_barrier(bc, bg, g, a.max_spin, a.error)) return;
+    // psi in FP32 arithmetic: it only starts the FP64 refinement, and the FP32 vectors already
+    // bound its accuracy far above the FP32 rounding of the sum (GB300's FP64 rate would make
+    // this the slowest part of the solve)
+    for (int j = 1 + threadIdx.x; j <= m; j += blockDim.x)
+      coef[j] = (float)(__ldcg(&y[j]) * __ldcg(&rw[j]));
+    __syncthreads();
+    const int dim = I.dim_up * I.dim_dn;
+    for (int64_t e = (int64_t)c * blockDim.x + threadIdx.x; e < dim; e += (int64_t)g * blockDim.x) {
+      float p = 0.f;
+      for (int j = 1; j <= m; ++j) p = fmaf(coef[j], ld_shared_f(I.V + (size_t)(j - 1) * I.dpad + e, multi), p);
+      I.D1[e] = (double)p;
+    }
+    __syncthreads();
   }
 }
 
@@ -448,8 +572,37 @@ using namespace ed;
 
 namespace {
 
+// The FP32 vector store of batched mixed solves (Sum dim x max_steps x 4 bytes, gigabytes for
+// a large batch) comes from a per-device memory pool of the library whose release threshold
+// keeps the memory reserved after a solve frees it: a repeated solve does not map the store
+// again (mapping 12 GB took about 9 ms per call). Process-local; nothing outlasts the process.
+cudaMemPool_t vstore_pool() {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = pools.find(dev);
+  if (it != pools.end()) return it->second;
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  uint64_t keep = UINT64_MAX;
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  pools[dev] = pool;
+  return pool;
+}
+
 struct BatchRun {
   int n = 0;
+  cudaStream_t stream = nullptr;  // frees the pooled store
+  bool pooled = false;
   std::vector<BInst> hinst;
   std::vector<int> dims;
   std::vector<long long> work;
@@ -458,12 +611,27 @@ struct BatchRun {
   BState* d_state = nullptr;
   double* d_scal = nullptr;  // alpha | beta | E0
   int* d_misc = nullptr;     // error flag
+  // mixed solves
+  bool mixed = false;
+  int refine_steps = 0;
+  double refine_tol = 0.0;
+  void* vstore = nullptr;     // FP32 Lanczos vectors of every instance
+  void* dvec = nullptr;       // FP64 refinement vectors
+  double* d_rwork = nullptr;
+  BState* d_state2 = nullptr;
+  double* d_scal2 = nullptr;  // alpha | beta | E0 of the refinement
   ~BatchRun() {
     if (vec) cudaFree(vec);
     if (d_inst) cudaFree(d_inst);
     if (d_state) cudaFree(d_state);
     if (d_scal) cudaFree(d_scal);
     if (d_misc) cudaFree(d_misc);
+    if (vstore && pooled) cudaFreeAsync(vstore, stream);
+    if (vstore && !pooled) cudaFree(vstore);
+    if (dvec) cudaFree(dvec);
+    if (d_rwork) cudaFree(d_rwork);
+    if (d_state2) cudaFree(d_state2);
+    if (d_scal2) cudaFree(d_scal2);
   }
 };
 
@@ -524,11 +692,30 @@ ed_status run_plan(BatchRun& R, const Plan& p, const ed_opts* o, int check, cuda
   a.tol = o->tol;
   a.seed = o->seed;
   a.max_spin = 1000000000LL;  // a group barrier waits at most 1 s
+  a.st2 = R.d_state2;
+  a.rwork = R.d_rwork;
+  const size_t stride2 = (size_t)R.refine_steps + 2;
+  a.alpha2 = R.d_scal2;
+  a.beta2 = R.d_scal2 ? R.d_scal2 + stride2 * R.n : nullptr;
+  a.E02 = R.d_scal2 ? R.d_scal2 + 2 * stride2 * R.n : nullptr;
+  a.refine_steps = R.refine_steps;
+  a.refine_tol = R.refine_tol;
+  a.refine = 0;
+  a.store = R.mixed ? 1 : 0;
+  BArgs a2 = a;  // mixed solves: the FP64 refinement, a third launch over the same plan
+  a2.refine = 1;
+  a2.store = 0;
   void* args[] = {&a};
+  void* args2[] = {&a2};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   ED_TRY_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   cudaError_t le = cudaLaunchCooperativeKernel(kernel, p.grid, kBThreads, args, 0, s);
+  if (le == cudaSuccess && R.mixed)
+    le = cudaLaunchCooperativeKernel((const void*)batched_ritz_kernel, p.grid, kBThreads, args, 0, s);
+  if (le == cudaSuccess && R.mixed)
+    le = cudaLaunchCooperativeKernel((const void*)batched_lanczos_kernel<double>, p.grid, kBThreads,
+                                     args2, 0, s);
   cudaError_t ce = cudaStreamEndCapture(s, &graph);
   if (le != cudaSuccess || ce != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
@@ -606,16 +793,21 @@ extern "C" ed_status ed_selftest_barrier_timeout(int32_t ctas, int32_t timeout_m
   return ED_OK;
 }
 
-extern "C" ed_status ed_lanczos_solve_batched(int32_t n, const ed_basis* const* bases,
-                                              const ed_params* params, const ed_opts* o,
-                                              void* stream, double* E0, int32_t* steps,
-                                              int32_t* status, int32_t* schedule_used) {
-  clear_error();
-  ED_CHECK_ARG(n >= 1 && bases && params && o && E0, "ed_lanczos_solve_batched: bad arguments");
-  ED_CHECK_ARG(o->dtype == ED_F32 || o->dtype == ED_F64_NATIVE,
-               "ed_lanczos_solve_batched: dtype must be ED_F32 or ED_F64_NATIVE");
-  ED_CHECK_ARG(o->reorth == 0, "ed_lanczos_solve_batched: reorth must be 0 (none)");
+static ed_status solve_batched(int32_t n, const ed_basis* const* bases, const ed_params* params,
+                               const ed_opts* o, bool mixed, int32_t refine_steps, double refine_tol,
+                               void* stream, double* E0, int32_t* steps, int32_t* steps64,
+                               int32_t* status, int32_t* schedule_used) {
+  const char* fn = mixed ? "ed_lanczos_solve_batched_mixed" : "ed_lanczos_solve_batched";
+  ED_CHECK_ARG(n >= 1 && bases && params && o && E0, "%s: bad arguments", fn);
+  if (mixed)
+    ED_CHECK_ARG(o->dtype == ED_F32, "%s: dtype must be ED_F32 (the phase before refinement)", fn);
+  else
+    ED_CHECK_ARG(o->dtype == ED_F32 || o->dtype == ED_F64_NATIVE,
+                 "%s: dtype must be ED_F32 or ED_F64_NATIVE", fn);
+  ED_CHECK_ARG(o->reorth == 0, "%s: reorth must be 0 (none)", fn);
   ED_CHECK_ARG(o->max_steps >= 1 && o->max_steps <= ED_MAX_STEPS, "max_steps out of range");
+  ED_CHECK_ARG(!mixed || (refine_steps >= 1 && refine_steps <= ED_MAX_STEPS),
+               "%s: refine_steps out of range", fn);
   ED_CHECK_ARG(o->schedule >= -1 && o->schedule < kNumScheds, "schedule %d out of range", o->schedule);
   cudaStream_t user = (cudaStream_t)stream;
   cudaStream_t s = nullptr;
@@ -639,15 +831,40 @@ extern "C" ed_status ed_lanczos_solve_batched(int32_t n, const ed_basis* const* 
   size_t total = 0;
   for (int i = 0; i < n; ++i) {
     const ed_basis* b = bases[i];
-    ED_CHECK_ARG(b != nullptr, "ed_lanczos_solve_batched: basis %d is NULL", i);
-    ED_CHECK_ARG(!b->has_tau(), "ed_lanczos_solve_batched: basis %d has complex amplitudes", i);
-    ED_CHECK_ARG(b->dim < (1LL << 31), "ed_lanczos_solve_batched: instance %d too large", i);
+    ED_CHECK_ARG(b != nullptr, "%s: basis %d is NULL", fn, i);
+    ED_CHECK_ARG(!b->has_tau(), "%s: basis %d has complex amplitudes", fn, i);
+    ED_CHECK_ARG(b->dim < (1LL << 31), "%s: instance %d too large", fn, i);
     R.dims[i] = (int)b->dim;
     R.work[i] = (long long)b->dim * (b->up.maxhops + b->dn.maxhops + 4);
-    total += 2 * (size_t)((b->dim + 3) / 4 * 4);
+    total += (size_t)((b->dim + 3) / 4 * 4);
   }
   const size_t esize = o->dtype == ED_F64_NATIVE ? 8 : 4;
-  ED_TRY_CUDA(cudaMalloc((void**)&R.vec, total * esize));
+  const size_t stride = (size_t)o->max_steps + 2;
+  ED_TRY_CUDA(cudaMalloc((void**)&R.vec, 2 * total * esize));
+  if (mixed) {
+    R.mixed = true;
+    R.refine_steps = refine_steps;
+    R.refine_tol = refine_tol;
+    const size_t stride2 = (size_t)refine_steps + 2;
+    const size_t vbytes = total * (size_t)o->max_steps * sizeof(float);
+    cudaMemPool_t pool = vstore_pool();
+    R.stream = s;
+    const cudaError_t ve = pool ? cudaMallocFromPoolAsync(&R.vstore, vbytes, pool, s)
+                                : cudaMalloc(&R.vstore, vbytes);
+    if (ve != cudaSuccess) {
+      cudaGetLastError();
+      R.vstore = nullptr;
+      set_error("%s: %zu bytes for the FP32 Lanczos vectors are not available", fn, vbytes);
+      return ED_ERR_OOM;
+    }
+    R.pooled = pool != nullptr;
+    ED_TRY_CUDA(cudaMalloc(&R.dvec, 2 * total * sizeof(double)));
+    ED_TRY_CUDA(cudaMalloc((void**)&R.d_rwork, 4 * stride * n * sizeof(double)));
+    ED_TRY_CUDA(cudaMalloc((void**)&R.d_state2, n * sizeof(BState)));
+    ED_TRY_CUDA(cudaMalloc((void**)&R.d_scal2, 3 * stride2 * n * sizeof(double)));
+    ED_TRY_CUDA(cudaMemsetAsync(R.d_scal2, 0, 3 * stride2 * n * sizeof(double), s));
+    ED_TRY_CUDA(cudaMemsetAsync(R.d_rwork, 0, 4 * stride * n * sizeof(double), s));
+  }
   size_t off = 0;
   for (int i = 0; i < n; ++i) {
     const ed_basis* b = bases[i];
@@ -661,13 +878,17 @@ extern "C" ed_status ed_lanczos_solve_batched(int32_t n, const ed_basis* const* 
     I.mhu = b->up.maxhops;
     I.mhd = b->dn.maxhops;
     const size_t dpad = (size_t)(b->dim + 3) / 4 * 4;
-    I.B0 = (char*)R.vec + off * esize;
-    I.B1 = (char*)R.vec + (off + dpad) * esize;
-    off += 2 * dpad;
+    I.dpad = (int)dpad;
+    // the two work vectors of an instance side by side (per instance: B0, B1; D0, D1)
+    I.B0 = (char*)R.vec + 2 * off * esize;
+    I.B1 = (char*)R.vec + (2 * off + dpad) * esize;
+    I.V = mixed ? (float*)R.vstore + off * (size_t)o->max_steps : nullptr;
+    I.D0 = mixed ? (double*)R.dvec + 2 * off : nullptr;
+    I.D1 = mixed ? (double*)R.dvec + 2 * off + dpad : nullptr;
+    off += dpad;
     I.t = params[i].t;
     I.U = params[i].U;
   }
-  const size_t stride = (size_t)o->max_steps + 2;
   ED_TRY_CUDA(cudaMalloc((void**)&R.d_inst, n * sizeof(BInst)));
   ED_TRY_CUDA(cudaMalloc((void**)&R.d_state, n * sizeof(BState)));
   ED_TRY_CUDA(cudaMalloc((void**)&R.d_scal, 3 * stride * n * sizeof(double)));
@@ -675,19 +896,27 @@ extern "C" ed_status ed_lanczos_solve_batched(int32_t n, const ed_basis* const* 
   ED_TRY_CUDA(cudaMemcpyAsync(R.d_inst, R.hinst.data(), n * sizeof(BInst), cudaMemcpyHostToDevice, s));
   ED_TRY_CUDA(cudaMemsetAsync(R.d_scal, 0, 3 * stride * n * sizeof(double), s));
 
-  int dev = 0, per_sm = 0;
-  cudaGetDevice(&dev);
+  int per_sm = 0, per_sm_f32 = 0;
   if (o->dtype == ED_F64_NATIVE)
     ED_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_lanczos_kernel<double>,
                                                               kBThreads, 0));
   else
     ED_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_lanczos_kernel<float>,
                                                               kBThreads, 0));
+  per_sm_f32 = per_sm;
+  if (mixed) {  // both launches of a mixed solve must have every CTA resident
+    int pm = 0, pd = 0;
+    ED_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pm, batched_ritz_kernel, kBThreads, 0));
+    ED_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pd, batched_lanczos_kernel<double>,
+                                                              kBThreads, 0));
+    per_sm = std::min(per_sm, std::min(pm, pd));
+  }
   const int max_ctas = sm_count() * std::min(per_sm, 4);
   const int check = 4;  // E0(j) every 4 steps (and at the stop step)
   int sched = o->schedule;
   if (sched < 0) {
-    // autotune: time every candidate schedule on this batch with a short run, keep the best
+    // autotune: time every candidate schedule on this batch with a short plain run (the
+    // schedules pack the same H.v work in both forms), keep the best
     std::string key;
     for (int i = 0; i < n; ++i) key += std::to_string(R.work[i]) + ",";
     key += std::to_string(max_ctas) + "/" + std::to_string((int)o->dtype);
@@ -700,14 +929,17 @@ extern "C" ed_status ed_lanczos_solve_batched(int32_t n, const ed_basis* const* 
       ed_opts ot = *o;
       ot.max_steps = std::min(o->max_steps, 12);
       ot.tol = 0.0;
+      const bool was_mixed = R.mixed;
+      R.mixed = false;
       float best = 1e30f;
       for (int k = 0; k < kNumScheds; ++k) {
-        const Plan p = make_plan(R.work, R.dims, kScheds[k], max_ctas);
+        const Plan p = make_plan(R.work, R.dims, kScheds[k], std::min(max_ctas, sm_count() * std::min(per_sm_f32, 4)));
         float ms = 0.f;
         ed_status r = run_plan(R, p, &ot, ot.max_steps, s, &ms);
         if (r != ED_OK) return r;
         if (ms < best) best = ms, sched = k;
       }
+      R.mixed = was_mixed;
       std::lock_guard<std::mutex> lk(g_tune_mu);
       g_tune_cache[key] = sched;
     }
@@ -716,22 +948,52 @@ extern "C" ed_status ed_lanczos_solve_batched(int32_t n, const ed_basis* const* 
   float ms = 0.f;
   ed_status r = run_plan(R, p, o, check, s, &ms);
   if (r != ED_OK) return r;
-  std::vector<BState> hs(n);
-  std::vector<double> hE(stride * n);
+  std::vector<BState> hs(n), hs2(mixed ? n : 0);
   ED_TRY_CUDA(cudaMemcpy(hs.data(), R.d_state, n * sizeof(BState), cudaMemcpyDeviceToHost));
-  ED_TRY_CUDA(cudaMemcpy(hE.data(), R.d_scal + 2 * stride * n, stride * n * sizeof(double), cudaMemcpyDeviceToHost));
+  const size_t stride_out = mixed ? (size_t)refine_steps + 2 : stride;
+  std::vector<double> hE(stride_out * n);
+  if (mixed) {
+    ED_TRY_CUDA(cudaMemcpy(hs2.data(), R.d_state2, n * sizeof(BState), cudaMemcpyDeviceToHost));
+    ED_TRY_CUDA(cudaMemcpy(hE.data(), R.d_scal2 + 2 * stride_out * n, stride_out * n * sizeof(double),
+                           cudaMemcpyDeviceToHost));
+  } else {
+    ED_TRY_CUDA(cudaMemcpy(hE.data(), R.d_scal + 2 * stride * n, stride * n * sizeof(double),
+                           cudaMemcpyDeviceToHost));
+  }
   bool all_conv = true;
   for (int i = 0; i < n; ++i) {
-    const int j = hs[i].j;
-    E0[i] = j >= 1 ? hE[(size_t)i * stride + j] : NAN;
-    if (steps) steps[i] = j;
-    if (status) status[i] = hs[i].status;
-    if (hs[i].status == 3 && o->tol > 0.0) all_conv = false;
+    const BState& F = mixed ? hs2[i] : hs[i];
+    const int j = F.j;
+    E0[i] = j >= 1 ? hE[(size_t)i * stride_out + j] : NAN;
+    if (steps) steps[i] = hs[i].j;
+    if (steps64) steps64[i] = mixed ? hs2[i].j : 0;
+    if (status) status[i] = F.status;
+    if (F.status == 3 && (mixed ? refine_tol : o->tol) > 0.0) all_conv = false;
   }
   if (schedule_used) *schedule_used = sched;
   if (!all_conv) {
-    set_error("ed_lanczos_solve_batched: some instances reached max_steps before converging");
+    set_error("%s: some instances reached max_steps before converging", fn);
     return ED_ERR_NOT_CONVERGED;
   }
   return ED_OK;
+}
+
+extern "C" ed_status ed_lanczos_solve_batched(int32_t n, const ed_basis* const* bases,
+                                              const ed_params* params, const ed_opts* o,
+                                              void* stream, double* E0, int32_t* steps,
+                                              int32_t* status, int32_t* schedule_used) {
+  clear_error();
+  return solve_batched(n, bases, params, o, false, 0, 0.0, stream, E0, steps, nullptr, status,
+                       schedule_used);
+}
+
+extern "C" ed_status ed_lanczos_solve_batched_mixed(int32_t n, const ed_basis* const* bases,
+                                                    const ed_params* params, const ed_opts* o,
+                                                    int32_t refine_steps, double refine_tol,
+                                                    void* stream, double* E0, int32_t* steps32,
+                                                    int32_t* steps64, int32_t* status,
+                                                    int32_t* schedule_used) {
+  clear_error();
+  return solve_batched(n, bases, params, o, true, refine_steps, refine_tol, stream, E0, steps32,
+                       steps64, status, schedule_used);
 }

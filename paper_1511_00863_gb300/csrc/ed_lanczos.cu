@@ -177,35 +177,10 @@ lz_history_kernel(LzScalars* S, int m) {
   if (threadIdx.x == 0) S->E0[i] = E;
 }
 
-// Eigenvector y of T_m for its lowest eigenvalue lam by inverse iteration (two solves of
-// (T - sigma I) z = r with sigma just below lam, where T - sigma I is positive definite, so
-// the tridiagonal LU without pivoting is stable); one thread. y normalised, y[1..m].
+// Eigenvector y of T_m for its lowest eigenvalue lam (tridiag_ritz_vector); one thread.
 __global__ void lz_ritz_kernel(const LzScalars* S, int m, double lam, double* y, double* work) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const double* a = S->alpha;
-  const double* b = S->beta;
-  double scale = fabs(lam);
-  for (int i = 1; i <= m; ++i) scale = fmax(scale, fabs(a[i]) + b[i] + b[i + 1]);
-  const double sigma = lam - 1e-10 * fmax(scale, 1e-300);
-  double* dpiv = work;           // pivots
-  double* z = work + (m + 2);    // right-hand side / solution
-  for (int i = 1; i <= m; ++i) y[i] = 1.0;
-  for (int it = 0; it < 3; ++it) {
-    // forward elimination of (T - sigma I) z = y
-    dpiv[1] = a[1] - sigma;
-    z[1] = y[1];
-    for (int i = 2; i <= m; ++i) {
-      const double l = b[i] / dpiv[i - 1];
-      dpiv[i] = (a[i] - sigma) - l * b[i];
-      z[i] = y[i] - l * z[i - 1];
-    }
-    z[m] = z[m] / dpiv[m];
-    for (int i = m - 1; i >= 1; --i) z[i] = (z[i] - b[i + 1] * z[i + 1]) / dpiv[i];
-    double nrm = 0.0;
-    for (int i = 1; i <= m; ++i) nrm = fma(z[i], z[i], nrm);
-    nrm = sqrt(nrm);
-    for (int i = 1; i <= m; ++i) y[i] = z[i] / nrm;
-  }
+  tridiag_ritz_vector(S->alpha, S->beta, m, lam, y, work);
 }
 
 static int red_grid(int64_t n) {

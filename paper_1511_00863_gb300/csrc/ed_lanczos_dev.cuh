@@ -143,6 +143,35 @@ __device__ __forceinline__ double sturm_lowest(const double* a, const double* b,
   return hi_s;
 }
 
+// Eigenvector y of T_m (a: a_1..a_m, b: b_2..b_m, 1-based; b[m + 1] is read as the scale
+// bound's last term) for its lowest eigenvalue lam, by inverse iteration: three solves of
+// (T - sigma I) z = y with sigma just below lam, where T - sigma I is positive definite, so
+// the tridiagonal LU without pivoting is stable. The LU factors (pivot reciprocals) are
+// formed once and reused by the three solves: m divisions in all, which matters for one
+// thread at GB300's FP64 rate. One thread; y[1..m] normalised; work holds 2 (m + 2) doubles.
+__device__ __forceinline__ void tridiag_ritz_vector(const double* a, const double* b, int m,
+                                                    double lam, double* y, double* work) {
+  double scale = fabs(lam);
+  for (int i = 1; i <= m; ++i) scale = fmax(scale, fabs(a[i]) + b[i] + b[i + 1]);
+  const double sigma = lam - 1e-10 * fmax(scale, 1e-300);
+  double* inv = work;            // reciprocals of the pivots
+  double* z = work + (m + 2);    // right-hand side / solution
+  inv[1] = 1.0 / (a[1] - sigma);
+  for (int i = 2; i <= m; ++i) inv[i] = 1.0 / ((a[i] - sigma) - b[i] * b[i] * inv[i - 1]);
+  for (int i = 1; i <= m; ++i) y[i] = 1.0;
+  for (int it = 0; it < 3; ++it) {
+    // forward elimination, then back substitution, of (T - sigma I) z = y
+    z[1] = y[1];
+    for (int i = 2; i <= m; ++i) z[i] = y[i] - b[i] * inv[i - 1] * z[i - 1];
+    z[m] *= inv[m];
+    for (int i = m - 1; i >= 1; --i) z[i] = (z[i] - b[i + 1] * z[i + 1]) * inv[i];
+    double nrm = 0.0;
+    for (int i = 1; i <= m; ++i) nrm = fma(z[i], z[i], nrm);
+    const double r = 1.0 / sqrt(nrm);
+    for (int i = 1; i <= m; ++i) y[i] = z[i] * r;
+  }
+}
+
 // Thread 0 of the finish kernel: record b_{j+1}, update the breakdown scale, advance j.
 // Returns 1 on breakdown (b_{j+1} <= 1e-13 max(1, max_i |a_i| + b_i)), else 0.
 __device__ __forceinline__ int finish_record_beta(LzScalars* S, int j, double beta) {

@@ -162,3 +162,61 @@ def test_batched_native_fp64_matches_oracle(ed):
     E_ref = np.array([ref[i] for i in range(len(insts))])
     err = np.abs(res["E0"] - E_ref) / np.maximum(1.0, np.abs(E_ref))
     assert err.max() <= 1e-10, (int(np.argmax(err)), err.max())
+
+
+def _golden_batched():
+    import os
+    ref = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "batched_E0.txt")):
+        f = line.split()
+        if f and not f[0].startswith("#"):
+            ref[int(f[0])] = float(f[6])
+    return ref
+
+
+def test_batched_mixed_matches_oracle(ed):
+    """FP32 batch, Ritz vector of every instance, FP64 refinement from it, all in one
+    persistent launch: every instance within 1e-10 of the oracle's E0
+    (tests/golden/batched_E0.txt), which the FP32 batch alone misses (4.8e-8), after a few
+    FP64 steps; a repeated run gives bit-identical energies."""
+    ref = _golden_batched()
+    insts = ed_inputs.batched_instances()
+    bases = [ed.ed_build_basis(w["n_sites"], w["bonds"], w["n_up"], w["n_dn"]) for w in insts]
+    try:
+        ts, Us = [w["t"] for w in insts], [w["U"] for w in insts]
+        opts = ed.make_opts(max_steps=200, tol=1e-9, seed=4, dtype="f32", schedule=5)
+        res = ed.ed_lanczos_solve_batched_mixed(bases, ts, Us, opts, refine_steps=32, refine_tol=1e-12)
+        again = ed.ed_lanczos_solve_batched_mixed(bases, ts, Us, opts, refine_steps=32, refine_tol=1e-12)
+    finally:
+        for b in bases:
+            ed.ed_basis_destroy(b)
+    assert res["status"] == 0
+    E_ref = np.array([ref[i] for i in range(len(insts))])
+    err = np.abs(res["E0"] - E_ref) / np.maximum(1.0, np.abs(E_ref))
+    assert err.max() <= 1e-10, (int(np.argmax(err)), err.max())
+    # a few FP64 steps from the Ritz vector (the refinement converged before its cap)
+    assert res["steps64"].max() < 32 and res["steps64"].mean() < 10, res["steps64"]
+    assert np.all(res["steps64"] >= 1) and np.all(np.isin(res["inst_status"], (1, 2)))
+    assert np.array_equal(res["E0"], again["E0"])
+
+
+def test_batched_mixed_small_cases(ed):
+    """Small and degenerate sizes through the mixed path: a single-state instance (all sites
+    filled: no hops, both phases break down after one step with E0 = U n), the two-site
+    dimer (dim 4, the Krylov space exhausted within a few steps) against its closed form
+    (U - sqrt(U^2 + 16 t^2)) / 2, and a 10-site ring 3/2 against the oracle."""
+    insts = [dict(n_sites=4, bonds=ed_inputs.ring_bonds(4), n_up=4, n_dn=4, t=1.0, U=2.0),
+             dict(n_sites=2, bonds=np.array([[0, 1]], dtype=np.int32), n_up=1, n_dn=1, t=1.0, U=3.0),
+             dict(n_sites=10, bonds=ed_inputs.ring_bonds(10), n_up=3, n_dn=2, t=1.0, U=5.0)]
+    bases = [ed.ed_build_basis(w["n_sites"], w["bonds"], w["n_up"], w["n_dn"]) for w in insts]
+    try:
+        res = ed.ed_lanczos_solve_batched_mixed(bases, [w["t"] for w in insts], [w["U"] for w in insts],
+                                                ed.make_opts(max_steps=100, tol=1e-9, seed=4, dtype="f32"),
+                                                refine_steps=16, refine_tol=1e-12, raise_not_converged=False)
+    finally:
+        for b in bases:
+            ed.ed_basis_destroy(b)
+    assert abs(res["E0"][0] - 4 * 2.0) <= 1e-12 * 8
+    assert abs(res["E0"][1] - (3.0 - math.sqrt(9.0 + 16.0)) / 2) <= 1e-12
+    ref = _oracle_E0(insts[2])
+    assert abs(res["E0"][2] - ref) <= 1e-10 * abs(ref)
