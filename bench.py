@@ -414,9 +414,9 @@ def learned_start_study(ed, rel=1e-8, train_steps=1500, batch=16384):
 
 
 def batched_study(ed, rel=1e-8):
-    """256 instances: one batched FP32 launch; sequential FP64-accurate solves; sequential
-    FP32 + FP64-accurate refinement solves. Errors against the oracle's E0 of every
-    instance."""
+    """256 instances: one batched FP32 launch; the batched FP32 + FP64 refinement; the batch
+    in FP64; sequential FP64-accurate, native-FP64 and FP32 + refinement solves. Errors against
+    the oracle's E0 of every instance."""
     import numpy as np
     insts = ed_inputs.batched_instances()
     ref = golden_batched()
@@ -440,6 +440,13 @@ def batched_study(ed, rel=1e-8):
                     for b, t, U in zip(bases, ts, Us)]
         _mixed()
         mix, t_m = _timed(_mixed)
+        # the batch in FP32 with its FP64 refinement (three cooperative launches in one graph)
+        bm_opts = ed.make_opts(max_steps=200, tol=1e-9, seed=4, dtype="f32", schedule=-1)
+        def _bmixed():
+            return ed.ed_lanczos_solve_batched_mixed(bases, ts, Us, bm_opts, refine_steps=64,
+                                                     refine_tol=rel / 100, raise_not_converged=False)
+        _bmixed()
+        resm, t_bm = _timed(_bmixed)
         # the batch in FP64 (one persistent launch), and the plain method one instance at a time
         o64 = ed.make_opts(max_steps=600, tol=1e-12, seed=4, dtype="f64n", schedule=-1)
         ed.ed_lanczos_solve_batched(bases, ts, Us, o64, raise_not_converged=False)   # autotune
@@ -451,7 +458,7 @@ def batched_study(ed, rel=1e-8):
         seqn, t_sn = _timed(_seqn)
         rerr = lambda E: np.abs(np.asarray(E) - E_ref) / np.maximum(1.0, np.abs(E_ref))
         eb, es, em = rerr(res["E0"]), rerr(seq), rerr(mix)
-        eb64, esn = rerr(res64["E0"]), rerr(seqn)
+        eb64, esn, ebm = rerr(res64["E0"]), rerr(seqn), rerr(resm["E0"])
         return {"instances": len(insts), "sum_dim": int(sum(ed.ed_basis_dims(b)[2] for b in bases)),
                 "E0_ref_source": "oracle E0 of every instance (tests/golden/batched_E0.txt)", "rel": rel,
                 "batched_f32_s": t_b, "schedule": res["schedule"],
@@ -461,15 +468,21 @@ def batched_study(ed, rel=1e-8):
                 "sequential_f64_s": t_s, "sequential_f64_first_solves_s": t_cold,
                 "sequential_f64_max_rel_err": float(es.max()),
                 "sequential_f32_mixed_s": t_m, "sequential_f32_mixed_max_rel_err": float(em.max()),
+                "batched_f32_mixed_s": t_bm, "batched_f32_mixed_max_rel_err": float(ebm.max()),
+                "batched_f32_mixed_steps32_mean": float(resm["steps32"].mean()),
+                "batched_f32_mixed_steps64_max": int(resm["steps64"].max()),
                 "batched_f64_native_s": t_b64, "batched_f64_native_max_rel_err": float(eb64.max()),
                 "batched_f64_native_schedule": res64["schedule"],
                 "sequential_f64_native_s": t_sn, "sequential_f64_native_max_rel_err": float(esn.max()),
-                "time_to_rel": {"batched_f64_native_s": t_b64 if eb64.max() <= rel else None,
+                "time_to_rel": {"batched_f32_mixed_s": t_bm if ebm.max() <= rel else None,
+                                "batched_f64_native_s": t_b64 if eb64.max() <= rel else None,
                                 "batched_f32_s": t_b if eb.max() <= rel else None,
                                 "sequential_f64_fixed_s": t_s if es.max() <= rel else None,
                                 "sequential_f64_native_s": t_sn if esn.max() <= rel else None,
                                 "sequential_f32_mixed_s": t_m if em.max() <= rel else None},
                 "speedup_batched_vs_sequential_f64": t_s / t_b,
+                "speedup_to_rel_batched_mixed_vs_sequential_f64_native":
+                    t_sn / t_bm if (ebm.max() <= rel and esn.max() <= rel) else None,
                 "repeat_identical": bool(np.array_equal(np.array(seq), np.array(seq2)))}
     finally:
         for b in bases:
