@@ -26,6 +26,13 @@
 namespace ed {
 
 constexpr int kBThreads = 256;
+// CTAs per SM the register bound allows: the batch is bound by latency across many small
+// instances, and 6 CTAs per SM (40 registers, a few words spilled) ran the FP32 batch in 56
+// ms against 72 ms with 4 (64 registers). The FP64 kernel keeps 4 (its 64-bit arithmetic
+// spills more at 40 registers: 204 ms against 191 ms).
+constexpr int kBCtasPerSm = 6;
+template <typename T>
+constexpr int bctas_per_sm() { return sizeof(T) == 4 ? kBCtasPerSm : 4; }
 // Shared buffer of the batched kernel: a block of up rows staged for the H.v phase, or the
 // Sturm workspace of the leader CTA (used at different times).
 constexpr int kBRowFloats = 4096;
@@ -370,7 +377,7 @@ __device__ bool run_instance(const BArgs& a, const BInst& I, const RunSpec& R, i
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBThreads, 4)
+__global__ void __launch_bounds__(kBThreads, bctas_per_sm<T>())
 batched_lanczos_kernel(BArgs a) {
   __shared__ double red[33];
   __shared__ int stop_s;
@@ -423,7 +430,7 @@ batched_lanczos_kernel(BArgs a) {
 // assembles the Ritz vector psi = sum_j y_j f_j into D1; batched_lanczos_kernel<double> with
 // `refine` runs Algorithm 1 in FP64 from psi, with E0 checked every step, until the
 // refinement's convergence test passes.
-__global__ void __launch_bounds__(kBThreads, 4)
+__global__ void __launch_bounds__(kBThreads, kBCtasPerSm)
 batched_ritz_kernel(BArgs a) {
   __shared__ __align__(16) float coef[ED_MAX_STEPS + 2];  // y_j times the stored vector's scale
   const int gi = a.group_of_cta[blockIdx.x];
@@ -664,13 +671,17 @@ ed_status upload_plan(const Plan& p, PlanDev& d, cudaStream_t s) {
 }
 
 // One cooperative launch of the whole batch, captured in a CUDA graph and replayed once.
-ed_status run_plan(BatchRun& R, const Plan& p, const ed_opts* o, int check, cudaStream_t s,
-                   float* ms_out) {
+// p: the plan of the (first) Lanczos launch; p2: the plan of a mixed solve's Ritz and
+// refinement launches (their kernels may allow fewer CTAs per SM; all state between the
+// launches is per instance, so each launch can pack the instances its own way).
+ed_status run_plan(BatchRun& R, const Plan& p, const Plan* p2, const ed_opts* o, int check,
+                   cudaStream_t s, float* ms_out) {
   const void* kernel = o->dtype == ED_F64_NATIVE ? (const void*)batched_lanczos_kernel<double>
                                                  : (const void*)batched_lanczos_kernel<float>;
-  PlanDev d;
+  PlanDev d, d2;
   ed_status st = upload_plan(p, d, s);
   if (st != ED_OK) return st;
+  if (R.mixed && (st = upload_plan(*p2, d2, s)) != ED_OK) return st;
   ED_TRY_CUDA(cudaMemsetAsync(R.d_misc, 0, sizeof(int), s));
   BArgs a;
   a.inst = R.d_inst;
@@ -702,19 +713,30 @@ ed_status run_plan(BatchRun& R, const Plan& p, const ed_opts* o, int check, cuda
   a.refine_tol = R.refine_tol;
   a.refine = 0;
   a.store = R.mixed ? 1 : 0;
-  BArgs a2 = a;  // mixed solves: the FP64 refinement, a third launch over the same plan
+  BArgs ar = a;  // mixed solves: the Ritz launch and the FP64 refinement over plan p2
+  if (R.mixed) {
+    ar.order = d2.order;
+    ar.groups = d2.groups;
+    ar.group_of_cta = d2.goc;
+    ar.part_a = d2.part;
+    ar.part_b = d2.part + p2->grid;
+    ar.bar_count = d2.bar;
+    ar.bar_gen = d2.bar + p2->groups.size();
+  }
+  ar.store = 0;
+  BArgs a2 = ar;
   a2.refine = 1;
-  a2.store = 0;
   void* args[] = {&a};
+  void* argsr[] = {&ar};
   void* args2[] = {&a2};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   ED_TRY_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   cudaError_t le = cudaLaunchCooperativeKernel(kernel, p.grid, kBThreads, args, 0, s);
   if (le == cudaSuccess && R.mixed)
-    le = cudaLaunchCooperativeKernel((const void*)batched_ritz_kernel, p.grid, kBThreads, args, 0, s);
+    le = cudaLaunchCooperativeKernel((const void*)batched_ritz_kernel, p2->grid, kBThreads, argsr, 0, s);
   if (le == cudaSuccess && R.mixed)
-    le = cudaLaunchCooperativeKernel((const void*)batched_lanczos_kernel<double>, p.grid, kBThreads,
+    le = cudaLaunchCooperativeKernel((const void*)batched_lanczos_kernel<double>, p2->grid, kBThreads,
                                      args2, 0, s);
   cudaError_t ce = cudaStreamEndCapture(s, &graph);
   if (le != cudaSuccess || ce != cudaSuccess) {
@@ -896,22 +918,25 @@ static ed_status solve_batched(int32_t n, const ed_basis* const* bases, const ed
   ED_TRY_CUDA(cudaMemcpyAsync(R.d_inst, R.hinst.data(), n * sizeof(BInst), cudaMemcpyHostToDevice, s));
   ED_TRY_CUDA(cudaMemsetAsync(R.d_scal, 0, 3 * stride * n * sizeof(double), s));
 
-  int per_sm = 0, per_sm_f32 = 0;
+  // a cooperative launch needs every CTA resident: grids of (resident CTAs per SM) x SMs
+  int per_sm = 0, per_sm2 = 0;
   if (o->dtype == ED_F64_NATIVE)
     ED_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_lanczos_kernel<double>,
                                                               kBThreads, 0));
   else
     ED_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_lanczos_kernel<float>,
                                                               kBThreads, 0));
-  per_sm_f32 = per_sm;
-  if (mixed) {  // both launches of a mixed solve must have every CTA resident
+  if (mixed) {  // the Ritz and refinement launches share a plan
     int pm = 0, pd = 0;
     ED_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pm, batched_ritz_kernel, kBThreads, 0));
     ED_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pd, batched_lanczos_kernel<double>,
                                                               kBThreads, 0));
-    per_sm = std::min(per_sm, std::min(pm, pd));
+    per_sm2 = std::min(pm, pd);
   }
-  const int max_ctas = sm_count() * std::min(per_sm, 4);
+  ED_CHECK_ARG(per_sm >= 1 && (!mixed || per_sm2 >= 1), "%s: the batched kernels do not fit an SM", fn);
+  const int max_ctas = sm_count() * std::min(per_sm, o->dtype == ED_F64_NATIVE
+                                                         ? bctas_per_sm<double>() : bctas_per_sm<float>());
+  const int max_ctas2 = sm_count() * std::min(std::max(per_sm2, 1), kBCtasPerSm);
   const int check = 4;  // E0(j) every 4 steps (and at the stop step)
   int sched = o->schedule;
   if (sched < 0) {
@@ -933,9 +958,9 @@ static ed_status solve_batched(int32_t n, const ed_basis* const* bases, const ed
       R.mixed = false;
       float best = 1e30f;
       for (int k = 0; k < kNumScheds; ++k) {
-        const Plan p = make_plan(R.work, R.dims, kScheds[k], std::min(max_ctas, sm_count() * std::min(per_sm_f32, 4)));
+        const Plan p = make_plan(R.work, R.dims, kScheds[k], max_ctas);
         float ms = 0.f;
-        ed_status r = run_plan(R, p, &ot, ot.max_steps, s, &ms);
+        ed_status r = run_plan(R, p, nullptr, &ot, ot.max_steps, s, &ms);
         if (r != ED_OK) return r;
         if (ms < best) best = ms, sched = k;
       }
@@ -945,8 +970,9 @@ static ed_status solve_batched(int32_t n, const ed_basis* const* bases, const ed
     }
   }
   const Plan p = make_plan(R.work, R.dims, kScheds[sched], max_ctas);
+  const Plan p2 = mixed ? make_plan(R.work, R.dims, kScheds[sched], max_ctas2) : Plan();
   float ms = 0.f;
-  ed_status r = run_plan(R, p, o, check, s, &ms);
+  ed_status r = run_plan(R, p, mixed ? &p2 : nullptr, o, check, s, &ms);
   if (r != ED_OK) return r;
   std::vector<BState> hs(n), hs2(mixed ? n : 0);
   ED_TRY_CUDA(cudaMemcpy(hs.data(), R.d_state, n * sizeof(BState), cudaMemcpyDeviceToHost));
