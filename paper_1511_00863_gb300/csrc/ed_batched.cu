@@ -13,6 +13,9 @@
 //            Sturm bisection (leader CTA), convergence / breakdown / max_steps.
 // The H.v phase stages blocks of up rows in shared memory (down-hop gathers there) and reads
 // up-neighbour rows coalesced; vectors of the batch stay in L2.
+// ed_lanczos_solve_batched_mixed carries the FP32 batch to FP64 accuracy: the FP32 run keeps
+// its vectors, a Ritz vector is assembled per instance and FP64 steps refine it
+// (batched_ritz_kernel and the `refine` form of the FP64 kernel, below).
 #include <algorithm>
 #include <cmath>
 #include <map>
@@ -424,8 +427,10 @@ batched_lanczos_kernel(BArgs a) {
 }
 
 // Mixed precision per instance (the batched form of ed_lanczos_solve_mixed) in three
-// cooperative launches over the same plan: batched_lanczos_kernel<float> with `store` runs
-// Algorithm 1 in FP32 and keeps its Lanczos vectors; batched_ritz_kernel computes the
+// cooperative launches (the first over a plan sized for its kernel's residency, the other two
+// over one sized for theirs; all state between them is per instance):
+// batched_lanczos_kernel<float> with `store` runs Algorithm 1 in FP32 and keeps its Lanczos
+// vectors; batched_ritz_kernel computes the
 // eigenvector y of T_m for its lowest eigenvalue (inverse iteration, leader thread) and
 // assembles the Ritz vector psi = sum_j y_j f_j into D1; batched_lanczos_kernel<double> with
 // `refine` runs Algorithm 1 in FP64 from psi, with E0 checked every step, until the
