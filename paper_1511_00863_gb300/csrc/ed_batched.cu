@@ -263,8 +263,12 @@ __device__ bool run_instance(const BArgs& a, const BInst& I, const RunSpec& R, i
         const T* xb = xc + (int64_t)u0 * I.dim_dn;
         for (int i = threadIdx.x; i < nel; i += blockDim.x) xsm[i] = ld_shared_f(xb + i, multi);
         __syncthreads();
+        // (row, column) of element i carried from one iteration to the next: i advances by
+        // blockDim.x = sr rows and sd columns
+        int r = threadIdx.x / I.dim_dn, d = threadIdx.x - r * I.dim_dn;
+        const int sr = blockDim.x / I.dim_dn, sd = blockDim.x - sr * I.dim_dn;
         for (int i = threadIdx.x; i < nel; i += blockDim.x) {
-          const int r = i / I.dim_dn, d = i - r * I.dim_dn, u = u0 + r;
+          const int u = u0 + r;
           const T* xr = xsm + r * I.dim_dn;
           T acc = T(0);
           for (int k = 0; k < I.mhd; ++k) {
@@ -288,12 +292,24 @@ __device__ bool run_instance(const BArgs& a, const BInst& I, const RunSpec& R, i
           xp[e] = w;
           if (vj) vj[e] = (float)xv;
           dot.add(w, sc * xv);
+          r += sr;
+          d += sd;
+          if (d >= I.dim_dn) {
+            d -= I.dim_dn;
+            ++r;
+          }
         }
         __syncthreads();
       }
     } else {
-      for (int64_t e = t0; e < dim; e += gt) {
-        const int u = (int)(e / I.dim_dn), d = (int)(e - (int64_t)u * I.dim_dn);
+      // (row, column) of element e carried from one iteration to the next (e < 2^31)
+      int u = (int)t0 / I.dim_dn, d = (int)t0 - u * I.dim_dn;
+      const int su = (int)gt / I.dim_dn, sdd = (int)gt - su * I.dim_dn;
+      for (int64_t e = t0; e < dim; e += gt, u += su, d += sdd) {
+        if (d >= I.dim_dn) {
+          d -= I.dim_dn;
+          ++u;
+        }
         const T* xr = xc + (int64_t)u * I.dim_dn;
         T acc = T(0);
         for (int k = 0; k < I.mhd; ++k) {
