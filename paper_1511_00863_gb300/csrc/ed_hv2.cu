@@ -32,7 +32,7 @@ struct Hv2Plan {
 
 // Split-row variants (hv2s_kernel): id, element, V, T, MB.
 #define HV2S_KINDS(X)              \
-  X(30, long long, 2, 512, 1)      \
+  X(30, long long, 2, 640, 1)      \
   X(31, float, 4, 512, 2)
 
 static int optin_smem() {
