@@ -57,3 +57,27 @@ def test_argument_errors_without_gpu(lib_path):
         ed.ed_build_basis(4, [[0, 0]], 1, 1, stream=0)
     with pytest.raises(ed.EdError):
         ed.ed_build_basis(4, [[0, 1]], 5, 1, stream=0)
+
+
+def test_batched_argument_errors_without_gpu(lib_path):
+    """The batched entry points reject bad options on the host before any CUDA call: the mixed
+    solve's FP32 phase must be ED_F32, its refinement length must be in range, neither takes
+    reorthogonalisation, and the plain batch takes only ED_F32 or ED_F64_NATIVE."""
+    import paper_1511_00863_gb300 as ed
+    bases = [None]   # not reached: the options are checked first
+    cases = [
+        (lambda: ed.ed_lanczos_solve_batched_mixed(bases, [1.0], [4.0], ed.make_opts(dtype="f64"), stream=0),
+         "ED_F32"),
+        (lambda: ed.ed_lanczos_solve_batched_mixed(bases, [1.0], [4.0], ed.make_opts(dtype="f32"),
+                                                   refine_steps=0, stream=0), "refine_steps"),
+        (lambda: ed.ed_lanczos_solve_batched_mixed(bases, [1.0], [4.0], ed.make_opts(dtype="f32", reorth=1),
+                                                   stream=0), "reorth"),
+        (lambda: ed.ed_lanczos_solve_batched(bases, [1.0], [4.0], ed.make_opts(dtype="c32"), stream=0),
+         "dtype"),
+        (lambda: ed.ed_lanczos_solve_batched(bases, [1.0], [4.0], ed.make_opts(dtype="f32", max_steps=0),
+                                             stream=0), "max_steps"),
+    ]
+    for call, word in cases:
+        with pytest.raises(ed.EdError) as e:
+            call()
+        assert e.value.status == ed.ED_ERR_ARG and word in str(e.value), str(e.value)
