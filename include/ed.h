@@ -288,10 +288,11 @@ ed_status ed_lanczos_solve_mixed(const ed_basis* basis, const ed_params* params,
  * products as for ED_F32 (compensated FP32 per thread, FP64 across threads); or
  * ED_F64_NATIVE: FP64 vectors and H.v; FP64 a_j, b_j and tridiagonal solve either way;
  * start vector of opts->seed for every instance; reorth 0). The convergence test of opts is evaluated every 4 steps.
- * opts->schedule picks how instances are packed onto groups of CTAs (0..5; 5 sizes groups
- * in proportion to each instance's work); -1 lets the
- * library time every schedule on this batch with a short run and keep the fastest (cached
- * per process for the same batch shape). Outputs (HOST arrays of n, steps/status optional):
+ * opts->schedule picks how instances are packed onto groups of CTAs (0..6; 5 sizes groups
+ * in proportion to each instance's work per step, 6 to that work times log2 of its
+ * dimension, an estimate of its step count); -1 lets the library time every schedule on
+ * this batch with the solve itself (at most 200 steps) and keep the fastest (cached per
+ * process for the same batch shape). Outputs (HOST arrays of n, steps/status optional):
  * E0[i], steps[i], status[i] (0 running, 1 breakdown, 2 converged, 3 max_steps) and
  * *schedule_used. Returns ED_ERR_NOT_CONVERGED if some instance hit max_steps with tol > 0,
  * ED_ERR_TIMEOUT if a group barrier's bounded wait ran out. Synchronises `stream`. */

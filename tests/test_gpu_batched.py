@@ -97,8 +97,8 @@ def test_batched_full_workload_vs_fp64_solver(ed):
 
 def test_batched_schedules_agree(ed):
     insts = ed_inputs.batched_instances()[:48]
-    out = [_run(ed, insts, schedule=s)["E0"] for s in range(6)]
-    for s in range(1, 6):
+    out = [_run(ed, insts, schedule=s)["E0"] for s in range(7)]
+    for s in range(1, 7):
         assert np.allclose(out[s], out[0], rtol=TOL32, atol=TOL32)
 
 
