@@ -238,7 +238,8 @@ ed_status ed_lanczos_buffers(const ed_lanczos* st, const void** f_next, const vo
                              const int32_t** colpos);
 
 /* ed_lanczos_energy - E0(j) = lowest eigenvalue of T_j (Sec. 2.2), computed on the device
- * by Sturm-sequence bisection in FP64, and the number of steps j taken. Synchronises. */
+ * by Sturm-sequence bisection to FP64 precision (float-float rounds first, FP64 rounds to
+ * finish), and the number of steps j taken. Synchronises. */
 ed_status ed_lanczos_energy(ed_lanczos* st, double* E0, int32_t* steps);
 
 void ed_lanczos_destroy(ed_lanczos* st);

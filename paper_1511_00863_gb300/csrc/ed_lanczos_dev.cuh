@@ -45,56 +45,187 @@ __device__ __forceinline__ int sturm_count(const double* aa, const double* bb, i
   return cnt;
 }
 
-// Shared-memory workspace of sturm_lowest: a_i and b_i^2 for i <= ED_MAX_STEPS + 1.
-constexpr int kSturmWork = 2 * (ED_MAX_STEPS + 2);
+// ------------------------------------------------------------------ float-float Sturm count
+// A value hi + lo of two FP32 numbers (about 48 significant bits), with the error-free
+// transformations TwoSum (Knuth), FastTwoSum (Dekker 1971; |a| >= |b|) and the FMA product
+// error (the product a b - fl(a b) is exact in one FMA). GB300 runs FP32 at about 64 times
+// its FP64 rate, so the ~12 FP32 operations of one float-float operation still cost a few
+// times less than one FP64 operation.
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return FF{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ FF ff_fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return FF{s, b - (s - a)};
+}
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+  const FF s = ff_two_sum(x.hi, y.hi);
+  const FF t = ff_two_sum(x.lo, y.lo);
+  const FF u = ff_fast_two_sum(s.hi, s.lo + t.hi);
+  return ff_fast_two_sum(u.hi, u.lo + t.lo);
+}
+__device__ __forceinline__ FF ff_mul(FF x, FF y) {
+  const float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ FF ff_of(double d) {
+  const float hi = (float)d;
+  return FF{hi, (float)(d - (double)hi)};
+}
+
+// sturm_count in float-float arithmetic (aa, bb as float-float copies of a_i and b_i^2). The
+// count is exact for a tridiagonal whose entries differ from T's by a few units of 2^-48
+// relative. The pair (p_{i-1}, p_i) is rescaled by powers of two to keep |p_i| within
+// 2^-30..2^30 (FP32's range is narrow); a vanishing p_i becomes -2^-50 p_{i-1}.
+__device__ __forceinline__ int sturm_count_ff(const FF* aa, const FF* bb, int m, FF x) {
+  int cnt = 0;
+  FF p2{0.f, 0.f}, p1{1.f, 0.f};
+  bool n1 = false;
+  const FF nx{-x.hi, -x.lo};
+  for (int i = 1; i <= m; ++i) {
+    const FF q = ff_mul(bb[i], p2);
+    FF p = ff_add(ff_mul(ff_add(aa[i], nx), p1), FF{-q.hi, -q.lo});
+    if (p.hi == 0.f) p = FF{-0x1.0p-50f * p1.hi, -0x1.0p-50f * p1.lo};  // (hi == 0 implies lo == 0)
+    const bool n = p.hi < 0.f;
+    cnt += n != n1 ? 1 : 0;
+    n1 = n;
+    p2 = p1;
+    p1 = p;
+    const int e = (int)((__float_as_uint(p1.hi) >> 23) & 0xFFu);
+    if (e > 127 + 30 || e < 127 - 30) {
+      const float sc = __uint_as_float((uint32_t)(254 - e) << 23);  // 2^(127 - e)
+      p1 = FF{p1.hi * sc, p1.lo * sc};
+      p2 = FF{p2.hi * sc, p2.lo * sc};
+    }
+  }
+  return cnt;
+}
+
+// Two float-float counts at once (x0, x1): two independent recurrences interleaved, so a
+// thread's dependent chain of FP32 operations hides its own latency.
+__device__ __forceinline__ void sturm_count_ff2(const FF* aa, const FF* bb, int m, FF x0, FF x1,
+                                                int& c0, int& c1) {
+  c0 = 0;
+  c1 = 0;
+  FF p2a{0.f, 0.f}, p1a{1.f, 0.f}, p2b{0.f, 0.f}, p1b{1.f, 0.f};
+  bool na = false, nb = false;
+  const FF nx0{-x0.hi, -x0.lo}, nx1{-x1.hi, -x1.lo};
+  for (int i = 1; i <= m; ++i) {
+    const FF ai = aa[i], bi = bb[i];
+    const FF qa = ff_mul(bi, p2a), qb = ff_mul(bi, p2b);
+    FF pa = ff_add(ff_mul(ff_add(ai, nx0), p1a), FF{-qa.hi, -qa.lo});
+    FF pb = ff_add(ff_mul(ff_add(ai, nx1), p1b), FF{-qb.hi, -qb.lo});
+    if (pa.hi == 0.f) pa = FF{-0x1.0p-50f * p1a.hi, -0x1.0p-50f * p1a.lo};
+    if (pb.hi == 0.f) pb = FF{-0x1.0p-50f * p1b.hi, -0x1.0p-50f * p1b.lo};
+    const bool ma = pa.hi < 0.f, mb = pb.hi < 0.f;
+    c0 += ma != na ? 1 : 0;
+    c1 += mb != nb ? 1 : 0;
+    na = ma;
+    nb = mb;
+    p2a = p1a;
+    p1a = pa;
+    p2b = p1b;
+    p1b = pb;
+    const int ea = (int)((__float_as_uint(p1a.hi) >> 23) & 0xFFu);
+    if (ea > 127 + 30 || ea < 127 - 30) {
+      const float sc = __uint_as_float((uint32_t)(254 - ea) << 23);
+      p1a = FF{p1a.hi * sc, p1a.lo * sc};
+      p2a = FF{p2a.hi * sc, p2a.lo * sc};
+    }
+    const int eb = (int)((__float_as_uint(p1b.hi) >> 23) & 0xFFu);
+    if (eb > 127 + 30 || eb < 127 - 30) {
+      const float sc = __uint_as_float((uint32_t)(254 - eb) << 23);
+      p1b = FF{p1b.hi * sc, p1b.lo * sc};
+      p2b = FF{p2b.hi * sc, p2b.lo * sc};
+    }
+  }
+}
+
+// Shared-memory workspace of sturm_lowest: a_i and b_i^2 for i <= ED_MAX_STEPS + 1, in FP64
+// and as float-float pairs.
+constexpr int kSturmWork = 4 * (ED_MAX_STEPS + 2);
 
 // lambda_min(T_m) by multisection, called by the whole block (>= 128 threads); returns the
 // upper end of the final bracket (valid in every thread). a, b: 1-based a_1..a_m, b_2..b_m.
 // The diagonal and the squared off-diagonal are staged in `work` (kSturmWork doubles of
-// shared memory). Each round
-// evaluates the Sturm count at 128 interior points of the bracket (four warps, one per SM
-// sub-partition) and keeps the sub-interval holding the first eigenvalue, until the bracket
-// stops shrinking in FP64. With a hint (a previous lambda_min of a leading block of T_m, an
-// upper bound by Cauchy interlacing; NaN = none), a first round probes geometrically spaced
-// points below it, so a bracket of the size of the last change is found in one round.
+// shared memory). Each round evaluates the Sturm count at 128 interior points of the bracket
+// (four warps, one per SM sub-partition) and keeps the sub-interval holding the first
+// eigenvalue. The rounds first count in float-float arithmetic, until the bracket is within
+// delta = 2^-40 ||T|| (256 times the float-float count's backward error); the bracket is
+// then widened by delta on both sides and FP64 rounds narrow it until it stops shrinking in
+// FP64, so the result has the precision of an all-FP64 multisection at about half its FP64
+// work. With a hint (a previous lambda_min of a leading block of T_m, an upper bound by
+// Cauchy interlacing; NaN = none), a first round probes geometrically spaced points below
+// it, so a bracket of the size of the last change is found in one round.
 __device__ __forceinline__ double sturm_lowest(const double* a, const double* b, int m,
                                                double hint, double* work) {
   constexpr int P = 128;
   double* aa = work;
   double* bb = work + (ED_MAX_STEPS + 2);
-  __shared__ double lo_s, hi_s;
+  FF* af = reinterpret_cast<FF*>(work + 2 * (ED_MAX_STEPS + 2));
+  FF* bf = af + (ED_MAX_STEPS + 2);
+  __shared__ double lo_s, hi_s, delta_s;
+  __shared__ double glo_s[32], ghi_s[32];
   __shared__ int first_s, last0_s, top_s;
+  // staging and the Gershgorin bounds, one row per thread (a serial pass over the rows costs
+  // about 10 us at m = 56 on GB300's FP64 pipe)
+  double glo = INFINITY, ghi = -INFINITY;
   for (int i = 1 + threadIdx.x; i <= m; i += blockDim.x) {
-    aa[i] = a[i];
+    const double ai = a[i];
+    aa[i] = ai;
     bb[i] = i > 1 ? b[i] * b[i] : 0.0;
+    af[i] = ff_of(ai);
+    bf[i] = ff_of(bb[i]);
+    const double r = (i > 1 ? fabs(b[i]) : 0.0) + (i < m ? fabs(b[i + 1]) : 0.0);
+    glo = fmin(glo, ai - r);
+    ghi = fmax(ghi, ai + r);
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    glo = fmin(glo, __shfl_xor_sync(0xffffffffu, glo, o));
+    ghi = fmax(ghi, __shfl_xor_sync(0xffffffffu, ghi, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    glo_s[threadIdx.x >> 5] = glo;
+    ghi_s[threadIdx.x >> 5] = ghi;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     double lo = INFINITY, hi = -INFINITY;
-    for (int i = 1; i <= m; ++i) {
-      const double r = (i > 1 ? fabs(b[i]) : 0.0) + (i < m ? fabs(b[i + 1]) : 0.0);
-      lo = fmin(lo, a[i] - r);
-      hi = fmax(hi, a[i] + r);
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) {
+      lo = fmin(lo, glo_s[w]);
+      hi = fmax(hi, ghi_s[w]);
     }
     const double span = fmax(fmax(fabs(lo), fabs(hi)), 1e-300);
     lo_s = lo - 1e-15 * span - 1e-300;
     hi_s = hi + 1e-15 * span + 1e-300;
+    delta_s = 0x1.0p-40 * span;
     last0_s = -1;
     top_s = 0;
   }
   __syncthreads();
-  // ---- probe round below the hint
+  const double delta = delta_s;
+  // ---- probe round below the hint (float-float counts, down to delta below it)
   if (isfinite(hint)) {
     const double lo = lo_s;
-    const double hi = fmin(hi_s, hint + 1e-14 * fmax(fabs(hint), 1e-300));
+    const double hi = fmin(hi_s, hint + 1e-14 * fmax(fabs(hint), 1e-300) + delta);
     const double D = hi - lo;
-    const double tiny = 1e-16 * fmax(fabs(hi), 1e-300);
+    const double tiny = delta;
     if (D > 2.0 * tiny) {
       // x_i = hi - D r^i, i = 0..P-2 (x_0 = lo), r^(P-2) = tiny / D; lane P-1 checks x = hi
       const double lr = log2(tiny / D) / (double)(P - 2);
       if (threadIdx.x < P) {
         const int i = threadIdx.x;
         const double x = (i == P - 1) ? hi : hi - D * exp2(lr * (double)i);
-        const int c = (x > lo && x <= hi) ? sturm_count(aa, bb, m, x) : (x <= lo ? 0 : 1);
+        const int c = (x > lo && x <= hi) ? sturm_count_ff(af, bf, m, ff_of(x)) : (x <= lo ? 0 : 1);
         if (i == P - 1) {
           top_s = c;
         } else if (c == 0) {
@@ -116,29 +247,54 @@ __device__ __forceinline__ double sturm_lowest(const double* a, const double* b,
       __syncthreads();
     }
   }
-  // ---- equally spaced rounds
-  for (int round = 0; round < 128; ++round) {
+  // ---- equally spaced rounds: float-float (2 P points, two per thread) while the bracket is
+  // wider than 4 delta, then (after widening by delta) FP64 (P points) until the bracket is
+  // within 4 units in the last place of its ends or stops shrinking
+  bool fp64 = false;
+  for (int round = 0; round < 160; ++round) {
+    if (!fp64 && !(hi_s - lo_s > 4.0 * delta)) {
+      fp64 = true;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        lo_s -= delta;
+        hi_s += delta;
+      }
+      __syncthreads();
+    }
+    const int np = fp64 ? P : 2 * P;
     const double lo = lo_s, hi = hi_s;
-    const double w = (hi - lo) / (double)(P + 1);
-    if (threadIdx.x == 0) first_s = P;
+    const double w = (hi - lo) / (double)(np + 1);
+    if (threadIdx.x == 0) first_s = np;
     __syncthreads();
     if (threadIdx.x < P) {
-      const double x = lo + w * (double)(threadIdx.x + 1);
-      const bool valid = x > lo && x < hi;
-      if (valid && sturm_count(aa, bb, m, x) >= 1) atomicMin(&first_s, (int)threadIdx.x);
+      if (fp64) {
+        const double x = lo + w * (double)(threadIdx.x + 1);
+        if (x > lo && x < hi && sturm_count(aa, bb, m, x) >= 1) atomicMin(&first_s, (int)threadIdx.x);
+      } else {
+        const int k0 = threadIdx.x, k1 = threadIdx.x + P;
+        const double x0 = lo + w * (double)(k0 + 1), x1 = lo + w * (double)(k1 + 1);
+        int c0, c1;
+        sturm_count_ff2(af, bf, m, ff_of(x0), ff_of(x1), c0, c1);
+        if (x0 > lo && x0 < hi && c0 >= 1) atomicMin(&first_s, k0);
+        else if (x1 > lo && x1 < hi && c1 >= 1) atomicMin(&first_s, k1);
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       const int k = first_s;
-      const double nhi = (k < P) ? lo + w * (double)(k + 1) : hi;
+      const double nhi = (k < np) ? lo + w * (double)(k + 1) : hi;
       const double nlo = (k > 0) ? lo + w * (double)k : lo;
       lo_s = fmax(nlo, lo);
       hi_s = fmin(nhi, hi);
     }
     __syncthreads();
-    if (!(lo_s < hi_s) || (lo_s == lo && hi_s == hi)) break;
-    const double mid = 0.5 * (lo_s + hi_s);
-    if (!(mid > lo_s && mid < hi_s)) break;
+    if (fp64) {
+      if (!(lo_s < hi_s) || (lo_s == lo && hi_s == hi)) break;
+      const double mid = 0.5 * (lo_s + hi_s);
+      if (!(mid > lo_s && mid < hi_s)) break;
+      const double mag = fmax(fabs(lo_s), fabs(hi_s));
+      if (hi_s - lo_s <= 4.0 * (mag > 0.0 ? ldexp(1.0, ilogb(mag) - 52) : 0.0)) break;
+    }
   }
   return hi_s;
 }
