@@ -39,7 +39,13 @@ constexpr int bctas_per_sm() { return sizeof(T) == 4 ? kBCtasPerSm : 4; }
 // Shared buffer of the batched kernel: a block of up rows staged for the H.v phase, or the
 // Sturm workspace of the leader CTA (used at different times).
 constexpr int kBRowFloats = 4096;
-constexpr int kBSmemBytes = kBRowFloats * 4 > kSturmWork * 8 ? kBRowFloats * 4 : kSturmWork * 8;
+// Dynamic shared memory of the batched kernels: the row-block staging area, or the bisection
+// workspace of T_m for m <= max_steps, whichever is larger (sized per run, so short runs keep
+// the L1 data cache that the hop tables are read through).
+static size_t bsmem_bytes(int max_steps) {
+  const size_t sturm = (size_t)sturm_work_doubles(max_steps + 2) * sizeof(double);
+  return sturm > (size_t)kBRowFloats * 4 ? sturm : (size_t)kBRowFloats * 4;
+}
 
 struct BInst {
   const uint32_t* upb;
@@ -199,7 +205,7 @@ template <typename T>
 __device__ bool run_instance(const BArgs& a, const BInst& I, const RunSpec& R, int c, int g,
                              int first_cta, unsigned* bc, unsigned* bg, double* red, int* stop_s,
                              unsigned char* bsm) {
-  constexpr int kRowElems = kBSmemBytes / (int)sizeof(T);  // staged elements of a row block
+  constexpr int kRowElems = kBRowFloats * 4 / (int)sizeof(T);  // staged elements of a row block
   T* xsm = reinterpret_cast<T*>(bsm);
   const bool leader = c == 0;
   const bool multi = g > 1;
@@ -372,7 +378,7 @@ __device__ bool run_instance(const BArgs& a, const BInst& I, const RunSpec& R, i
       int st = *stop_s;
       if (st != 0 || j >= R.max_steps || (j % R.check) == 0) {
         const double E = sturm_lowest(al, be, j, S->last_E0_step > 0 ? S->last_E0 : NAN,
-                                      reinterpret_cast<double*>(bsm));
+                                      reinterpret_cast<double*>(bsm), R.max_steps + 2);
         if (threadIdx.x == 0) {
           e0[j] = E;
           if (st == 0 && R.tol > 0.0 && S->last_E0_step > 0 &&
@@ -400,7 +406,7 @@ __global__ void __launch_bounds__(kBThreads, bctas_per_sm<T>())
 batched_lanczos_kernel(BArgs a) {
   __shared__ double red[33];
   __shared__ int stop_s;
-  __shared__ __align__(16) unsigned char bsm[kBSmemBytes];
+  extern __shared__ __align__(16) unsigned char bsm[];
   const int gi = a.group_of_cta[blockIdx.x];
   const BGroup G = a.groups[gi];
   const int c = blockIdx.x - G.first_cta, g = G.ncta;
@@ -763,12 +769,13 @@ ed_status run_plan(BatchRun& R, const Plan& p, const Plan* p2, const ed_opts* o,
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   ED_TRY_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  cudaError_t le = cudaLaunchCooperativeKernel(kernel, p.grid, kBThreads, args, 0, s);
+  const size_t dsm = bsmem_bytes(o->max_steps), dsm2 = bsmem_bytes(R.refine_steps);
+  cudaError_t le = cudaLaunchCooperativeKernel(kernel, p.grid, kBThreads, args, dsm, s);
   if (le == cudaSuccess && R.mixed)
     le = cudaLaunchCooperativeKernel((const void*)batched_ritz_kernel, p2->grid, kBThreads, argsr, 0, s);
   if (le == cudaSuccess && R.mixed)
     le = cudaLaunchCooperativeKernel((const void*)batched_lanczos_kernel<double>, p2->grid, kBThreads,
-                                     args2, 0, s);
+                                     args2, dsm2, s);
   cudaError_t ce = cudaStreamEndCapture(s, &graph);
   if (le != cudaSuccess || ce != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
@@ -953,15 +960,15 @@ static ed_status solve_batched(int32_t n, const ed_basis* const* bases, const ed
   int per_sm = 0, per_sm2 = 0;
   if (o->dtype == ED_F64_NATIVE)
     ED_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_lanczos_kernel<double>,
-                                                              kBThreads, 0));
+                                                              kBThreads, bsmem_bytes(o->max_steps)));
   else
     ED_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_lanczos_kernel<float>,
-                                                              kBThreads, 0));
+                                                              kBThreads, bsmem_bytes(o->max_steps)));
   if (mixed) {  // the Ritz and refinement launches share a plan
     int pm = 0, pd = 0;
     ED_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pm, batched_ritz_kernel, kBThreads, 0));
     ED_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pd, batched_lanczos_kernel<double>,
-                                                              kBThreads, 0));
+                                                              kBThreads, bsmem_bytes(refine_steps)));
     per_sm2 = std::min(pm, pd);
   }
   ED_CHECK_ARG(per_sm >= 1 && (!mixed || per_sm2 >= 1), "%s: the batched kernels do not fit an SM", fn);

@@ -149,14 +149,16 @@ __device__ __forceinline__ void sturm_count_ff2(const FF* aa, const FF* bb, int 
   }
 }
 
-// Shared-memory workspace of sturm_lowest: a_i and b_i^2 for i <= ED_MAX_STEPS + 1, in FP64
-// and as float-float pairs.
-constexpr int kSturmWork = 4 * (ED_MAX_STEPS + 2);
+// Shared-memory workspace of sturm_lowest for T_m with m <= cap - 2: a_i and b_i^2 in FP64
+// and as float-float pairs, 4 cap doubles (kSturmWork for any m <= ED_MAX_STEPS).
+__host__ __device__ constexpr int sturm_work_doubles(int cap) { return 4 * cap; }
+constexpr int kSturmCap = ED_MAX_STEPS + 2;
+constexpr int kSturmWork = sturm_work_doubles(kSturmCap);
 
 // lambda_min(T_m) by multisection, called by the whole block (>= 128 threads); returns the
 // upper end of the final bracket (valid in every thread). a, b: 1-based a_1..a_m, b_2..b_m.
-// The diagonal and the squared off-diagonal are staged in `work` (kSturmWork doubles of
-// shared memory). Each round evaluates the Sturm count at 128 interior points of the bracket
+// The diagonal and the squared off-diagonal are staged in `work` (sturm_work_doubles(cap)
+// doubles of shared memory, m <= cap - 2). Each round evaluates the Sturm count at 128 interior points of the bracket
 // (four warps, one per SM sub-partition) and keeps the sub-interval holding the first
 // eigenvalue. The rounds first count in float-float arithmetic, until the bracket is within
 // delta = 2^-40 ||T|| (256 times the float-float count's backward error); the bracket is
@@ -166,12 +168,12 @@ constexpr int kSturmWork = 4 * (ED_MAX_STEPS + 2);
 // Cauchy interlacing; NaN = none), a first round probes geometrically spaced points below
 // it, so a bracket of the size of the last change is found in one round.
 __device__ __forceinline__ double sturm_lowest(const double* a, const double* b, int m,
-                                               double hint, double* work) {
+                                               double hint, double* work, int cap = kSturmCap) {
   constexpr int P = 128;
   double* aa = work;
-  double* bb = work + (ED_MAX_STEPS + 2);
-  FF* af = reinterpret_cast<FF*>(work + 2 * (ED_MAX_STEPS + 2));
-  FF* bf = af + (ED_MAX_STEPS + 2);
+  double* bb = work + cap;
+  FF* af = reinterpret_cast<FF*>(work + 2 * cap);
+  FF* bf = af + cap;
   __shared__ double lo_s, hi_s, delta_s;
   __shared__ double glo_s[32], ghi_s[32];
   __shared__ int first_s, last0_s, top_s;
