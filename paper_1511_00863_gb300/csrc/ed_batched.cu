@@ -1,12 +1,13 @@
 // Batched Lanczos (Sec. 2.2, Algorithm 1) over many independent (lattice, filling, U)
 // instances in ONE persistent cooperative kernel launch, captured in a CUDA graph.
 //
-// Instances are packed onto groups of co-resident CTAs by a schedule (sch_*): an instance
+// Instances are packed onto groups of co-resident CTAs by a schedule (kScheds): an instance
 // whose dimension reaches a threshold gets a group of several CTAs, smaller instances run
 // one after another inside single-CTA groups (only __syncthreads needed there). Groups
 // with several CTAs synchronise through a global-memory barrier whose spin is bounded:
 // when it runs out the kernel records ED_ERR_TIMEOUT for the batch and returns.
-// Per instance and step (FP32 vectors, FP64 scalars, as the single-instance ED_F32 path):
+// Per instance and step (FP32 or FP64 vectors, FP64 scalars, as the single-instance ED_F32 /
+// ED_F64_NATIVE paths):
 //   phase 1: w = s_c H B_c - b_j s_p B_p (written over B_p), partial sums of w . f_j
 //   phase 2: a_j, q = w - a_j f_j, partial sums of q . q
 //   phase 3: b_{j+1}, scale of f_{j+1}, every `check` steps E0(j) = lambda_min(T_j) by
@@ -36,8 +37,8 @@ constexpr int kBThreads = 256;
 constexpr int kBCtasPerSm = 6;
 template <typename T>
 constexpr int bctas_per_sm() { return sizeof(T) == 4 ? kBCtasPerSm : 4; }
-// Shared buffer of the batched kernel: a block of up rows staged for the H.v phase, or the
-// Sturm workspace of the leader CTA (used at different times).
+// Staging area of the H.v phase (a block of up rows, at most kBRowFloats * 4 bytes); the same
+// shared buffer holds the leader CTA's bisection workspace at another time.
 constexpr int kBRowFloats = 4096;
 // Dynamic shared memory of the batched kernels: the row-block staging area, or the bisection
 // workspace of T_m for m <= max_steps, whichever is larger (sized per run, so short runs keep
