@@ -435,7 +435,7 @@ ed_status ed_hv_down_tables(const int32_t* hop, const int32_t* hop_amp, const ui
  *  slot_lo [*ld]: slot of column p within its aligned group of G (columns counted from the
  *          slice start); cstart[3] the slice starts (*ld = cstart[2]); colpos [dim] the
  *          column of each down rank; *rows, *xrows the row counts of table and xtable.
- * ED_ERR_ARG when a capacity is too small, a slice does not fit 15 bits, or a column has
+ * ED_ERR_ARG when a capacity is too small, a slice does not fit 16 bits, or a column has
  * more than 255 hops of one sign. */
 ed_status ed_hv_split_tables(const int32_t* hop, const uint32_t* bits, int64_t dim,
                              int32_t maxhops, int32_t V, int32_t G, int32_t site,

@@ -422,8 +422,8 @@ ed_status build_split_tables(const int32_t* hop, const uint32_t* bits, int64_t n
     const int64_t ns = (int64_t)members[sl].size();
     lds[sl] = (int)((ns + 1 + CW - 1) / CW * CW);  // at least one padding column
   }
-  if (lds[0] + G > 32768 || lds[1] + G > 32768) {
-    set_error("split tables: a slice of %d columns does not fit the 15-bit slot field",
+  if (lds[0] + G > 65536 || lds[1] + G > 65536) {  // slots and columns are 16-bit entries
+    set_error("split tables: a slice of %d columns does not fit the 16-bit table entries",
               std::max(lds[0], lds[1]));
     return ED_ERR_ARG;
   }
