@@ -556,3 +556,27 @@ def test_fp32_norm_accumulation_matches_fp64_norm(ed, name):
             ed.ed_lanczos_destroy(st)
     finally:
         ed.ed_basis_destroy(b)
+
+
+@pytest.mark.parametrize("t,U", [(1e-3, 1e6), (1e4, 0.5), (1.0, 1e-9)])
+@pytest.mark.parametrize("tol", [1e-14, 0.0])
+def test_per_step_lowest_ritz_value_at_extreme_scales(ed, t, U, tol):
+    """E0(j) at every step against LAPACK on the returned a_j, b_j when the entries of T span
+    many orders of magnitude (U / t up to 1e9) or sit far from 1 in size: the bisection's
+    float-float rounds (FP32 exponents, rescaled) and its FP64 finish must still give E0 to a
+    few units in the last place of ||T_j||."""
+    import scipy.linalg
+    L, nu, nd = 8, 3, 3
+    b = ed.ed_build_basis(L, ed_inputs.ring_bonds(L), nu, nd)
+    try:
+        res = ed.ed_lanczos_solve(b, t, U, ed.make_opts(max_steps=60, tol=tol, seed=5, dtype="f64"),
+                                  raise_not_converged=False)
+    finally:
+        ed.ed_basis_destroy(b)
+    a, bt, hist = res["alpha"], res["beta"], res["E0_hist"]
+    n = res["steps"]
+    assert n >= 3
+    for j in range(1, n + 1):
+        w = scipy.linalg.eigvalsh_tridiagonal(a[:j], bt[:j - 1], select="i", select_range=(0, 0))
+        scale = np.max(np.abs(a[:j])) + (np.max(np.abs(bt[:j - 1])) if j > 1 else 0.0)
+        assert abs(hist[j - 1] - w[0]) <= 8 * EPS64 * max(scale, 1e-300), (j, hist[j - 1], w[0])
