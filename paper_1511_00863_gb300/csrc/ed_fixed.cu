@@ -250,6 +250,35 @@ struct FxHvArgs {
   int maxhops_up, maxhops_dn;
 };
 
+// s += the signed values of a state's hop targets (integers: the order does not matter),
+// four hops at a time with their table entries and values loaded before any is added, so a
+// thread has more loads in flight. tab[k * stride] is hop k's entry; a target >= n is
+// padding, and the rest of the state's list is padding too.
+template <typename Load>
+__device__ __forceinline__ void fx_add_hops(long long& s, const int32_t* tab, int64_t stride, int mh,
+                                            int64_t n, Load load) {
+  int k = 0;
+  for (; k + 4 <= mh; k += 4) {
+    uint32_t e[4];
+    long long v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) e[q] = (uint32_t)tab[(int64_t)(k + q) * stride];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t tg = (int64_t)(e[q] & kTargetMask);
+      v[q] = tg < n ? sgn_apply(load(tg), e[q]) : 0LL;
+    }
+    s += (v[0] + v[1]) + (v[2] + v[3]);
+    if ((int64_t)(e[3] & kTargetMask) >= n) return;
+  }
+  for (; k < mh; ++k) {
+    const uint32_t e = (uint32_t)tab[(int64_t)k * stride];
+    const int64_t tg = (int64_t)(e & kTargetMask);
+    if (tg >= n) return;
+    s += sgn_apply(load(tg), e);
+  }
+}
+
 // W = round((a S + b n X + c P) 2^k), written over P; partial sums of W X (exact).
 // Row-staged like hv_staged_kernel: R up rows per CTA, interleaved in shared memory.
 template <int R>
@@ -298,12 +327,8 @@ fx_hv_staged_kernel(FxHvArgs a, const long long* __restrict__ x, long long* __re
     for (int r = 0; r < R; ++r) {
       const int64_t u = u0 + r;
       if (u < a.dim_up) {
-        for (int kk = 0; kk < a.maxhops_up; ++kk) {
-          const uint32_t e = (uint32_t)ut[r * a.maxhops_up + kk];
-          const int64_t tg = (int64_t)(e & kTargetMask);
-          if (tg >= a.dim_up) break;
-          hs[r] += sgn_apply(x[tg * a.ld + d], e);
-        }
+        fx_add_hops(hs[r], ut + r * a.maxhops_up, 1, a.maxhops_up, a.dim_up,
+                    [&](int64_t tg) { return x[tg * a.ld + d]; });
         const long long xc = xs[d * R + r];
         const long long nx = xc * (long long)__popc(ub[r] & db);
         long long* yp = y + u * a.ld + d;
@@ -332,18 +357,9 @@ fx_hv_global_kernel(FxHvArgs a, const long long* __restrict__ x, long long* __re
     const int64_t u = g / a.dim_dn, d = g - u * a.dim_dn;
     const long long* xr = x + u * a.ld;
     long long hs = 0;
-    for (int kk = 0; kk < a.maxhops_dn; ++kk) {
-      const uint32_t e = (uint32_t)a.hop_dn[(int64_t)kk * a.dim_dn + d];
-      const int64_t tg = (int64_t)(e & kTargetMask);
-      if (tg >= a.dim_dn) break;
-      hs += sgn_apply(xr[tg], e);
-    }
-    for (int kk = 0; kk < a.maxhops_up; ++kk) {
-      const uint32_t e = (uint32_t)a.hop_up[(int64_t)kk * a.dim_up + u];
-      const int64_t tg = (int64_t)(e & kTargetMask);
-      if (tg >= a.dim_up) break;
-      hs += sgn_apply(x[tg * a.ld + d], e);
-    }
+    fx_add_hops(hs, a.hop_dn + d, a.dim_dn, a.maxhops_dn, a.dim_dn, [&](int64_t tg) { return xr[tg]; });
+    fx_add_hops(hs, a.hop_up + u, a.dim_up, a.maxhops_up, a.dim_up,
+                [&](int64_t tg) { return x[tg * a.ld + d]; });
     const long long xc = xr[d];
     const long long nx = xc * (long long)__popc(a.up_bits[u] & a.dn_bits[d]);
     long long* yp = y + u * a.ld + d;
