@@ -26,6 +26,38 @@ struct HvArgs {
   double t, U;
 };
 
+// acc += c_k v_k over a state's hops in table order (c_k = -t or +t by the fermion sign; the
+// same sequence of multiply-adds as a one-at-a-time loop, so the same rounding), taking the
+// table entries and gathered values of four hops before adding any: more loads in flight.
+// tab[k * stride] is hop k's entry; a target >= n is padding, and the rest of the state's
+// list is padding too.
+template <typename T, typename Load>
+__device__ __forceinline__ void hv_add_hops(T& acc, const int32_t* tab, int64_t stride, int mh, int64_t n,
+                                            T tt, Load load) {
+  int k = 0;
+  for (; k + 4 <= mh; k += 4) {
+    uint32_t e[4];
+    T v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) e[q] = (uint32_t)tab[(int64_t)(k + q) * stride];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t tg = (int64_t)(e[q] & kTargetMask);
+      v[q] = tg < n ? load(tg) : T(0);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if ((int64_t)(e[q] & kTargetMask) < n) acc += ((e[q] & kSignBit) ? tt : -tt) * v[q];
+    if ((int64_t)(e[3] & kTargetMask) >= n) return;
+  }
+  for (; k < mh; ++k) {
+    const uint32_t e = (uint32_t)tab[(int64_t)k * stride];
+    const int64_t tg = (int64_t)(e & kTargetMask);
+    if (tg >= n) return;
+    acc += ((e & kSignBit) ? tt : -tt) * load(tg);
+  }
+}
+
 template <typename T, int R, bool kLz>
 __global__ void __launch_bounds__(kHvThreads)
 hv_staged_kernel(HvArgs a, const T* __restrict__ x, T* __restrict__ y, LzHvArgs lz) {
@@ -78,13 +110,8 @@ hv_staged_kernel(HvArgs a, const T* __restrict__ x, T* __restrict__ y, LzHvArgs 
     for (int r = 0; r < R; ++r) {
       const int64_t u = u0 + r;
       if (u < a.dim_up) {
-        for (int k = 0; k < a.maxhops_up; ++k) {
-          const uint32_t e = (uint32_t)ut[r * a.maxhops_up + k];
-          const int64_t tg = (int64_t)(e & kTargetMask);
-          if (tg >= a.dim_up) break;
-          const T c = (e & kSignBit) ? tt : -tt;
-          acc[r] += c * x[tg * a.ld + d];
-        }
+        hv_add_hops(acc[r], ut + r * a.maxhops_up, 1, a.maxhops_up, a.dim_up, tt,
+                    [&](int64_t tg) { return x[tg * a.ld + d]; });
         if (kLz) {
           const T f = sc * xs[d * R + r];
           const T w = sc * acc[r] - bsp * y[u * a.ld + d];
@@ -123,18 +150,9 @@ hv_global_kernel(HvArgs a, const T* __restrict__ x, T* __restrict__ y, LzHvArgs 
     const int64_t u = g / a.dim_dn, d = g - u * a.dim_dn;
     const T* xr = x + u * a.ld;
     T acc = UU * (T)__popc(a.up_bits[u] & a.dn_bits[d]) * xr[d];
-    for (int k = 0; k < a.maxhops_dn; ++k) {
-      const uint32_t e = (uint32_t)a.hop_dn[(int64_t)k * a.dim_dn + d];
-      const int64_t tg = (int64_t)(e & kTargetMask);
-      if (tg >= a.dim_dn) break;
-      acc += ((e & kSignBit) ? tt : -tt) * xr[tg];
-    }
-    for (int k = 0; k < a.maxhops_up; ++k) {
-      const uint32_t e = (uint32_t)a.hop_up[(int64_t)k * a.dim_up + u];
-      const int64_t tg = (int64_t)(e & kTargetMask);
-      if (tg >= a.dim_up) break;
-      acc += ((e & kSignBit) ? tt : -tt) * x[tg * a.ld + d];
-    }
+    hv_add_hops(acc, a.hop_dn + d, a.dim_dn, a.maxhops_dn, a.dim_dn, tt, [&](int64_t tg) { return xr[tg]; });
+    hv_add_hops(acc, a.hop_up + u, a.dim_up, a.maxhops_up, a.dim_up, tt,
+                [&](int64_t tg) { return x[tg * a.ld + d]; });
     if (kLz) {
       const T f = sc * xr[d];
       const T w = sc * acc - bsp * y[u * a.ld + d];
