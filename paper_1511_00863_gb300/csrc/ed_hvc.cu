@@ -80,6 +80,42 @@ __device__ __forceinline__ V signed_amp(V A, uint32_t e) {
   return A;
 }
 
+// acc += A_k v_k over a state's hops in table order (the same complex multiply-adds as a
+// one-at-a-time loop), taking the table entries and gathered values of four hops before
+// adding any: more loads in flight. entry(k) gives hop k's table entry, amp(k, e) its signed
+// amplitude, load(target) the gathered value; a target >= n is padding, and the rest of the
+// state's list is padding too.
+template <typename V, typename Entry, typename Amp, typename Load>
+__device__ __forceinline__ void hvc_add_hops(V& acc, int mh, int64_t n, Entry entry, Amp amp, Load load) {
+  int k = 0;
+  for (; k + 4 <= mh; k += 4) {
+    uint32_t e[4];
+    V v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) e[q] = entry(k + q);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t tg = (int64_t)(e[q] & kTargetMask);
+      if (tg < n) {
+        v[q] = load(tg);
+      } else {
+        v[q].x = 0;
+        v[q].y = 0;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if ((int64_t)(e[q] & kTargetMask) < n) cmac(acc, amp(k + q, e[q]), v[q]);
+    if ((int64_t)(e[3] & kTargetMask) >= n) return;
+  }
+  for (; k < mh; ++k) {
+    const uint32_t e = entry(k);
+    const int64_t tg = (int64_t)(e & kTargetMask);
+    if (tg >= n) return;
+    cmac(acc, amp(k, e), load(tg));
+  }
+}
+
 template <typename T, int R, bool kLz>
 __global__ void __launch_bounds__(kHvcThreads)
 hvc_staged_kernel(HvcArgs a, const typename CVec<T>::type* __restrict__ x,
@@ -140,12 +176,10 @@ hvc_staged_kernel(HvcArgs a, const typename CVec<T>::type* __restrict__ x,
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      for (int k = 0; k < a.maxhops_up; ++k) {
-        const uint32_t e = (uint32_t)ut[r * MH + k];
-        const int64_t tg = (int64_t)(e & kTargetMask);
-        if (tg >= a.dim_up) break;
-        cmac(acc[r], signed_amp(amp[ua[r * MH + k]], e), x[tg * a.ld + d]);
-      }
+      hvc_add_hops(
+          acc[r], a.maxhops_up, a.dim_up, [&](int k) { return (uint32_t)ut[r * MH + k]; },
+          [&](int k, uint32_t e) { return signed_amp(amp[ua[r * MH + k]], e); },
+          [&](int64_t tg) { return x[tg * a.ld + d]; });
     }
     const uint32_t db = a.dn_bits[d];
 #pragma unroll
@@ -204,20 +238,18 @@ hvc_global_kernel(HvcArgs a, const typename CVec<T>::type* __restrict__ x,
     const T nU = UU * (T)__popc(a.up_bits[u] & a.dn_bits[d]);
     acc.x = nU * xc.x;
     acc.y = nU * xc.y;
-    for (int k = 0; k < a.maxhops_dn; ++k) {
-      const uint32_t e = (uint32_t)a.hop_dn[(int64_t)k * a.dim_dn + d];
-      const int64_t tg = (int64_t)(e & kTargetMask);
-      if (tg >= a.dim_dn) break;
-      const int ai = a.hopa_dn ? a.hopa_dn[(int64_t)k * a.dim_dn + d] : 0;
-      cmac(acc, signed_amp(amp_entry<V>(a, ai), e), xr[tg]);
-    }
-    for (int k = 0; k < a.maxhops_up; ++k) {
-      const uint32_t e = (uint32_t)a.hop_up[(int64_t)k * a.dim_up + u];
-      const int64_t tg = (int64_t)(e & kTargetMask);
-      if (tg >= a.dim_up) break;
-      const int ai = a.hopa_up ? a.hopa_up[(int64_t)k * a.dim_up + u] : 0;
-      cmac(acc, signed_amp(amp_entry<V>(a, ai), e), x[tg * a.ld + d]);
-    }
+    hvc_add_hops(
+        acc, a.maxhops_dn, a.dim_dn, [&](int k) { return (uint32_t)a.hop_dn[(int64_t)k * a.dim_dn + d]; },
+        [&](int k, uint32_t e) {
+          return signed_amp(amp_entry<V>(a, a.hopa_dn ? a.hopa_dn[(int64_t)k * a.dim_dn + d] : 0), e);
+        },
+        [&](int64_t tg) { return xr[tg]; });
+    hvc_add_hops(
+        acc, a.maxhops_up, a.dim_up, [&](int k) { return (uint32_t)a.hop_up[(int64_t)k * a.dim_up + u]; },
+        [&](int k, uint32_t e) {
+          return signed_amp(amp_entry<V>(a, a.hopa_up ? a.hopa_up[(int64_t)k * a.dim_up + u] : 0), e);
+        },
+        [&](int64_t tg) { return x[tg * a.ld + d]; });
     V* yp = y + u * a.ld + d;
     if (kLz) {
       const V P = *yp;
