@@ -90,3 +90,27 @@ def test_matrix_free_rows_match_the_matrix(case):
     x = r.normal(size=H.shape[0]) + 1j * r.normal(size=H.shape[0])
     rows = np.arange(H.shape[0])
     assert np.allclose(ch.hv_rows_complex(L, bonds, tb, nu, nd, 0.9, 1.7, x, rows), H @ x, atol=1e-13)
+
+
+@pytest.mark.parametrize("species", ["up", "down"])
+def test_one_particle_sector_is_the_hopping_matrix(species):
+    """With one particle in the lattice the many-body basis is the site basis (state 1 << s
+    has rank s) and no fermion sign arises, so H is the first-quantised matrix of the model:
+    bond b = (i, j) moves the particle from j to i with amplitude -t tau_b (row i, column j)
+    and back with -t conj(tau_b). This fixes which end of a bond gets tau and which its
+    conjugate, a convention every spectrum is blind to (conjugating all tau leaves the
+    spectrum unchanged)."""
+    L, bonds = 7, CASES[2][1]
+    tb = _rand_tb(len(bonds), 8)
+    t = 0.8
+    nu, nd = (1, 0) if species == "up" else (0, 1)
+    H = ch.hamiltonian_csr_complex(L, bonds, tb, nu, nd, t, 5.0).toarray()
+    h = np.zeros((L, L), dtype=complex)
+    for (i, j), tau in zip(bonds, tb):
+        h[i, j] += -t * tau
+        h[j, i] += -t * np.conj(tau)
+    assert np.array_equal(H, h)
+    assert np.array_equal(ch.single_particle_matrix(L, bonds, tb, t), h)
+    x = np.random.default_rng(9).normal(size=L) + 1j
+    assert np.allclose(ch.hv_rows_complex(L, bonds, tb, nu, nd, t, 5.0, x, np.arange(L)), h @ x,
+                       rtol=0, atol=1e-14)

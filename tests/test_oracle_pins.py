@@ -65,6 +65,16 @@ def test_species_states_ascending_and_counted(L, N):
     assert np.all(basis.rank_of(s, s) == np.arange(len(s)))
 
 
+@pytest.mark.parametrize("L,nu,nd", [(6, 1, 4), (7, 3, 2), (8, 0, 5), (5, 5, 2)])
+def test_dimension_unequal_fillings(L, nu, nd):
+    """Eq. 2 with N_up != N_dn (every dimension the paper prints is at N_up = N_dn), for the
+    enumerated count and for the size of the explicit H."""
+    expect = math.comb(L, nu) * math.comb(L, nd)
+    assert basis.dimension(L, nu, nd) == expect
+    H = hamiltonian.hamiltonian_csr(L, ed_inputs.ring_bonds(L), nu, nd, 1.0, 2.0)
+    assert H.shape == (expect, expect)
+
+
 def test_popcount_against_python():
     rng = np.random.default_rng(0)
     a = rng.integers(0, 2**62, size=1000)
@@ -234,6 +244,58 @@ def test_lanczos_matches_dense(case):
     E_dense = dense.spectrum(*case)[0]
     E = _lanczos_E0(*case)
     assert abs(E - E_dense) <= 1e-11 * max(1, abs(E_dense))
+
+
+@pytest.mark.parametrize("reorth", [False, True])
+def test_lanczos_on_tridiagonal_returns_its_entries(reorth):
+    """Algorithm 1 applied to an unreduced symmetric tridiagonal matrix T (positive off-
+    diagonal) from f_1 = e_1 produces f_j = e_j, a_j = T_jj and b_{j+1} = T_{j,j+1}: the
+    Krylov basis of e_1 under T is the unit-vector basis. In FP64 every step is exact
+    (each subtraction cancels equal numbers, sqrt(b^2) rounds back to b), so the
+    coefficients must match bit for bit. The start is given with norm 3, which Algorithm 1
+    normalises. fixed_steps must run all m steps although E0(j) settles earlier; at step m
+    the residual is exactly zero (breakdown). Small off-diagonals (down to 0.01 against a
+    spread of diagonal entries) must not be taken for a breakdown."""
+    rng = np.random.default_rng(12)
+    m = 40
+    a = rng.normal(size=m) * 2.0
+    b = rng.uniform(0.01, 1.0, size=m - 1)
+    b[7] = 0.01
+    T = sp.diags([b, a, b], [-1, 0, 1], format="csr")
+    e1 = np.zeros(m)
+    e1[0] = 3.0
+    r = lanczos.lanczos(lambda v: T @ v, e1, max_steps=m, tol=1e-12, reorth=reorth,
+                        fixed_steps=True)
+    assert r.steps == m and r.breakdown
+    assert np.array_equal(np.array(r.alpha), a)
+    assert np.array_equal(np.array(r.beta[:-1]), b) and r.beta[-1] == 0.0
+    ref = sla.eigh_tridiagonal(a, b, eigvals_only=True)[0]
+    assert abs(r.E0 - ref) <= 4e-15 * max(1.0, abs(ref))
+    # the same run with the convergence test on stops as soon as E0(j) settles, before m
+    r2 = lanczos.lanczos(lambda v: T @ v, e1, max_steps=m, tol=1e-12, reorth=reorth)
+    assert r2.converged and not r2.breakdown and r2.steps < m
+    assert r2.alpha == r.alpha[:r2.steps]
+
+
+def test_normalized_start_is_unit_and_parallel():
+    raw = ed_inputs.start_vector_raw(5, 1000) * 7.5
+    f = lanczos.normalized_start(raw)
+    assert abs(np.linalg.norm(f) - 1.0) <= 1e-15
+    k = int(np.argmax(np.abs(raw)))
+    assert np.allclose(f * (raw[k] / f[k]), raw, rtol=1e-14, atol=0)
+    assert np.sign(f[k]) == np.sign(raw[k])
+
+
+@pytest.mark.parametrize("case", CASES[:3])
+def test_dense_ground_state_is_a_gauged_eigenvector(case):
+    """ground_state returns a unit eigenvector for the lowest eigenvalue, gauged so that its
+    largest-magnitude entry (lowest index on ties) is positive."""
+    E0, psi = dense.ground_state(*case)
+    H = hamiltonian.hamiltonian_csr(*case)
+    assert abs(np.linalg.norm(psi) - 1.0) <= 1e-13
+    assert np.max(np.abs(H @ psi - E0 * psi)) <= 1e-11
+    k = int(np.argmax(np.abs(psi)))
+    assert psi[k] > 0
 
 
 def test_lanczos_breakdown_on_eigenvector():
