@@ -81,3 +81,23 @@ def test_batched_argument_errors_without_gpu(lib_path):
         with pytest.raises(ed.EdError) as e:
             call()
         assert e.value.status == ed.ED_ERR_ARG and word in str(e.value), str(e.value)
+
+
+def test_null_arguments_rejected_without_gpu(lib_path):
+    """Every entry point called with NULL pointers and zero sizes returns ED_ERR_ARG with a
+    message, on the host and before any CUDA call; the destroy functions accept NULL."""
+    import ctypes
+
+    import paper_1511_00863_gb300 as ed
+    scalars = (ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double)
+    for name, (res, args) in ed._SIGS.items():
+        if name == "ed_last_error":
+            continue
+        vals = [0 if a in scalars else None for a in args]
+        r = getattr(ed._lib, name)(*vals)
+        if res is None:
+            assert name.endswith("_destroy")
+            continue
+        assert r == ed.ED_ERR_ARG, (name, r)
+        msg = ed._lib.ed_last_error().decode()
+        assert msg.startswith(name + ":"), (name, msg)
