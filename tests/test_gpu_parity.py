@@ -126,6 +126,45 @@ def test_hv_small_elementwise(ed, case, dtype):
         ed.ed_basis_destroy(b)
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_hv_rejects_overlap_and_misalignment(ed, dtype):
+    """ed_hv refuses, with ED_ERR_ARG and before any launch, an output that overlaps the
+    input (the same buffer, or one shifted by 16 bytes) and vectors that are not 16-byte
+    aligned (shifted by one element). The output keeps its contents, and a valid call on the
+    same basis afterwards matches the oracle."""
+    case = HV_CASES[0]
+    L, bonds, nu, nd, t, U = case
+    b = ed.ed_build_basis(L, bonds, nu, nd)
+    try:
+        dim = ed.ed_basis_dims(b)[2]
+        tdt = torch.float64 if dtype == "f64" else torch.float32
+        es = 8 if dtype == "f64" else 4
+        buf = torch.zeros(dim + 16 // es, device="cuda", dtype=tdt)
+        other = torch.full((dim + 1,), 7.0, device="cuda", dtype=tdt)
+        assert buf.data_ptr() % 16 == 0 and other.data_ptr() % 16 == 0
+        a = buf[:dim]
+        cases = [(a, a, "overlap"), (a, buf[16 // es:], "overlap"),
+                 (other[1:], buf[:dim], "aligned"), (buf[:dim], other[1:], "aligned")]
+        for x, y, word in cases:
+            before = y.clone()
+            with pytest.raises(ed.EdError) as ei:
+                ed.ed_hv(b, t, U, x, y)
+            assert ei.value.status == ed.ED_ERR_ARG and word in str(ei.value), str(ei.value)
+            torch.cuda.synchronize()
+            assert torch.equal(y, before)
+        x = ed_inputs.uniform_pm1(21, dim)
+        xd = torch.tensor(x, device="cuda", dtype=tdt)
+        yd = torch.empty_like(xd)
+        ed.ed_hv(b, t, U, xd, yd)
+        xr = xd.double().cpu().numpy()
+        rows = np.arange(dim)
+        ref = hamiltonian.hv_rows(L, bonds, nu, nd, t, U, xr, rows)
+        bound = _hv_bound(case, xr, rows, EPS64 if dtype == "f64" else EPS32)
+        assert np.all(np.abs(yd.double().cpu().numpy() - ref) <= bound)
+    finally:
+        ed.ed_basis_destroy(b)
+
+
 FULL = [("torus4x4_5_5", "f64"), ("ring16_8_8", "f32"), ("ring16_8_8", "f64")]
 
 
