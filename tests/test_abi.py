@@ -57,6 +57,13 @@ def test_argument_errors_without_gpu(lib_path):
         ed.ed_build_basis(4, [[0, 0]], 1, 1, stream=0)
     with pytest.raises(ed.EdError):
         ed.ed_build_basis(4, [[0, 1]], 5, 1, stream=0)
+    bad = [((4, [[0, 4]], 1, 1), "bond 0"), ((4, [[-1, 2]], 1, 1), "bond 0"),
+           ((4, [[0, 1]], -1, 1), "particle numbers"), ((0, [], 0, 0), "n_sites"),
+           ((33, [[0, 1]], 1, 1), "n_sites"), ((32, [[0, 31]], 33, 0), "particle numbers")]
+    for args, word in bad:
+        with pytest.raises(ed.EdError) as e:
+            ed.ed_build_basis(*args, stream=0)
+        assert e.value.status == ed.ED_ERR_ARG and word in str(e.value), str(e.value)
 
 
 def test_batched_argument_errors_without_gpu(lib_path):
