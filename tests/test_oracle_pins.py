@@ -212,6 +212,25 @@ def test_energy_monotone_in_U():
     assert all(np.diff(Es) > 0)
 
 
+@pytest.mark.parametrize("L,bonds,nu,nd", [
+    (6, ed_inputs.ring_bonds(6), 3, 3),
+    (5, ed_inputs.ring_bonds(5), 2, 1),
+    (8, ed_inputs.torus_bonds(2, 4), 1, 3),
+])
+def test_variational_bound_and_concavity_in_U(L, bonds, nu, nd):
+    """E0(U) = min over unit psi of <psi|H_0|psi> + U <psi|D|psi> (D = number of doubly
+    occupied sites) is a minimum of functions linear in U, hence concave, and lies below the
+    line through the U = 0 ground state: E0(U) <= E0(0) + U <D>_0, evaluated here with the
+    U = 0 ground state's own energy functional (<psi0|H(U)|psi0>, no closed form of D)."""
+    Us = np.linspace(0.0, 8.0, 9)
+    E = np.array([dense.spectrum(L, bonds, nu, nd, 1.0, U)[0] for U in Us])
+    assert np.all(E[:-2] - 2 * E[1:-1] + E[2:] <= 1e-12)
+    _, psi0 = dense.ground_state(L, bonds, nu, nd, 1.0, 0.0)
+    for U, e in zip(Us, E):
+        H = hamiltonian.hamiltonian_csr(L, bonds, nu, nd, 1.0, U)
+        assert e <= float(psi0 @ (H @ psi0)) + 1e-12
+
+
 # ----------------------------------------------------------------------- tridiagonal
 def test_sturm_against_lapack():
     rng = np.random.default_rng(3)
