@@ -850,6 +850,15 @@ extern "C" ed_status ed_selftest_barrier_timeout(int32_t ctas, int32_t timeout_m
   cudaStream_t s = (cudaStream_t)stream;
   unsigned* bar = nullptr;
   int* err = nullptr;
+  struct ReleaseOnReturn {  // frees the scratch on every return path, error returns included
+    cudaStream_t s;
+    unsigned*& bar;
+    int*& err;
+    ~ReleaseOnReturn() {
+      if (bar) cudaFreeAsync(bar, s);
+      if (err) cudaFreeAsync(err, s);
+    }
+  } release{s, bar, err};
   ED_TRY_CUDA(cudaMallocAsync((void**)&bar, 2 * sizeof(unsigned), s));
   ED_TRY_CUDA(cudaMallocAsync((void**)&err, sizeof(int), s));
   ED_TRY_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
@@ -861,8 +870,6 @@ extern "C" ed_status ed_selftest_barrier_timeout(int32_t ctas, int32_t timeout_m
   int h = 0;
   ED_TRY_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
   ED_TRY_CUDA(cudaStreamSynchronize(s));
-  cudaFreeAsync(bar, s);
-  cudaFreeAsync(err, s);
   if (h) {
     set_error("group barrier wait ran out after %d ms (as the self-test intends)", timeout_ms);
     return ED_ERR_TIMEOUT;

@@ -686,24 +686,28 @@ extern "C" ed_status ed_lanczos_ground_state(const ed_basis* b, const ed_params*
   ed_lanczos* st = nullptr;
   long long* P = nullptr;
   double* yd = nullptr;
-  auto cleanup = [&](ed_status e) {
-    if (st) ed_lanczos_destroy(st);
-    if (P) cudaFree(P);
-    if (yd) cudaFree(yd);
-    return e;
-  };
+  struct ReleaseOnReturn {  // frees the state and scratch on every return path
+    ed_lanczos*& st;
+    long long*& P;
+    double*& yd;
+    ~ReleaseOnReturn() {
+      if (st) ed_lanczos_destroy(st);
+      if (P) cudaFree(P);
+      if (yd) cudaFree(yd);
+    }
+  } release{st, P, yd};
   // ---- pass 1: Algorithm 1 to convergence (stepwise, E0 every step)
   ed_status r = lz_init(b, o, f1, s, 1, false, &st);
-  if (r != ED_OK) return cleanup(r);
-  if ((r = fx_prepare(b)) != ED_OK) return cleanup(r);
+  if (r != ED_OK) return r;
+  if ((r = fx_prepare(b)) != ED_OK) return r;
   int hdr[2] = {0, 0};
   for (int done = 0; done < o->max_steps; done += 8) {
     for (int i = 0; i < 8; ++i)
-      if ((r = lz_launch_step(st, p, s)) != ED_OK) return cleanup(r);
+      if ((r = lz_launch_step(st, p, s)) != ED_OK) return r;
     if (cudaMemcpyAsync(hdr, st->S, 2 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
       set_error("ed_lanczos_ground_state: %s", cudaGetErrorString(cudaGetLastError()));
-      return cleanup(ED_ERR_CUDA);
+      return ED_ERR_CUDA;
     }
     if (hdr[1] != 0) break;
   }
@@ -713,28 +717,27 @@ extern "C" ed_status ed_lanczos_ground_state(const ed_basis* b, const ed_params*
   ED_TRY_CUDA(cudaMemcpy(&lam, &st->S->E0[m], sizeof(double), cudaMemcpyDeviceToHost));
   // ---- Ritz vector of T_m on the device
   if (cudaMalloc((void**)&yd, (size_t)(3 * (m + 2)) * sizeof(double)) != cudaSuccess)
-    return cleanup(ED_ERR_OOM);
+    return ED_ERR_OOM;
   lz_ritz_kernel<<<1, 32, 0, s>>>(st->S, m, lam, yd, yd + (m + 2));
   ED_TRY_CUDA(cudaGetLastError());
   // ---- pass 2: the same steps again from the same start, accumulating y_j f_j
   ed_lanczos* st2 = nullptr;
-  if ((r = lz_init(b, o, f1, s, ED_MAX_STEPS + 1, true, &st2)) != ED_OK) return cleanup(r);
+  if ((r = lz_init(b, o, f1, s, ED_MAX_STEPS + 1, true, &st2)) != ED_OK) return r;
   ed_lanczos_destroy(st);
   st = st2;
   if (cudaMalloc((void**)&P, (size_t)b->dim * sizeof(long long)) != cudaSuccess)
-    return cleanup(ED_ERR_OOM);
+    return ED_ERR_OOM;
   ED_TRY_CUDA(cudaMemsetAsync(P, 0, (size_t)b->dim * sizeof(long long), s));
   for (int j = 1; j <= m; ++j) {
     if ((r = fx_psi_accum(b, st->S, st->cur, yd, j, (const long long*)st->B[st->cur], st->ld,
                           hv2_colpos(st->plan), P, s)) != ED_OK)
-      return cleanup(r);
-    if (j < m && (r = lz_launch_step(st, p, s)) != ED_OK) return cleanup(r);
+      return r;
+    if (j < m && (r = lz_launch_step(st, p, s)) != ED_OK) return r;
   }
-  if ((r = fx_psi_finish(b, P, (long long*)st->pb, (double*)psi, s)) != ED_OK) return cleanup(r);
+  if ((r = fx_psi_finish(b, P, (long long*)st->pb, (double*)psi, s)) != ED_OK) return r;
   ED_TRY_CUDA(cudaStreamSynchronize(s));
   *E0 = lam;
   if (steps) *steps = m;
-  cleanup(ED_OK);
   if (status == 3 && o->tol > 0.0) {
     set_error("ed_lanczos_ground_state: not converged after %d steps", m);
     return ED_ERR_NOT_CONVERGED;
