@@ -185,13 +185,17 @@ def test_split_tables_keep_every_hop(L, bonds, N, V, G):
     (padding on the slice's zero slots) and the cross-slice ones as columns of the other
     slice (padding on one of its padding columns); the in-slice gathers keep the modelled
     bank conflicts of the plain tables."""
+    check_split(L, bonds, N, V, G, 0, wavefront_bound=2.0)
+
+
+def check_split(L, bonds, N, V, G, site, wavefront_bound=None):
     hop, _, bits = hop_table(L, N, bonds)
     n = bits.size
-    out = ed.ed_hv_split_tables(hop, bits, V, G, site=0)
+    out = ed.ed_hv_split_tables(hop, bits, V, G, site=site)
     T, X, kpn, lo, cs, pos, ld = (out[k] for k in ("table", "xtable", "kpn", "slot_lo", "cstart",
                                                    "colpos", "ld"))
     CW = 32 * V
-    occ = (bits & 1) == 1
+    occ = ((bits >> site) & 1) == 1
     nsl = [int(occ.sum()), int(n - occ.sum())]
     assert cs[0] == 0 and cs[2] == ld
     for s_ in range(2):
@@ -246,8 +250,9 @@ def test_split_tables_keep_every_hop(L, bonds, N, V, G):
                     if tgt[k, d] < n:
                         cnt[2 * int(occ[tgt[k, d]] != occ[d]) + int(neg[k, d]), j] += 1
             assert list(kpn[c]) == list(cnt.max(axis=1)), c
-        sub = {"table": T[:, c0:c1], "kpn": kpn[c0 // CW:c1 // CW, :2], "ld": lds}
-        assert modelled_wavefronts(sub, V, G, False) < 2.0
+        if wavefront_bound is not None:
+            sub = {"table": T[:, c0:c1], "kpn": kpn[c0 // CW:c1 // CW, :2], "ld": lds}
+            assert modelled_wavefronts(sub, V, G, False) < wavefront_bound
 
 
 def test_split_tables_bad_geometry():
@@ -255,3 +260,33 @@ def test_split_tables_bad_geometry():
     with pytest.raises(ed.EdError) as e:
         ed.ed_hv_split_tables(hop, bits, 2, 12)
     assert e.value.status == ed.ED_ERR_ARG
+
+
+def _random_lattice(rng):
+    """A bond list on 5-11 sites with random pairs, one of them listed twice and one in both
+    orders (duplicates add), and a random filling with at least one state per slice."""
+    L = int(rng.integers(5, 12))
+    nb = int(rng.integers(L, 2 * L + 1))
+    bonds = []
+    while len(bonds) < nb:
+        i, j = (int(v) for v in rng.integers(0, L, size=2))
+        if i != j:
+            bonds.append((i, j))
+    bonds += [bonds[0], bonds[1][::-1]]
+    N = int(rng.integers(1, L))
+    return L, np.array(bonds), N
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_random_lattices_all_geometries(seed):
+    """Seeded random bond lists (irregular degrees, doubled and reversed bonds) through both
+    table builders at every geometry the ABI allows (V from 1 to 8, odd V included, and G of
+    8, 16 and 32), real and complex entries, and the split tables cut at a random site."""
+    rng = np.random.default_rng(1000 + seed)
+    L, bonds, N = _random_lattice(rng)
+    hop, amp, bits = hop_table(L, N, bonds)
+    V = int(rng.choice([1, 2, 3, 4, 8]))
+    G = int(rng.choice([8, 16, 32]))
+    check_tables(hop, amp, bits, V, G, False)
+    check_tables(hop, amp, bits, V, G, True)
+    check_split(L, bonds, N, V, G, int(rng.integers(0, L)))
