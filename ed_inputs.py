@@ -159,6 +159,35 @@ def batched_instances(seed: int = 4, count: int = 256) -> list[dict]:
     return out
 
 
+def random_lattices(seed: int = 7, count: int = 6) -> list[dict]:
+    """Irregular bond lists for robustness tests of the row-staged H.v: L uniform in 10..12
+    sites, L..2L random pairs (i != j; pairs may repeat, in either order) plus the first pair
+    listed once more and the second reversed; N_up uniform in [3, L - 3] (at least 120 up
+    states), N_dn uniform over the fillings in [1, L - 1] with C(L, N_up) C(L, N_dn) <=
+    400,000; U uniform in [-2, 8), t = 1. Lattice m draws from the SplitMix64 stream seeded
+    seed * 1000 + m."""
+    from math import comb
+    out = []
+    for m in range(count):
+        r = iter(int(v) for v in splitmix64(seed * 1000 + m, 256))
+        L = 10 + next(r) % 3
+        nb = L + next(r) % (L + 1)
+        bonds = []
+        while len(bonds) < nb:
+            i, j = next(r) % L, next(r) % L
+            if i != j:
+                bonds.append((i, j))
+        bonds += [bonds[0], bonds[1][::-1]]
+        n_up = 3 + next(r) % (L - 5)
+        fits = [n for n in range(1, L) if comb(L, n_up) * comb(L, n) <= 400_000]
+        n_dn = fits[next(r) % len(fits)]
+        U = -2.0 + 10.0 * ((next(r) >> 11) * 2.0 ** -53)
+        out.append(dict(name=f"random{m}_L{L}_{n_up}_{n_dn}", n_sites=L,
+                        bonds=np.array(bonds, dtype=np.int64), n_up=n_up, n_dn=n_dn,
+                        t=1.0, U=U))
+    return out
+
+
 def heldout_U(seed: int = 5, count: int = 16) -> np.ndarray:
     """Held-out interaction strengths uniform[0, 8) for the learned-start evaluation."""
     return 8.0 * (splitmix64(seed ^ 0x5555, count) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53

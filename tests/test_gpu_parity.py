@@ -619,3 +619,64 @@ def test_per_step_lowest_ritz_value_at_extreme_scales(ed, t, U, tol):
         w = scipy.linalg.eigvalsh_tridiagonal(a[:j], bt[:j - 1], select="i", select_range=(0, 0))
         scale = np.max(np.abs(a[:j])) + (np.max(np.abs(bt[:j - 1])) if j > 1 else 0.0)
         assert abs(hist[j - 1] - w[0]) <= 8 * EPS64 * max(scale, 1e-300), (j, hist[j - 1], w[0])
+
+
+# ------------------------------------------------- irregular lattices on the row-staged path
+RANDOM_LARGE = ed_inputs.random_lattices()
+
+
+def _tuple(case):
+    return (case["n_sites"], case["bonds"], case["n_up"], case["n_dn"], case["t"], case["U"])
+
+
+@pytest.fixture(scope="module")
+def random_large_reference():
+    """Oracle a_j, b_{j+1} of 12 steps of plain Algorithm 1 (no reorthogonalisation) from
+    the seeded start, one explicit H per lattice."""
+    out = {}
+    for case in RANDOM_LARGE:
+        H = hamiltonian.hamiltonian_csr(*_tuple(case))
+        f1 = olz.normalized_start(ed_inputs.start_vector_raw(41, H.shape[0]))
+        out[case["name"]] = (f1, olz.lanczos(lambda v: H @ v, f1, max_steps=12, reorth=False,
+                                             fixed_steps=True))
+    return out
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("case", RANDOM_LARGE, ids=lambda c: c["name"])
+def test_random_lattices_hv_elementwise(ed, case, dtype):
+    """ed_hv on irregular bond lists (uneven degrees, a doubled and a reversed bond, U of
+    either sign) with 210 to 792 up rows, every element against the oracle's rows within
+    the rounding bound."""
+    L, bonds, nu, nd, t, U = _tuple(case)
+    b = ed.ed_build_basis(L, bonds, nu, nd)
+    try:
+        dim = ed.ed_basis_dims(b)[2]
+        tdt = torch.float64 if dtype == "f64" else torch.float32
+        xd = torch.tensor(ed_inputs.uniform_pm1(43, dim), device="cuda", dtype=tdt)
+        yd = torch.empty_like(xd)
+        ed.ed_hv(b, t, U, xd, yd)
+        xr = xd.double().cpu().numpy()
+        rows = np.arange(dim)
+        ref = hamiltonian.hv_rows(L, bonds, nu, nd, t, U, xr, rows)
+        bound = _hv_bound(_tuple(case), xr, rows, EPS64 if dtype == "f64" else EPS32)
+        err = np.abs(yd.double().cpu().numpy() - ref)
+        assert np.all(err <= bound), float((err / bound).max())
+    finally:
+        ed.ed_basis_destroy(b)
+
+
+@pytest.mark.parametrize("dtype", F64_KINDS + ["f32"])
+@pytest.mark.parametrize("case", RANDOM_LARGE, ids=lambda c: c["name"])
+def test_random_lattices_alpha_beta_follow_oracle(ed, case, dtype, random_large_reference):
+    """The fused Lanczos step (autotuned variant) on the same irregular lattices: 12 steps
+    of a_j, b_{j+1} from the oracle's start vector against the oracle's plain Algorithm 1."""
+    L, bonds, nu, nd, t, U = _tuple(case)
+    f1, ref = random_large_reference[case["name"]]
+    fdev = torch.tensor(f1, dtype=torch.float32 if dtype == "f32" else torch.float64,
+                        device="cuda")
+    res = _solve(ed, L, bonds, nu, nd, t, U, max_steps=12, tol=0.0, f1=fdev, dtype=dtype)
+    assert res["steps"] == 12
+    tol = 2e-5 if dtype == "f32" else 1e-11
+    assert np.allclose(res["alpha"], ref.alpha, rtol=tol, atol=tol), (res["alpha"], ref.alpha)
+    assert np.allclose(res["beta"], ref.beta, rtol=tol, atol=tol), (res["beta"], ref.beta)

@@ -290,3 +290,14 @@ def test_random_lattices_all_geometries(seed):
     check_tables(hop, amp, bits, V, G, False)
     check_tables(hop, amp, bits, V, G, True)
     check_split(L, bonds, N, V, G, int(rng.integers(0, L)))
+
+
+@pytest.mark.parametrize("case", ed_inputs.random_lattices(), ids=lambda c: c["name"])
+def test_random_lattice_workloads_at_kernel_geometries(case):
+    """The random lattices the GPU parity tests run: both species' tables at the geometries
+    of the fused H.v's variants (int64: V = 2 with G = 16 or 8; FP32: V = 4 with G = 32, 16
+    or 8), every hop decoded back and every slot inside the staged row or its zero slots."""
+    for n in (case["n_up"], case["n_dn"]):
+        hop, amp, bits = hop_table(case["n_sites"], n, case["bonds"])
+        for V, G in ((2, 16), (2, 8), (4, 32), (4, 16), (4, 8)):
+            check_tables(hop, amp, bits, V, G, False)

@@ -72,3 +72,19 @@ def test_heldout_U():
     U = ed_inputs.heldout_U()
     assert U.shape == (16,) and ((U >= 0) & (U < 8)).all()
     assert not np.isin(U, np.arange(17) * 0.5).any()  # none on the training grid
+
+
+def test_random_lattices_as_described():
+    from math import comb
+    cases = ed_inputs.random_lattices()
+    again = ed_inputs.random_lattices()
+    assert all(a["name"] == b["name"] and np.array_equal(a["bonds"], b["bonds"]) and a["U"] == b["U"]
+               for a, b in zip(cases, again))
+    for c in cases:
+        L, b = c["n_sites"], c["bonds"]
+        assert 10 <= L <= 12 and L + 2 <= len(b) <= 2 * L + 2
+        assert np.all(b[:, 0] != b[:, 1]) and b.min() >= 0 and b.max() < L
+        assert tuple(b[-2]) == tuple(b[0]) and tuple(b[-1]) == tuple(b[1][::-1])
+        assert 3 <= c["n_up"] <= L - 3 and 1 <= c["n_dn"] <= L - 1
+        assert comb(L, c["n_up"]) * comb(L, c["n_dn"]) <= 400_000
+        assert -2.0 <= c["U"] < 8.0 and c["t"] == 1.0
