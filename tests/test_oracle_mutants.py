@@ -10,8 +10,9 @@ unmutated oracle passes the same battery through the same harness
 
 Only mutants that change a result are listed. Mutants that leave every result unchanged
 are not: for example, Algorithm 1's a_j taken against f_j + f_{j-1} instead of f_j
-(q_j . f_{j-1} = 0 by construction). The GPU library is not involved; everything runs on
-the CPU.
+(q_j . f_{j-1} = 0 by construction), or the sign of 2 pi J_a in the Lieb-Wu equations
+(the centred J set and its mirror image give the same energy). The GPU library is not
+involved; everything runs on the CPU.
 """
 import importlib
 import inspect
@@ -167,6 +168,10 @@ MUTANTS = [
     M("abs-rows-signed-U", "hamiltonian", ("y = abs(U) * popcount", "y = U * popcount")),
     M("abs-rows-down-hops-dropped", "hamiltonian",
       ("np.add.at(y, src, abs(t) * ax[col])", "np.add.at(y, src, 0.0 * ax[col])", 2)),
+    M("hop-table-sign-dropped", "hamiltonian", ("lists[r].append((t_, int(sg)))", "lists[r].append((t_, 1))")),
+    M("hop-table-source-as-target", "hamiltonian", ("lists[r].append((t_, int(sg)))", "lists[r].append((r, int(sg)))")),
+    M("hop-table-bond-order-reversed", "hamiltonian",
+      ("for src, s2, sign in hops_of(states, bonds):", "for src, s2, sign in hops_of(states, np.asarray(bonds)[::-1]):")),
     # tridiag: Sturm count and bisection for lambda_min(T), Sec. 2.2
     M("sturm-offdiag-not-squared", "tridiag", ("off = b[i - 1] * b[i - 1] / d", "off = b[i - 1] / d")),
     M("sturm-offdiag-sign", "tridiag", ("d = (a[i] - x) - off", "d = (a[i] - x) + off")),
@@ -196,6 +201,7 @@ MUTANTS = [
     M("double-occupancy-not-normalised", "observables", ("/ norm2", "/ 1.0")),
     M("double-occupancy-amplitude-not-squared", "observables", (") ** 2", ").__abs__()")),
     M("double-occupancy-up-twice", "observables", ("occ_up @ p2 @ occ_dn", "occ_up @ p2 @ occ_up[:len(dn)]")),
+    M("double-occupancy-site-shift", "observables", ("occ_dn = ((dn >> np.uint32(i))", "occ_dn = ((dn >> np.uint32((i + 1) % n_sites))")),
     # complex_hopping: complex amplitude per bond
     M("complex-conjugate-swapped-matrix", "complex_hopping",
       ("np.where(from_j, -tau[b], -np.conj(tau[b]))", "np.where(from_j, -np.conj(tau[b]), -tau[b])")),
@@ -211,6 +217,9 @@ MUTANTS = [
       ("h[i, j] += -tau[b]", "h[j, i] += -tau[b]")),
     M("complex-u0-down-count", "complex_hopping", ("e[:n_up].sum() + e[:n_dn].sum()", "2.0 * e[:n_up].sum()")),
     M("real-view-imag-sign", "complex_hopping", ("out[1::2] = w.imag", "out[1::2] = -w.imag")),
+    M("complex-rows-up-column", "complex_hopping",
+      ("col = rank_of(up, s2) * dim_dn + (rows[src] % dim_dn)", "col = rank_of(up, s2) * dim_dn + (rows[src] // dim_dn) % dim_dn")),
+    M("complex-rows-end-test", "complex_hopping", ("j = int(bonds[b, 1])", "j = int(bonds[b, 0])")),
     # mlp: the start-vector network
     M("bf16-round-half-up", "mlp", ("np.uint64(0x7FFF) + lsb", "np.uint64(0x8000)")),
     M("bf16-truncates", "mlp", ("np.uint64(0x7FFF) + lsb", "np.uint64(0)")),
@@ -224,6 +233,10 @@ MUTANTS = [
                                       "h1b = h1\n    h2 = np.tanh(h1b @ W2 + b2)\n    out = h2 @ W3 + b3\n    return")),
     M("forward-outputs-swapped", "mlp", ("return out[:, 0], out[:, 1], (x, h1, h2)", "return out[:, 1], out[:, 0], (x, h1, h2)")),
     M("predict-sign-inverted", "mlp", ("np.where(z >= 0, 1.0, -1.0)", "np.where(z >= 0, -1.0, 1.0)")),
+    M("unpack-b1-offset", "mlp", ("b1 = p[o:o + HIDDEN]; o += HIDDEN\n    W2", "b1 = p[o + 1:o + 1 + HIDDEN]; o += HIDDEN\n    W2")),
+    M("unpack-W3-layout", "mlp", ("W3 = p[o:o + HIDDEN * 2].reshape(HIDDEN, 2)", "W3 = p[o:o + HIDDEN * 2].reshape(2, HIDDEN).T")),
+    M("param-count-short", "mlp", ("+ HIDDEN * 2 + 2\n", "+ HIDDEN * 2\n")),
+    M("features-site-order", "mlp", ("x[:, i] = (up >> i) & 1", "x[:, n_sites - 1 - i] = (up >> i) & 1")),
     M("loss-hidden-W2-transposed", "mlp", ("h2 = np.tanh(h1b @ W2 + b2)\n    out = h2 @ W3 + b3\n    a, z",
                                            "h2 = np.tanh(h1b @ W2.T + b2)\n    out = h2 @ W3 + b3\n    a, z")),
     M("loss-weight-not-squared", "mlp", ("weight_scale * psi * psi", "weight_scale * np.abs(psi)")),
@@ -242,6 +255,8 @@ MUTANTS = [
     M("bethe-charge-sign", "bethe", ("L * k - 2 * np.pi * I + _theta", "L * k - 2 * np.pi * I - _theta")),
     M("bethe-energy-scale", "bethe", ("-2.0 * t * np.sum(np.cos(k))", "-t * np.sum(np.cos(k))")),
     M("bethe-lowest-spin-only", "bethe", ("cands = range(min(n_up, n_dn) + 1)", "cands = [min(n_up, n_dn)]")),
+    M("bethe-numbers-off-centre", "bethe", ("q = np.arange(n, dtype=np.float64) - (n - 1) / 2.0",
+                                            "q = np.arange(n, dtype=np.float64) - (n - 1) / 2.0 + 1.0")),
 ]
 
 
@@ -279,7 +294,7 @@ def _install(monkeypatch, name, mutant):
 
 
 def test_battery_passes_unmutated():
-    assert len(BATTERY) >= 149
+    assert len(BATTERY) >= 151
     assert _first_failure(BATTERY) is None
 
 

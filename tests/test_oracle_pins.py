@@ -135,6 +135,32 @@ def test_rows_match_columns(case):
     assert np.allclose(hamiltonian.hv_rows(*case, x, rows), H @ x, rtol=0, atol=1e-13)
 
 
+@pytest.mark.parametrize("L,bonds,N", [
+    (8, ed_inputs.ring_bonds(8), 3),
+    (9, np.array([[0, 5], [3, 8], [1, 2], [7, 0], [6, 4], [2, 8], [5, 1], [8, 3]]), 4),
+])
+def test_hop_table_rebuilds_the_single_species_hamiltonian(L, bonds, N):
+    """The per-state hop lists (the reference of the device hop tables) hold, for state r,
+    the hopped states' ranks and signs in bond order: summing -sign |target><r| over them
+    gives the one-species Hamiltonian at U = 0 (pinned above by the free-fermion energies
+    and the symmetries), and entry k of state r comes from the k-th bond that moves one of
+    its particles."""
+    states, lists = hamiltonian.species_hop_table(L, N, bonds)
+    n = len(states)
+    M = np.zeros((n, n))
+    for r, lst in enumerate(lists):
+        for tgt, sg in lst:
+            M[tgt, r] += -1.0 * sg
+    H = hamiltonian.hamiltonian_csr(L, bonds, N, 0, 1.0, 0.0).toarray()
+    assert np.array_equal(M, H)
+    for r, lst in enumerate(lists):
+        movers = [b for b, (i, j) in enumerate(bonds) if ((states[r] >> i) & 1) != ((states[r] >> j) & 1)]
+        assert len(movers) == len(lst)
+        for (tgt, _), b in zip(lst, movers):
+            i, j = bonds[b]
+            assert states[tgt] == states[r] ^ ((1 << int(i)) | (1 << int(j)))
+
+
 def test_wrap_sign_is_fermionic():
     """Ring wrap-around hop with N particles crosses the other N-1: sign (-1)^(N-1)."""
     for N in (2, 3, 4):
